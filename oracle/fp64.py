@@ -1,0 +1,270 @@
+"""FP64 CPU oracle for the sWLR algorithm of Dutta & Li, "A Fast Algorithm for a
+Weighted Low Rank Approximation" (arXiv 1703.06303).
+
+TEST INFRASTRUCTURE ONLY.  This module is the plain, slow, obviously-correct
+restatement of the method that the CUDA path is checked against.  Only the test
+suite, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` / reference leg of
+``bench.py`` may import or run it.  The product path never does, and this module
+imports nothing from the product package.
+
+Everything is float64 NumPy / LAPACK.  Library primitives used as single steps:
+``numpy.linalg.qr`` (Householder thin QR), ``numpy.linalg.svd`` (thin SVD),
+``numpy.linalg.solve`` (per-row dense solve), ``scipy.linalg.solve_triangular``.
+No blocking, fusion or reordering beyond what the paper states.
+
+Notation (Section 1 and Section 3 of the paper):
+  A = (A1 A2) in R^{m x n}; A1 = first k columns (the weighted frames), A2 = rest.
+  W = (W1 1);  W1 in R_+^{m x k} (taken strictly positive, as Theorem 2 needs).
+  r = target rank, s = r - k = rank budget of D.
+  F(X1, C, D) = ||(A1 - X1) o W1||_F^2 + ||A2 - X1 C - D||_F^2      (Eq. 8)
+
+Readings of the paper taken here (each also listed in the design doc):
+  * The gradient in Section 3 is written F(X1, C_p, B_p): B_p is read as D_p.
+  * The row update "sequentially along each row" uses E_p computed before the
+    loop (Algorithm 1), so the m rows are independent (Jacobi-style update).
+  * Output of Algorithm 1 after p <- p+1: C and D are recomputed for the final X1.
+  * X_p = (X1_p, X1_p C_p + D_p) as in Section 4.1 (the update-rule display of
+    Section 3 shifts the index by one; Section 4.1's form is used).
+  * Error_p = ||X_{p+1} - X_p||_F; stop if Error_p < eps or Error_p/||X_p||_F < eps
+    or max_iter is reached (Section 4.1); "relative" mode uses the second test only.
+  * r = k is allowed (Theorem 1 allows r >= k): H_0 = 0, so D = 0.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+from scipy.linalg import solve_triangular
+
+__all__ = [
+    "hard_threshold", "ghs", "objective", "cd_step", "objective_tilde", "x1_update",
+    "x1_update_row_constant", "swlr_step", "swlr", "splitmix64", "random_normal_init",
+    "SwlrResult",
+]
+
+
+# --------------------------------------------------------------------------- L0
+def hard_threshold(A: np.ndarray, r: int) -> np.ndarray:
+    """H_r(A) = U Sigma_r V^T: keep the r largest singular triplets (Eq. 2,
+    Eckart-Young-Mirsky).  r = 0 gives the zero matrix."""
+    A = np.asarray(A, dtype=np.float64)
+    if r <= 0 or A.size == 0:
+        return np.zeros_like(A)
+    U, sig, Vt = np.linalg.svd(A, full_matrices=False)
+    r = min(r, sig.size)
+    return (U[:, :r] * sig[:r]) @ Vt[:r]
+
+
+def ghs(A1: np.ndarray, A2: np.ndarray, r: int) -> np.ndarray:
+    """Theorem 1 (Golub-Hoffman-Stewart, Eq. 4): the X2 that keeps A1 exactly and
+    minimises ||A2 - X2||_F subject to rank(A1 X2) <= r is
+    P_{A1}(A2) + H_{r-k}(P_perp_{A1}(A2)), k = rank(A1), r >= k.
+    A1 is taken to have full column rank k (its column count)."""
+    A1 = np.asarray(A1, dtype=np.float64)
+    A2 = np.asarray(A2, dtype=np.float64)
+    k = A1.shape[1]
+    Q, _ = np.linalg.qr(A1, mode="reduced")
+    PA2 = Q @ (Q.T @ A2)
+    return PA2 + hard_threshold(A2 - PA2, r - k)
+
+
+# --------------------------------------------------------------------------- L2
+def objective(A: np.ndarray, W1: np.ndarray, X1: np.ndarray, C: np.ndarray,
+              D: np.ndarray) -> float:
+    """F(X1, C, D) of Eq. 8, written out directly (no cancellation shortcut)."""
+    k = W1.shape[1]
+    A1, A2 = A[:, :k], A[:, k:]
+    t1 = np.sum(((A1 - X1) * W1) ** 2)
+    t2 = np.sum((A2 - X1 @ C - D) ** 2)
+    return float(t1 + t2)
+
+
+# --------------------------------------------------------------------------- L3
+@dataclass
+class CD:
+    """Result of the (C, D) step for a fixed X1 (Section 3)."""
+    Q: np.ndarray      # m x k, orthonormal columns
+    R: np.ndarray      # k x k, upper triangular, X1 = Q R
+    B: np.ndarray      # k x n2, Q^T A2
+    C: np.ndarray      # k x n2, R^{-1} Q^T A2
+    P: np.ndarray      # m x n2, (I - Q Q^T) A2
+    sigma: np.ndarray  # singular values of P, descending
+    U: np.ndarray      # m x s left singular vectors kept in D
+    Vt: np.ndarray     # s x n2 right singular vectors kept in D
+    D: np.ndarray      # m x n2, U (Sigma)_s V^T
+
+
+def cd_step(A2: np.ndarray, X1: np.ndarray, s: int) -> CD:
+    """Given X1 (rank k), the minimisers of F(X1, ., .) over C and rank-s D
+    (Section 3, consequence of Theorem 2 / Theorem 1 with A1 := X1):
+        X1 = Q R (thin QR),  C = R^{-1} Q^T A2,
+        D = H_{s}((I - Q Q^T) A2) = U (Sigma)_{s} V^T."""
+    A2 = np.asarray(A2, dtype=np.float64)
+    X1 = np.asarray(X1, dtype=np.float64)
+    Q, R = np.linalg.qr(X1, mode="reduced")
+    B = Q.T @ A2
+    C = solve_triangular(R, B, lower=False)
+    P = A2 - Q @ B
+    m, n2 = P.shape
+    if n2 == 0:
+        sig = np.zeros(0)
+        U = np.zeros((m, 0)); Vt = np.zeros((0, 0))
+        D = np.zeros_like(P)
+    else:
+        Uf, sig, Vtf = np.linalg.svd(P, full_matrices=False)
+        s_eff = max(0, min(s, sig.size))
+        U = Uf[:, :s_eff]
+        Vt = Vtf[:s_eff]
+        D = (U * sig[:s_eff]) @ Vt
+    return CD(Q=Q, R=R, B=B, C=C, P=P, sigma=sig, U=U, Vt=Vt, D=D)
+
+
+def objective_tilde(A: np.ndarray, W1: np.ndarray, X1: np.ndarray, r: int) -> float:
+    """F~(X1) = min over C and rank-(r-k) D of F(X1, C, D): the objective of an
+    iterate, with (C, D) from the closed form of Section 3 (Theorem 2)."""
+    k = W1.shape[1]
+    cd = cd_step(A[:, k:], X1, r - k)
+    return objective(A, W1, X1, cd.C, cd.D)
+
+
+def x1_update(A: np.ndarray, W1: np.ndarray, C: np.ndarray, D: np.ndarray,
+              chunk: int = 4096) -> np.ndarray:
+    """X1 <- argmin_X1 F(X1, C, D), Eq. 9, solved row by row (Section 3):
+        E = A1 o W1 o W1 + (A2 - D) C^T,
+        X1(i,:) = E(i,:) (diag(W1(i,1)^2, ..., W1(i,k)^2) + C C^T)^{-1}.
+    The matrix is symmetric, so the row equation is solved as M_i x = E(i,:)^T.
+    Rows are independent; ``chunk`` only bounds the memory of the batched solve."""
+    k = W1.shape[1]
+    A1, A2 = A[:, :k], A[:, k:]
+    E = A1 * W1 * W1 + (A2 - D) @ C.T
+    G = C @ C.T
+    m = A.shape[0]
+    X1 = np.empty((m, k))
+    for i0 in range(0, m, chunk):
+        i1 = min(m, i0 + chunk)
+        M = np.repeat(G[None, :, :], i1 - i0, axis=0)
+        idx = np.arange(k)
+        M[:, idx, idx] += W1[i0:i1] ** 2
+        X1[i0:i1] = np.linalg.solve(M, E[i0:i1, :, None])[:, :, 0]
+    return X1
+
+
+def x1_update_row_constant(A: np.ndarray, w: np.ndarray, C: np.ndarray,
+                           D: np.ndarray) -> np.ndarray:
+    """The same update when W1(i,:) = w_i is constant along each row: then
+    M_i = w_i^2 I + G with G = C C^T = V diag(lam) V^T, so
+    X1(i,:) = ((E V)(i,:) / (w_i^2 + lam)) V^T.  Used as an independent check of
+    the general row solve (a different route to the same unique minimiser)."""
+    k = C.shape[0]
+    A1, A2 = A[:, :k], A[:, k:]
+    w = np.asarray(w, dtype=np.float64).reshape(-1)
+    E = A1 * (w ** 2)[:, None] + (A2 - D) @ C.T
+    lam, V = np.linalg.eigh(C @ C.T)
+    return ((E @ V) / ((w ** 2)[:, None] + lam[None, :])) @ V.T
+
+
+@dataclass
+class StepOut:
+    X1_next: np.ndarray
+    cd: CD
+    F: float           # F_p = F(X1_p, C_p, D_p)
+
+
+def swlr_step(A: np.ndarray, W1: np.ndarray, X1: np.ndarray, r: int) -> StepOut:
+    """One pass of the loop body of Algorithm 1: QR and SVD for X1_p, C_p, D_p,
+    E_p, then the m independent row updates giving X1_{p+1}."""
+    k = W1.shape[1]
+    cd = cd_step(A[:, k:], X1, r - k)
+    F = objective(A, W1, X1, cd.C, cd.D)
+    X1n = x1_update(A, W1, cd.C, cd.D)
+    return StepOut(X1_next=X1n, cd=cd, F=F)
+
+
+@dataclass
+class SwlrResult:
+    X1: np.ndarray
+    X2: np.ndarray
+    iters: int                       # number of X1 updates performed
+    converged: bool
+    F: list = field(default_factory=list)        # F_p for p = 0..iters
+    error: list = field(default_factory=list)    # Error_p = ||X_{p+1} - X_p||_F
+    rel_error: list = field(default_factory=list)
+    X1_history: list = field(default_factory=list)
+
+
+def swlr(A: np.ndarray, W1: np.ndarray, r: int, X1_0: np.ndarray, eps: float = 1e-7,
+         max_iter: int = 100, stop: str = "paper", keep_history: bool = False) -> SwlrResult:
+    """Algorithm 1 (sWLR).  Input A = (A1 A2), W = (W1 1), threshold eps; X1_0 the
+    initial X1.  Each iteration forms Q_p R_p = X1_p, C_p, D_p, E_p and the row
+    updates.  Stopping rule of Section 4.1 with X_p = (X1_p, X1_p C_p + D_p):
+      stop = "paper":    Error_p < eps or Error_p / ||X_p||_F < eps,
+      stop = "relative": Error_p / ||X_p||_F < eps,
+      stop = "none":     run max_iter updates.
+    Output (X1_p, X1_p C_p + D_p) with C_p, D_p recomputed for the final X1."""
+    A = np.asarray(A, dtype=np.float64)
+    W1 = np.asarray(W1, dtype=np.float64)
+    k = W1.shape[1]
+    A2 = A[:, k:]
+    s = r - k
+    X1 = np.array(X1_0, dtype=np.float64, copy=True)
+    cd = cd_step(A2, X1, s)
+    X2 = X1 @ cd.C + cd.D
+    res = SwlrResult(X1=X1, X2=X2, iters=0, converged=False)
+    res.F.append(objective(A, W1, X1, cd.C, cd.D))
+    if keep_history:
+        res.X1_history.append(X1.copy())
+    for p in range(max_iter):
+        X1n = x1_update(A, W1, cd.C, cd.D)
+        cdn = cd_step(A2, X1n, s)
+        X2n = X1n @ cdn.C + cdn.D
+        err = math.sqrt(float(np.sum((X1n - X1) ** 2) + np.sum((X2n - X2) ** 2)))
+        nrm = math.sqrt(float(np.sum(X1 ** 2) + np.sum(X2 ** 2)))
+        rel = err / nrm if nrm > 0 else math.inf
+        X1, cd, X2 = X1n, cdn, X2n
+        res.F.append(objective(A, W1, X1, cd.C, cd.D))
+        res.error.append(err)
+        res.rel_error.append(rel)
+        res.iters = p + 1
+        if keep_history:
+            res.X1_history.append(X1.copy())
+        if stop == "paper" and (err < eps or rel < eps):
+            res.converged = True
+            break
+        if stop == "relative" and rel < eps:
+            res.converged = True
+            break
+    res.X1, res.X2 = X1, X2
+    return res
+
+
+# ------------------------------------------------------------- random init (L4)
+_MASK64 = (1 << 64) - 1
+_GAMMA = 0x9E3779B97F4A7C15
+
+
+def splitmix64(seed: int, n: np.ndarray) -> np.ndarray:
+    """Output number n (0-based) of the SplitMix64 generator seeded with ``seed``
+    (Steele, Lea & Flood, OOPSLA 2014): state_n = seed + (n+1)*gamma, then the
+    64-bit finaliser with shifts 30, 27, 31 and the published multipliers."""
+    n = np.asarray(n, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed & _MASK64) + (n + np.uint64(1)) * np.uint64(_GAMMA)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def random_normal_init(m: int, k: int, seed: int) -> np.ndarray:
+    """The "random matrix" initial X1 (Section 4.1), distribution fixed here as
+    i.i.d. N(0,1): element (i, a) has column-major index t = i + a*m and uses
+    SplitMix64 outputs 2t and 2t+1 as uniforms u1, u2 = (x >> 11) * 2^-53; then the
+    Box-Muller transform z = sqrt(-2 ln(1 - u1)) cos(2 pi u2)."""
+    t = np.arange(m * k, dtype=np.uint64)
+    x1 = splitmix64(seed, np.uint64(2) * t)
+    x2 = splitmix64(seed, np.uint64(2) * t + np.uint64(1))
+    u1 = (x1 >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+    u2 = (x2 >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+    z = np.sqrt(-2.0 * np.log1p(-u1)) * np.cos(2.0 * np.pi * u2)
+    return z.reshape((k, m)).T.copy()
