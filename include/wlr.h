@@ -1,0 +1,187 @@
+/*
+ * wlr.h -- C ABI of the GB300 sWLR library (libwlr.so).
+ *
+ * Solves the special weighted low-rank approximation of Dutta & Li,
+ * "A Fast Algorithm for a Weighted Low Rank Approximation" (arXiv 1703.06303):
+ *
+ *     min_{X1, X2 : rank(X1 X2) <= r}  ||(A1 - X1) o W1||_F^2 + ||A2 - X2||_F^2     (Eq. 5)
+ *
+ * with A = (A1 A2) in R^{m x n}, A1 the first k columns (the weighted frames), and
+ * W1 in R^{m x k}, W1 > 0 (Theorem 2 needs strictly positive weights).  The solver is
+ * Algorithm 1 (sWLR): per iteration p
+ *     X1_p = Q_p R_p,  C_p = R_p^{-1} Q_p^T A2,  D_p = H_{r-k}((I - Q_p Q_p^T) A2),
+ *     E_p = A1 o W1 o W1 + (A2 - D_p) C_p^T,
+ *     X1_{p+1}(i,:) = E_p(i,:) (diag(W1(i,:)^2) + C_p C_p^T)^{-1}   for every row i.
+ *
+ * Conventions for every entry point:
+ *   - Matrices are column-major with a leading dimension (columns = video frames,
+ *     rows = pixels).  A is m x n with lda >= m; W1 and X1 are m x k.
+ *   - Pointers are plain host or device pointers; the memory argument says which.
+ *     Caller-owned device buffers passed to wlr_set_data are borrowed (not copied,
+ *     not modified) when their dtype matches the handle's precision and they are
+ *     device memory; they must then stay valid until wlr_destroy or the next
+ *     wlr_set_data.  In every other case the library copies them.
+ *   - The library owns all of its workspace; it allocates in wlr_create and frees in
+ *     wlr_destroy.
+ *   - Work is issued on the handle's CUDA stream.  Entry points that return a host
+ *     scalar or copy into host memory synchronise that stream; the others are
+ *     asynchronous.
+ *   - Nothing aborts: every failure is a returned status, and wlr_last_error gives a
+ *     one-line message.  Device-side failures (a row system that is not positive
+ *     definite, a rank-deficient X1) set an error word that the next synchronising
+ *     call reports.
+ */
+#ifndef WLR_H
+#define WLR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  WLR_OK = 0,
+  WLR_ERR_INVALID_ARG = 1,        /* shape, k >= 1, k <= r <= min(m, n), null pointer  */
+  WLR_ERR_NONPOSITIVE_WEIGHT = 2, /* some W1 entry <= 0 or not finite (Theorem 2)       */
+  WLR_ERR_RANK_DEFICIENT = 3,     /* Cholesky of X1^T X1 broke down (Eq. 8 needs rank k)*/
+  WLR_ERR_NOT_SPD = 4,            /* a row system diag(W1(i,:)^2) + C C^T broke down    */
+  WLR_ERR_NO_CONVERGENCE = 5,     /* max_iter reached first: a warning, results valid   */
+  WLR_ERR_DEVICE_TIMEOUT = 6,     /* a bounded device wait gave up                       */
+  WLR_ERR_CUDA = 7,               /* a CUDA runtime call failed                          */
+  WLR_ERR_OOM = 8,                /* device allocation failed                            */
+  WLR_ERR_NOT_READY = 9,          /* call order: e.g. wlr_step before wlr_set_data       */
+  WLR_ERR_UNSUPPORTED = 10        /* size outside what this build supports (k > 64 ...) */
+} wlr_status;
+
+typedef enum { WLR_F32 = 0, WLR_F64 = 1 } wlr_dtype;
+typedef enum { WLR_MEM_DEVICE = 0, WLR_MEM_HOST = 1 } wlr_memory;
+
+/* Arithmetic of the iteration.  FP64: every step in double.  FP32: float storage
+ * and arithmetic, partial sums across thread blocks added in double. */
+typedef enum { WLR_PREC_FP64 = 0, WLR_PREC_FP32 = 1 } wlr_precision;
+
+/* Initial X1 (Algorithm 1, "Initialize (X1)_0"; Section 4.1 uses a random matrix). */
+typedef enum {
+  WLR_INIT_A1 = 0,      /* X1_0 = A1                                                    */
+  WLR_INIT_RANDOM = 1,  /* X1_0 i.i.d. N(0,1): element (i,a), t = i + a*m, uses          */
+                        /* SplitMix64(seed) outputs 2t, 2t+1 as u1, u2 = (x >> 11) 2^-53, */
+                        /* z = sqrt(-2 ln(1 - u1)) cos(2 pi u2)  (Box-Muller)            */
+  WLR_INIT_USER = 2     /* X1_0 given by the caller                                     */
+} wlr_init;
+
+/* Stopping rule of Section 4.1 with X_p = (X1_p, X1_p C_p + D_p) and
+ * Error_p = ||X_{p+1} - X_p||_F. */
+typedef enum {
+  WLR_STOP_PAPER = 0,     /* Error_p < tol or Error_p / ||X_p||_F < tol              */
+  WLR_STOP_RELATIVE = 1,  /* Error_p / ||X_p||_F < tol                               */
+  WLR_STOP_NONE = 2,      /* run exactly max_iter iterations                          */
+  WLR_STOP_OBJECTIVE = 3  /* |F_{p-1} - F_p| / F_p < tol (in-loop objective)          */
+} wlr_stop;
+
+typedef struct {
+  int32_t precision;      /* wlr_precision (default FP32)                                */
+  int32_t stop;           /* wlr_stop (default WLR_STOP_RELATIVE)                        */
+  int32_t eig_block;      /* subspace block size b >= r-k for the rank-(r-k) SVD step;  */
+                          /* 0 = min(n-k, 32, max(r-k+8, 2(r-k)))                      */
+  int32_t eig_iters;      /* subspace iterations per sWLR iteration (warm start); 0 = 2 */
+  int32_t eig_iters_cold; /* subspace iterations from a cold start; 0 = 40              */
+  int32_t use_graph;      /* capture one iteration in a CUDA graph and replay it (1)    */
+  uint64_t seed;          /* seed of the random subspace start (and WLR_INIT_RANDOM)     */
+} wlr_options;
+
+typedef struct wlr_handle_s* wlr_handle;
+
+/* Fill *opt with the defaults listed above. */
+void wlr_default_options(wlr_options* opt);
+
+/* Create a solver for an m x n problem with k weighted columns and target rank r.
+ * Requires 1 <= k <= 64, k <= r <= min(m, n), r - k <= 32.  opt may be NULL
+ * (defaults).  cuda_stream is a cudaStream_t (NULL = the library creates its own).
+ * Allocates all device workspace.  Returns WLR_ERR_INVALID_ARG / _UNSUPPORTED /
+ * _OOM / _CUDA on failure, with *out set to NULL. */
+wlr_status wlr_create(wlr_handle* out, int64_t m, int64_t n, int64_t k, int64_t r,
+                      const wlr_options* opt, void* cuda_stream);
+
+/* Attach the data of Eq. 5: A (m x n, leading dimension lda) and W1 (m x k,
+ * leading dimension ldw), both of dtype dt in memory mem.  Runs the once-per-problem
+ * setup: ||A2||_F^2 and K = A2^T A2 (the Gram of the unweighted frames, used to form
+ * (P_perp A2)^T (P_perp A2) = K - B^T B each iteration).  Checks W1 > 0 and finite
+ * (synchronises): WLR_ERR_NONPOSITIVE_WEIGHT otherwise. */
+wlr_status wlr_set_data(wlr_handle h, const void* A, int64_t lda, const void* W1,
+                        int64_t ldw, wlr_dtype dt, wlr_memory mem);
+
+/* Set X1_0 (Algorithm 1, initialisation).  X1_0 (m x k, leading dimension ldx, dtype
+ * dt, memory mem) is read only for WLR_INIT_USER and may be NULL otherwise.  Resets
+ * the iteration counter and the subspace warm start. */
+wlr_status wlr_set_init(wlr_handle h, wlr_init kind, const void* X1_0, int64_t ldx,
+                        wlr_dtype dt, wlr_memory mem, uint64_t seed);
+
+/* One sWLR iteration (one pass of the loop body of Algorithm 1): from X1_p compute
+ * C_p, D_p, the objective F_p = F(X1_p, C_p, D_p) (Eq. 8) and X1_{p+1}.  If
+ * objective_out is non-NULL the call synchronises and stores F_p there (computed as
+ * ||(A1-X1_p) o W1||^2 + ||A2||^2 - ||Q_p^T A2||^2 - sum of the r-k largest
+ * sigma_j(P_perp A2)^2, i.e. the in-loop value). */
+wlr_status wlr_step(wlr_handle h, double* objective_out);
+
+/* Run Algorithm 1 from the current X1 until the stopping rule of the options holds
+ * with threshold tol (Section 4.1 uses 1e-7) or max_iter iterations are done.
+ * Synchronises.  *iters_out = iterations run, *objective_out = the last F_p (either
+ * may be NULL).  Returns WLR_ERR_NO_CONVERGENCE (a warning; results valid) if
+ * max_iter was reached with a rule other than WLR_STOP_NONE. */
+wlr_status wlr_solve(wlr_handle h, double tol, int32_t max_iter, int32_t* iters_out,
+                     double* objective_out);
+
+/* F~(X1) = min_{C, rank-(r-k) D} F(X1, C, D) for the current X1, evaluated in FP64
+ * with the residual ||A2 - X1 C - D||_F^2 summed entry by entry and the rank-(r-k)
+ * SVD step iterated to convergence.  Synchronises.  For an FP32 handle this builds
+ * (once) an FP64 copy of the problem. */
+wlr_status wlr_objective(wlr_handle h, double* F_out);
+
+/* Copy the current X1 (m x k) to X1 and, if X2 is non-NULL, X2 = X1 C + D
+ * (m x (n-k)) with C, D recomputed for this X1 (the output of Algorithm 1).
+ * dt/mem describe the destination buffers.  Synchronises when mem is host. */
+wlr_status wlr_get_result(wlr_handle h, void* X1, int64_t ldx, void* X2, int64_t ldx2,
+                          wlr_dtype dt, wlr_memory mem);
+
+/* Factors of the last (C, D) step: C (k x (n-k)), V_s (the (n-k) x (r-k) right
+ * singular vectors kept in D) and sigma2 (the r-k largest sigma_j(P_perp A2)^2).
+ * Any pointer may be NULL.  Host memory, double precision, column-major.
+ * Synchronises. */
+wlr_status wlr_get_factors(wlr_handle h, double* C, double* Vs, double* sigma2);
+
+/* Per-iteration history of the last wlr_solve / wlr_step calls since wlr_set_init:
+ * F (in-loop objective F_p) and err (Error_p / ||X_p||_F, only with the paper or
+ * relative stop rule; else NaN), up to cap entries each (host, may be NULL).
+ * *count_out = entries available.  Synchronises. */
+wlr_status wlr_get_history(wlr_handle h, double* F, double* rel_err, int32_t cap,
+                           int32_t* count_out);
+
+/* Iterations performed since wlr_set_init. */
+wlr_status wlr_get_iteration(wlr_handle h, int32_t* p_out);
+
+/* Release the handle and all its device memory.  NULL is accepted. */
+wlr_status wlr_destroy(wlr_handle h);
+
+/* Static string for a status code. */
+const char* wlr_status_string(wlr_status s);
+
+/* Message of the last failing call on h (or of wlr_create when h is NULL). */
+const char* wlr_last_error(wlr_handle h);
+
+/* Measurement aid: run reps further sWLR iterations without CUDA graphs, each kernel
+ * bracketed by CUDA events on the handle's stream.  For up to max_kernels distinct
+ * kernels: names ('\n'-separated, NUL-terminated, at most names_cap bytes), total
+ * milliseconds and launch counts.  Advances the iterate like wlr_solve.  Synchronises. */
+wlr_status wlr_profile(wlr_handle h, int32_t reps, char* names, int32_t names_cap,
+                       double* ms_total, int32_t* launches, int32_t max_kernels,
+                       int32_t* n_kernels);
+
+/* Number of kernels this handle has launched (graph replays count each node). */
+int64_t wlr_kernel_launches(wlr_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WLR_H */

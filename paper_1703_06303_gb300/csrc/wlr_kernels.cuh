@@ -1,0 +1,1032 @@
+// Device kernels of the sWLR iteration (Dutta & Li, arXiv 1703.06303, Algorithm 1).
+//
+// Every kernel is templated on the storage/arithmetic type T (float or double).
+// Matrices are column-major with leading dimensions; A2 = A + k*lda.
+//
+// Step map (Section 3 / Algorithm 1):
+//   a1  X1 = Q R by CholeskyQR2:  S1 = X1^T X1 -> R1;  Q1 = X1 R1^{-1};
+//       S2 = Q1^T Q1 -> R2;  R = R2 R1                    gemm_tn_partial, chol_small, form_q
+//   a2  B = Q^T A2 = R2^{-T} Q1^T A2,  C = R^{-1} B        gemm_tn_partial, coef_kernel
+//   a3  D = H_{r-k}((I - Q Q^T) A2) through the Gram (P_perp A2)^T (P_perp A2) = K - B^T B,
+//       K = A2^T A2 formed once; top-(r-k) eigenpairs by subspace iteration with
+//       Rayleigh-Ritz (parallel Jacobi on the b x b projection)
+//                                                         form_g2, eig_mult, eig_small, eig_update
+//   a4  E = A1 o W1 o W1 + A2 C^T - U_s (V_s^T C^T), U_s = A2 V_s - X1 (C V_s)  = (A2 - D) C^T
+//   a5  X1(i,:) = E(i,:) (diag(W1(i,:)^2) + C C^T)^{-1}   prep_rowpass, row_pass
+//   a6  F_p = ||(A1-X1) o W1||^2 + ||A2||^2 - ||B||^2 - sum_{j<=r-k} sigma_j^2
+//                                                         finalize_objective, x2_pass (exact)
+#pragma once
+
+#include "wlr_common.cuh"
+
+namespace wlr {
+
+constexpr int EIG_BMAX = 32;   // largest subspace block (Jacobi size)
+
+// --------------------------------------------------------------------------------
+// part[off + c*stride + a + b*P] = sum_{i in rows of chunk c} X[i + a*ldx] * Y[i + b*ldy]
+// for a < P, b < Q.  One (PT x QT) output tile per block, rows in steps of 32.
+// Thread (tx, ty) owns rows ty + (PT/4) u and columns tx + (QT/4) v of the tile, so the
+// shared-memory reads are conflict-free.
+template <typename T, int PT, int QT>
+__global__ void __launch_bounds__((PT / 4) * (QT / 4))
+gemm_tn_partial(const T* __restrict__ X, int64_t ldx, const T* __restrict__ Y, int64_t ldy,
+                int m, int P, int Q, int chunk_rows, T* __restrict__ part,
+                int64_t part_stride, int64_t part_offset) {
+  constexpr int BK = 32;
+  constexpr int NTX = QT / 4, NTY = PT / 4, NT = NTX * NTY;
+  __shared__ T Xs[BK][PT + 1];
+  __shared__ T Ys[BK][QT + 1];
+  const int a0 = blockIdx.x * PT, b0 = blockIdx.y * QT, c = blockIdx.z;
+  const int i_begin = c * chunk_rows;
+  const int i_end = min(m, i_begin + chunk_rows);
+  const int tx = threadIdx.x % NTX, ty = threadIdx.x / NTX;
+  T acc[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
+
+  for (int i0 = i_begin; i0 < i_end; i0 += BK) {
+    for (int e = threadIdx.x; e < BK * PT; e += NT) {
+      const int kk = e % BK, a = e / BK;
+      const int i = i0 + kk, ga = a0 + a;
+      Xs[kk][a] = (i < i_end && ga < P) ? X[i + (int64_t)ga * ldx] : T(0);
+    }
+    for (int e = threadIdx.x; e < BK * QT; e += NT) {
+      const int kk = e % BK, b = e / BK;
+      const int i = i0 + kk, gb = b0 + b;
+      Ys[kk][b] = (i < i_end && gb < Q) ? Y[i + (int64_t)gb * ldy] : T(0);
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < BK; ++kk) {
+      T xa[4], yb[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) xa[u] = Xs[kk][ty + NTY * u];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) yb[v] = Ys[kk][tx + NTX * v];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fma(xa[u], yb[v], acc[u][v]);
+    }
+    __syncthreads();
+  }
+  T* out = part + part_offset + (int64_t)c * part_stride;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int a = a0 + ty + NTY * u;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int b = b0 + tx + NTX * v;
+      if (a < P && b < Q) out[a + (int64_t)b * P] = acc[u][v];
+    }
+  }
+}
+
+// out64[e] = sum_c part[c*stride + e] (in double, fixed order); outT the same rounded.
+template <typename T>
+__global__ void reduce_partials(const T* __restrict__ part, int64_t stride, int nchunks,
+                                int64_t len, double* __restrict__ out64, T* __restrict__ outT) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < len;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int c = 0; c < nchunks; ++c) s += (double)part[(int64_t)c * stride + e];
+    if (out64) out64[e] = s;
+    if (outT) outT[e] = (T)s;
+  }
+}
+
+// Sum of squares of an m x ncols column-major block, partial per block (double).
+template <typename T>
+__global__ void sumsq_partial(const T* __restrict__ A, int64_t lda, int m, int ncols,
+                              double* __restrict__ part) {
+  __shared__ double sh[32];
+  const int64_t total = (int64_t)m * ncols;
+  double s = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = e / m, i = e - j * m;
+    const double v = (double)A[i + j * lda];
+    s += v * v;
+  }
+  s = block_sum_double(s, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// W1 > 0 and finite everywhere, else set the error bit.
+template <typename T>
+__global__ void check_weights(const T* __restrict__ W1, int64_t ldw, int m, int k,
+                              int* __restrict__ err) {
+  const int64_t total = (int64_t)m * k;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = e / m, i = e - j * m;
+    const T w = W1[i + j * ldw];
+    if (!(w > T(0)) || !wfinite(w)) atomicOr(err, ERRBIT_BAD_WEIGHT);
+  }
+}
+
+// dst (m x ncols, ld_dst) <- src (m x ncols, ld_src) with type conversion.
+template <typename TD, typename TS>
+__global__ void convert_copy(TD* __restrict__ dst, int64_t ld_dst, const TS* __restrict__ src,
+                             int64_t ld_src, int m, int ncols) {
+  const int64_t total = (int64_t)m * ncols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = e / m, i = e - j * m;
+    dst[i + j * ld_dst] = (TD)src[i + j * ld_src];
+  }
+}
+
+// X1_0 i.i.d. N(0,1) from the counter-based SplitMix64 + Box-Muller stream.
+template <typename T>
+__global__ void random_normal_fill(T* __restrict__ X, int64_t ldx, int m, int k, uint64_t seed) {
+  const int64_t total = (int64_t)m * k;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = t / m, i = t - j * m;
+    X[i + j * ldx] = (T)normal_at(seed, (uint64_t)t);
+  }
+}
+
+// --------------------------------------------------------------------------------
+// In-place Cholesky S = L L^T of a k x k matrix held column-major in shared memory
+// (lower triangle used).  All threads of the block take part.  Returns false (in every
+// thread) when a pivot is not positive and finite.
+template <typename T>
+__device__ bool block_cholesky(T* L, int k, int* flag_sh) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (tid == 0) *flag_sh = 0;
+  __syncthreads();
+  for (int t = 0; t < k; ++t) {
+    if (tid == 0) {
+      T d = L[t + t * k];
+      if (!(d > T(0)) || !wfinite(d)) { *flag_sh = 1; d = T(1); }
+      L[t + t * k] = wsqrt(d);
+    }
+    __syncthreads();
+    const T piv = L[t + t * k];
+    for (int i = t + 1 + tid; i < k; i += nt) L[i + t * k] /= piv;
+    __syncthreads();
+    const int w = k - t - 1;
+    for (int e = tid; e < w * w; e += nt) {
+      const int i = t + 1 + e % w, j = t + 1 + e / w;
+      if (i >= j) L[i + j * k] -= L[i + t * k] * L[j + t * k];
+    }
+    __syncthreads();
+  }
+  return *flag_sh == 0;
+}
+
+// One block: R (upper, S = R^T R) and R^{-1} from a reduced k x k Gram S (double).
+template <typename T>
+__global__ void chol_small(const double* __restrict__ S, int k, T* __restrict__ R,
+                           T* __restrict__ Rinv, int* __restrict__ err) {
+  extern __shared__ unsigned char smem_raw[];
+  T* L = reinterpret_cast<T*>(smem_raw);
+  __shared__ int flag;
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+    const int i = e % k, j = e / k;
+    L[e] = i >= j ? (T)S[i + j * k] : T(0);
+  }
+  __syncthreads();
+  const bool ok = block_cholesky(L, k, &flag);
+  if (!ok && threadIdx.x == 0) atomicOr(err, ERRBIT_RANK_DEFICIENT);
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+    const int a = e % k, b = e / k;  // R(a, b) = L(b, a)
+    R[e] = a <= b ? L[b + a * k] : T(0);
+  }
+  // R^{-1}: column c solves R x = e_c by back substitution (R(a,l) = L(l,a)).
+  for (int c = threadIdx.x; c < k; c += blockDim.x) {
+    for (int a = k - 1; a >= 0; --a) {
+      T v = a == c ? T(1) : T(0);
+      for (int l = a + 1; l <= c; ++l) v -= L[l + a * k] * Rinv[l + c * k];
+      Rinv[a + c * k] = a <= c ? v / L[a + a * k] : T(0);
+    }
+  }
+}
+
+// Q1 = X1 R1^{-1} (m x k); R1^{-1} upper triangular.
+template <typename T>
+__global__ void form_q(const T* __restrict__ X1, int64_t ldx, const T* __restrict__ Rinv,
+                       int m, int k, T* __restrict__ Q1) {
+  extern __shared__ unsigned char smem_raw[];
+  T* Ri = reinterpret_cast<T*>(smem_raw);
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) Ri[e] = Rinv[e];
+  __syncthreads();
+  const int64_t total = (int64_t)m * k;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int a = (int)(e / m);
+    const int64_t i = e - (int64_t)a * m;
+    T v = T(0);
+    for (int b = 0; b <= a; ++b) v = fma(X1[i + b * ldx], Ri[b + a * k], v);
+    Q1[i + (int64_t)a * m] = v;
+  }
+}
+
+// Coefficient step.  In every block: R2 = chol(S2) (upper), R = R2 R1.  Thread per
+// column j of A2: B(:,j) = R2^{-T} (Q1^T A2)(:,j), C(:,j) = R^{-1} B(:,j).
+// Writes C (k x n2), B (k x n2), the C^T part of Z2 (row j: Z2[j*NP + a] = C(a,j)),
+// and the block's partial ||B||_F^2.
+template <typename T>
+__global__ void __launch_bounds__(64)
+coef_kernel(const double* __restrict__ S2, const double* __restrict__ QtA2,
+            const T* __restrict__ R1, int k, int n2, int NP, T* __restrict__ Cout,
+            T* __restrict__ Bout, T* __restrict__ Z2, double* __restrict__ bnorm_part,
+            int* __restrict__ err) {
+  extern __shared__ unsigned char smem_raw[];
+  T* L2 = reinterpret_cast<T*>(smem_raw);  // k*k, chol of S2 (lower)
+  T* R = L2 + k * k;                        // k*k, R = R2 R1 (upper)
+  __shared__ int flag;
+  __shared__ double sh[32];
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+    const int i = e % k, j = e / k;
+    L2[e] = i >= j ? (T)S2[i + j * k] : T(0);
+  }
+  __syncthreads();
+  const bool ok = block_cholesky(L2, k, &flag);
+  if (!ok && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(err, ERRBIT_RANK_DEFICIENT);
+  // R(a,c) = sum_{b=a..c} R2(a,b) R1(b,c),  R2(a,b) = L2(b,a)
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+    const int a = e % k, c = e / k;
+    T v = T(0);
+    for (int b = a; b <= c; ++b) v = fma(L2[b + a * k], R1[b + c * k], v);
+    R[e] = a <= c ? v : T(0);
+  }
+  __syncthreads();
+  double bn = 0.0;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n2) {
+    T bv[64];
+    T cv[64];
+    // forward: L2 b = t
+    for (int a = 0; a < k; ++a) {
+      T v = (T)QtA2[a + (int64_t)j * k];
+      for (int l = 0; l < a; ++l) v -= L2[a + l * k] * bv[l];
+      bv[a] = v / L2[a + a * k];
+      bn += (double)bv[a] * (double)bv[a];
+    }
+    // back: R c = b
+    for (int a = k - 1; a >= 0; --a) {
+      T v = bv[a];
+      for (int l = a + 1; l < k; ++l) v -= R[a + l * k] * cv[l];
+      cv[a] = v / R[a + a * k];
+    }
+    for (int a = 0; a < k; ++a) {
+      Cout[a + (int64_t)j * k] = cv[a];
+      Bout[a + (int64_t)j * k] = bv[a];
+      Z2[(int64_t)j * NP + a] = cv[a];
+    }
+  }
+  bn = block_sum_double(bn, sh);
+  if (threadIdx.x == 0) bnorm_part[blockIdx.x] = bn;
+}
+
+// G2 = K - B^T B (n2 x n2): 32x32 tile per block, 256 threads (each 4 entries).
+template <typename T>
+__global__ void __launch_bounds__(256)
+form_g2(const T* __restrict__ K, const T* __restrict__ B, int k, int n2, T* __restrict__ G2) {
+  __shared__ T Bi[64][33];
+  __shared__ T Bj[64][33];
+  const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
+  for (int e = threadIdx.x; e < k * 32; e += blockDim.x) {
+    const int a = e % k, c = e / k;
+    Bi[a][c] = (i0 + c < n2) ? B[a + (int64_t)(i0 + c) * k] : T(0);
+    Bj[a][c] = (j0 + c < n2) ? B[a + (int64_t)(j0 + c) * k] : T(0);
+  }
+  __syncthreads();
+  const int ti = threadIdx.x % 32, tj = threadIdx.x / 32;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int jj = tj + 8 * u;
+    T v = T(0);
+    for (int a = 0; a < k; ++a) v = fma(Bi[a][ti], Bj[a][jj], v);
+    const int i = i0 + ti, j = j0 + jj;
+    if (i < n2 && j < n2) G2[i + (int64_t)j * n2] = K[i + (int64_t)j * n2] - v;
+  }
+}
+
+// --------------------------------------------------------------------------------
+// Subspace iteration, multiply: Z = G2 V (n2 x b), one warp per row of Z (G2 is
+// symmetric, so row j of Z uses the contiguous column j of G2).  Per block partials
+// H = V^T Z and P = Z^T Z over its rows: part[blk][0][b][b], part[blk][1][b][b].
+template <typename T>
+__global__ void __launch_bounds__(256)
+eig_mult(const T* __restrict__ G2, const T* __restrict__ V, int n2, int b, T* __restrict__ Z,
+         T* __restrict__ part) {
+  constexpr int RB = 32;
+  __shared__ T Zs[RB][EIG_BMAX + 1];
+  __shared__ T Vr[RB][EIG_BMAX + 1];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int j0 = blockIdx.x * RB;
+  for (int rr = w; rr < RB; rr += 8) {
+    const int j = j0 + rr;
+    T acc[EIG_BMAX];
+#pragma unroll
+    for (int c = 0; c < EIG_BMAX; ++c) acc[c] = T(0);
+    if (j < n2) {
+      for (int l = lane; l < n2; l += 32) {
+        const T g = G2[l + (int64_t)j * n2];
+#pragma unroll
+        for (int c = 0; c < EIG_BMAX; ++c)
+          if (c < b) acc[c] = fma(g, V[l + (int64_t)c * n2], acc[c]);
+      }
+    }
+    T mine = T(0);
+#pragma unroll
+    for (int c = 0; c < EIG_BMAX; ++c) {
+      if (c < b) {
+        const T sum = warp_sum(acc[c]);
+        if (lane == c) mine = sum;
+      }
+    }
+    if (lane < b) {
+      Zs[rr][lane] = j < n2 ? mine : T(0);
+      Vr[rr][lane] = j < n2 ? V[j + (int64_t)lane * n2] : T(0);
+      if (j < n2) Z[j + (int64_t)lane * n2] = mine;
+    }
+  }
+  __syncthreads();
+  T* out = part + (int64_t)blockIdx.x * 2 * b * b;
+  for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+    const int c1 = e % b, c2 = e / b;
+    T h = T(0), p = T(0);
+    for (int rr = 0; rr < RB; ++rr) {
+      h = fma(Vr[rr][c1], Zs[rr][c2], h);
+      p = fma(Zs[rr][c1], Zs[rr][c2], p);
+    }
+    out[e] = h;
+    out[b * b + e] = p;
+  }
+}
+
+// Subspace iteration, small step (one block of 512 threads, b <= 32):
+//  1. H = V^T G2 V, P = Z^T Z from the partials (double sums).
+//  2. Rayleigh-Ritz: H = Y Theta Y^T by the parallel cyclic Jacobi method (round-robin
+//     ordering, b/2 disjoint rotations per round), sorted descending.
+//  3. Next basis W = [V Y F_v + Z Y F_z], F_z = diag(1/||Z y_c||) for the columns with a
+//     non-negligible Ritz value and F_v = diag(1) for the others (which keeps an
+//     orthonormal Ritz vector where G2 V has no component); W^T W is formed from
+//     I, Y^T P Y and Theta, factored W^T W = L L^T, and Mv = Y F_v L^{-T},
+//     Mz = Y F_z L^{-T}, so that V_next = V Mv + Z Mz has orthonormal columns.
+// Outputs (T, b x b col-major): Y, Mv, Mz; theta (b, descending); resid (b): estimate of
+// ||G2 v_c - theta_c v_c||^2 = (Y^T P Y)_cc - theta_c^2.
+template <typename T>
+__global__ void __launch_bounds__(512)
+eig_small(const T* __restrict__ part, int nblk, int b, int max_sweeps, T* __restrict__ Yout,
+          T* __restrict__ Mv, T* __restrict__ Mz, T* __restrict__ theta,
+          T* __restrict__ resid, int* __restrict__ err) {
+  constexpr int BM = EIG_BMAX;
+  __shared__ T H[BM][BM + 1];
+  __shared__ T P[BM][BM + 1];
+  __shared__ T Y[BM][BM + 1];
+  __shared__ T Wg[BM][BM + 1];
+  __shared__ T cs[BM / 2][2];
+  __shared__ int pairs[BM / 2][2];
+  __shared__ int perm[BM];
+  __shared__ T th[BM];
+  __shared__ int flag;
+  __shared__ double sh[32];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int bb = b * b;
+  for (int e = tid; e < bb; e += nt) {
+    double h = 0.0, p = 0.0;
+    for (int c = 0; c < nblk; ++c) {
+      h += (double)part[(int64_t)c * 2 * bb + e];
+      p += (double)part[(int64_t)c * 2 * bb + bb + e];
+    }
+    const int r = e % b, q = e / b;
+    H[r][q] = (T)h;
+    P[r][q] = (T)p;
+    Y[r][q] = r == q ? T(1) : T(0);
+  }
+  __syncthreads();
+  // symmetrise H
+  for (int e = tid; e < bb; e += nt) {
+    const int r = e % b, q = e / b;
+    if (r < q) {
+      const T v = T(0.5) * (H[r][q] + H[q][r]);
+      H[r][q] = v;
+      H[q][r] = v;
+    }
+  }
+  __syncthreads();
+  // ---- parallel Jacobi
+  const int N = (b + 1) & ~1;  // even number of players (index b is a dummy when b odd)
+  const T eps = sizeof(T) == 4 ? T(1e-7) : T(1e-15);
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    // convergence: off-diagonal mass relative to the total
+    double off = 0.0, tot = 0.0;
+    for (int e = tid; e < bb; e += nt) {
+      const int r = e % b, q = e / b;
+      const double v = (double)H[r][q];
+      tot += v * v;
+      if (r != q) off += v * v;
+    }
+    const double offs = block_sum_double(off, sh);
+    __syncthreads();
+    const double tots = block_sum_double(tot, sh);
+    if (tid == 0) flag = (offs <= (double)eps * (double)eps * tots) ? 1 : 0;
+    __syncthreads();
+    if (flag) break;
+    for (int round = 0; round < N - 1; ++round) {
+      if (tid < N / 2) {
+        // circle method: player N-1 fixed, the others rotate by `round`
+        const int i = tid;
+        int p = (i == 0) ? N - 1 : (round + i) % (N - 1);
+        int q = (round + N - 1 - i) % (N - 1);
+        if (p > q) { const int t = p; p = q; q = t; }
+        pairs[i][0] = p;
+        pairs[i][1] = q;
+        T c = T(1), s = T(0);
+        if (q < b) {
+          const T apq = H[p][q];
+          if (apq != T(0)) {
+            const T tau = (H[q][q] - H[p][p]) / (T(2) * apq);
+            const T t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + wsqrt(T(1) + tau * tau));
+            c = T(1) / wsqrt(T(1) + t * t);
+            s = t * c;
+          }
+        }
+        cs[i][0] = c;
+        cs[i][1] = s;
+      }
+      __syncthreads();
+      // rows: H <- J^T H
+      for (int e = tid; e < (N / 2) * b; e += nt) {
+        const int i = e % (N / 2), l = e / (N / 2);
+        const int p = pairs[i][0], q = pairs[i][1];
+        if (q < b) {
+          const T c = cs[i][0], s = cs[i][1];
+          const T hp = H[p][l], hq = H[q][l];
+          H[p][l] = c * hp - s * hq;
+          H[q][l] = s * hp + c * hq;
+        }
+      }
+      __syncthreads();
+      // columns: H <- H J, Y <- Y J
+      for (int e = tid; e < (N / 2) * b; e += nt) {
+        const int i = e % (N / 2), l = e / (N / 2);
+        const int p = pairs[i][0], q = pairs[i][1];
+        if (q < b) {
+          const T c = cs[i][0], s = cs[i][1];
+          const T hp = H[l][p], hq = H[l][q];
+          H[l][p] = c * hp - s * hq;
+          H[l][q] = s * hp + c * hq;
+          const T yp = Y[l][p], yq = Y[l][q];
+          Y[l][p] = c * yp - s * yq;
+          Y[l][q] = s * yp + c * yq;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // ---- sort descending
+  if (tid == 0) {
+    for (int c = 0; c < b; ++c) perm[c] = c;
+    for (int c = 0; c < b; ++c) {
+      int best = c;
+      for (int d = c + 1; d < b; ++d)
+        if (H[perm[d]][perm[d]] > H[perm[best]][perm[best]]) best = d;
+      const int t = perm[c]; perm[c] = perm[best]; perm[best] = t;
+    }
+    for (int c = 0; c < b; ++c) th[c] = H[perm[c]][perm[c]];
+    flag = 0;
+    for (int c = 0; c < b; ++c)
+      if (!wfinite(th[c])) flag = 1;
+    if (flag) atomicOr(err, ERRBIT_EIG);
+  }
+  __syncthreads();
+  // Wg <- Y permuted (columns sorted)
+  for (int e = tid; e < bb; e += nt) {
+    const int r = e % b, c = e / b;
+    Wg[r][c] = Y[r][perm[c]];
+  }
+  __syncthreads();
+  for (int e = tid; e < bb; e += nt) {
+    const int r = e % b, c = e / b;
+    Y[r][c] = Wg[r][c];
+  }
+  __syncthreads();
+  // H <- P Y   (b x b), then Wg <- Y^T P Y
+  for (int e = tid; e < bb; e += nt) {
+    const int r = e % b, c = e / b;
+    T v = T(0);
+    for (int l = 0; l < b; ++l) v = fma(P[r][l], Y[l][c], v);
+    H[r][c] = v;
+  }
+  __syncthreads();
+  for (int e = tid; e < bb; e += nt) {
+    const int r = e % b, c = e / b;
+    T v = T(0);
+    for (int l = 0; l < b; ++l) v = fma(Y[l][r], H[l][c], v);
+    Wg[r][c] = v;
+  }
+  __syncthreads();
+  // scaling: z-columns for non-negligible Ritz values, v-columns otherwise
+  __shared__ T fz[BM];
+  __shared__ int usev[BM];
+  if (tid < b) {
+    const int c = tid;
+    const T tmax = fabs(th[0]);
+    const T small = sizeof(T) == 4 ? T(1e-6) : T(1e-13);
+    const T nz2 = Wg[c][c];
+    const bool use_v = !(th[c] > small * tmax) || !(nz2 > T(0));
+    usev[c] = use_v ? 1 : 0;
+    fz[c] = use_v ? T(0) : T(1) / wsqrt(nz2);
+    resid[c] = nz2 - th[c] * th[c];
+    theta[c] = th[c];
+  }
+  __syncthreads();
+  // Gram of W into P (overwrite): W_c = v-column (Vy_c) or z-column (Zy_c * fz_c)
+  //   <Vy_a, Vy_b> = delta_ab, <Zy_a, Zy_b> = Wg_ab, <Vy_a, Zy_b> = theta_b delta_ab
+  for (int e = tid; e < bb; e += nt) {
+    const int r = e % b, c = e / b;
+    T g;
+    if (usev[r] && usev[c]) g = r == c ? T(1) : T(0);
+    else if (!usev[r] && !usev[c]) g = fz[r] * fz[c] * Wg[r][c];
+    else if (usev[r]) g = r == c ? th[c] * fz[c] : T(0);
+    else g = r == c ? th[r] * fz[r] : T(0);
+    P[r][c] = g;
+  }
+  __syncthreads();
+  // Cholesky of the Gram (lower, in place, b x b) -- small: one thread column loop
+  if (tid == 0) flag = 0;
+  __syncthreads();
+  for (int t = 0; t < b; ++t) {
+    if (tid == 0) {
+      T d = P[t][t];
+      if (!(d > T(0)) || !wfinite(d)) { flag = 1; d = T(1); }
+      P[t][t] = wsqrt(d);
+    }
+    __syncthreads();
+    for (int i = t + 1 + tid; i < b; i += nt) P[i][t] /= P[t][t];
+    __syncthreads();
+    const int w = b - t - 1;
+    for (int e = tid; e < w * w; e += nt) {
+      const int i = t + 1 + e % w, j = t + 1 + e / w;
+      if (i >= j) P[i][j] -= P[i][t] * P[j][t];
+    }
+    __syncthreads();
+  }
+  if (tid == 0 && flag) atomicOr(err, ERRBIT_EIG);
+  // Linv^T: H <- L^{-T} (upper).  Column c of L^{-T} solves L^T x = e_c.
+  for (int c = tid; c < b; c += nt) {
+    for (int a = b - 1; a >= 0; --a) {
+      T v = a == c ? T(1) : T(0);
+      for (int l = a + 1; l <= c; ++l) v -= P[l][a] * H[l][c];
+      H[a][c] = a <= c ? v / P[a][a] : T(0);
+    }
+  }
+  __syncthreads();
+  // outputs: Y, Mv = Y Fv L^{-T}, Mz = Y Fz L^{-T}
+  for (int e = tid; e < bb; e += nt) {
+    const int r = e % b, c = e / b;
+    T mv = T(0), mz = T(0);
+    for (int l = 0; l <= c; ++l) {
+      const T yl = Y[r][l] * H[l][c];
+      if (usev[l]) mv += yl;
+      else mz += yl * fz[l];
+    }
+    Yout[e] = Y[r][c];
+    Mv[e] = mv;
+    Mz[e] = mz;
+  }
+}
+
+// Subspace iteration, update (rows of V in place): Vs = (V Y)(:, :s) (the Ritz vectors
+// kept for D, also written into the V_s part of Z2) and V <- V Mv + Z Mz.
+template <typename T>
+__global__ void __launch_bounds__(256)
+eig_update(T* __restrict__ V, const T* __restrict__ Z, const T* __restrict__ Y,
+           const T* __restrict__ Mv, const T* __restrict__ Mz, int n2, int b, int s, int k,
+           int NP, T* __restrict__ Vs, T* __restrict__ Z2) {
+  constexpr int RB = 8;
+  __shared__ T Vr[RB][EIG_BMAX];
+  __shared__ T Zr[RB][EIG_BMAX];
+  const int j0 = blockIdx.x * RB;
+  for (int e = threadIdx.x; e < RB * b; e += blockDim.x) {
+    const int rr = e % RB, c = e / RB, j = j0 + rr;
+    Vr[rr][c] = j < n2 ? V[j + (int64_t)c * n2] : T(0);
+    Zr[rr][c] = j < n2 ? Z[j + (int64_t)c * n2] : T(0);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < RB * b; e += blockDim.x) {
+    const int rr = e % RB, c = e / RB, j = j0 + rr;
+    if (j >= n2) continue;
+    T vr = T(0), vn = T(0);
+    for (int l = 0; l < b; ++l) {
+      vr = fma(Vr[rr][l], Y[l + c * b], vr);
+      vn = fma(Vr[rr][l], Mv[l + c * b], vn);
+      vn = fma(Zr[rr][l], Mz[l + c * b], vn);
+    }
+    V[j + (int64_t)c * n2] = vn;
+    if (c < s) {
+      Vs[j + (int64_t)c * n2] = vr;
+      Z2[(int64_t)j * NP + k + c] = vr;
+    }
+  }
+}
+
+// Random start for the subspace basis (orthonormalised by the first eig_small).
+template <typename T>
+__global__ void eig_random_start(T* __restrict__ V, int n2, int b, uint64_t seed) {
+  const int total = n2 * b;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x)
+    V[t] = (T)normal_at(seed ^ 0x5DEECE66Dull, (uint64_t)t);
+}
+
+// Copy the first s Ritz vectors (b >= n2 case, or s = 0 bookkeeping) is done by eig_update.
+
+// G = C C^T (k x k) and CV = C V_s (k x s); block a computes row a.
+template <typename T>
+__global__ void prep_rowpass(const T* __restrict__ C, const T* __restrict__ Vs, int k, int n2,
+                             int s, T* __restrict__ G, T* __restrict__ CV) {
+  const int a = blockIdx.x;
+  for (int t = threadIdx.x; t < k + s; t += blockDim.x) {
+    T v = T(0);
+    if (t < k) {
+      for (int j = 0; j < n2; ++j) v = fma(C[a + (int64_t)j * k], C[t + (int64_t)j * k], v);
+      G[a + t * k] = v;
+    } else {
+      const int c = t - k;
+      for (int j = 0; j < n2; ++j) v = fma(C[a + (int64_t)j * k], Vs[j + (int64_t)c * n2], v);
+      CV[a + c * k] = v;
+    }
+  }
+}
+
+// --------------------------------------------------------------------------------
+// Fused row pass (steps a4 + a5), BM = 64 rows per block, 256 threads.
+//   Y = A2(rows,:) [C^T | V_s]                     (GEMM over n2, Z2 row-major n2 x NP)
+//   U = Y_V - X1old(rows,:) (C V_s)                (= rows of U_s Sigma_s = P_perp A2 V_s)
+//   E = A1 o W1^2 + Y_C - U (C V_s)^T              (= A1 o W1 o W1 + (A2 - D) C^T)
+//   X1new(i,:) solves (diag(W1(i,:)^2) + C C^T) x = E(i,:)^T, one group of KMAX/2 lanes
+//   per row, the k x k matrix held column-wise in registers (each lane owns two
+//   columns), right-looking Cholesky with shuffles, then two triangular solves.
+// Also the block's partial of ||(A1 - X1old) o W1||_F^2.
+constexpr int RP_BM = 64;
+constexpr int RP_BK = 32;
+
+template <typename T>
+struct RowPassSmem {
+  static size_t bytes(int NP, int k, int s) {
+    return sizeof(T) * ((size_t)RP_BK * RP_BM + (size_t)RP_BK * NP + (size_t)RP_BM * (NP + 1) +
+                        (size_t)k * k + (size_t)k * (s > 0 ? s : 1) +
+                        (size_t)RP_BM * (EIG_BMAX + 1));
+  }
+};
+
+template <typename T, int KMAX>
+__global__ void __launch_bounds__(256)
+row_pass(const T* __restrict__ A, int64_t lda, const T* __restrict__ W1, int64_t ldw,
+         const T* __restrict__ X1old, const T* __restrict__ Z2, const T* __restrict__ Gm,
+         const T* __restrict__ CV, int m, int n2, int k, int s, int NP, T* __restrict__ X1new,
+         double* __restrict__ wpart, int* __restrict__ err) {
+  extern __shared__ unsigned char smem_raw[];
+  T* As = reinterpret_cast<T*>(smem_raw);   // [RP_BK][RP_BM]
+  T* Zs = As + RP_BK * RP_BM;               // [RP_BK][NP]
+  T* Ys = Zs + RP_BK * NP;                  // [RP_BM][NP+1]
+  T* Gs = Ys + RP_BM * (NP + 1);            // [k][k]
+  T* CVs = Gs + k * k;                      // [k][s]
+  T* Us = CVs + k * (s > 0 ? s : 1);        // [RP_BM][EIG_BMAX+1]
+  __shared__ double sh[32];
+
+  const int tid = threadIdx.x;
+  const int i0 = blockIdx.x * RP_BM;
+  const T* A2 = A + (int64_t)k * lda;
+  const int NPU = NP / 16;
+
+  for (int e = tid; e < k * k; e += 256) Gs[e] = Gm[e];
+  for (int e = tid; e < k * s; e += 256) CVs[e] = CV[e];
+
+  // ---- phase 1: Y = A2 rows * Z2
+  {
+    const int rg = tid % 16, cg = tid / 16;
+    T acc[4][6];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 6; ++v) acc[u][v] = T(0);
+    for (int j0 = 0; j0 < n2; j0 += RP_BK) {
+      __syncthreads();
+      for (int e = tid; e < RP_BK * RP_BM; e += 256) {
+        const int r = e % RP_BM, kk = e / RP_BM;
+        const int i = i0 + r, j = j0 + kk;
+        As[kk * RP_BM + r] = (i < m && j < n2) ? A2[i + (int64_t)j * lda] : T(0);
+      }
+      for (int e = tid; e < RP_BK * NP; e += 256) {
+        const int kk = e / NP, c = e % NP;
+        const int j = j0 + kk;
+        Zs[kk * NP + c] = j < n2 ? Z2[(int64_t)j * NP + c] : T(0);
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int kk = 0; kk < RP_BK; ++kk) {
+        T a[4], z[6];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) a[u] = As[kk * RP_BM + rg + 16 * u];
+#pragma unroll
+        for (int v = 0; v < 6; ++v) z[v] = v < NPU ? Zs[kk * NP + cg + 16 * v] : T(0);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 6; ++v) acc[u][v] = fma(a[u], z[v], acc[u][v]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 6; ++v)
+        if (v < NPU) Ys[(rg + 16 * u) * (NP + 1) + cg + 16 * v] = acc[u][v];
+  }
+  __syncthreads();
+
+  // ---- phase 2a: U = Y_V - X1old C V_s
+  for (int e = tid; e < RP_BM * s; e += 256) {
+    const int r = e % RP_BM, c = e / RP_BM;
+    const int i = i0 + r;
+    T v = Ys[r * (NP + 1) + k + c];
+    if (i < m)
+      for (int a = 0; a < k; ++a) v -= X1old[i + (int64_t)a * m] * CVs[a + c * k];
+    Us[r * (EIG_BMAX + 1) + c] = v;
+  }
+  __syncthreads();
+
+  // ---- phase 2b: E (into Ys[:, :k]) and the weighted objective term
+  double wsum = 0.0;
+  for (int e = tid; e < RP_BM * k; e += 256) {
+    const int r = e % RP_BM, a = e / RP_BM;
+    const int i = i0 + r;
+    if (i >= m) continue;
+    const T w = W1[i + (int64_t)a * ldw];
+    const T a1 = A[i + (int64_t)a * lda];
+    const T xo = X1old[i + (int64_t)a * m];
+    T v = a1 * w * w + Ys[r * (NP + 1) + a];
+    for (int c = 0; c < s; ++c) v -= Us[r * (EIG_BMAX + 1) + c] * CVs[a + c * k];
+    Ys[r * (NP + 1) + a] = v;
+    const double d = ((double)a1 - (double)xo) * (double)w;
+    wsum += d * d;
+  }
+  wsum = block_sum_double(wsum, sh);
+  if (tid == 0) wpart[blockIdx.x] = wsum;
+  __syncthreads();
+
+  // ---- phase 3: row solves
+  constexpr int GS = KMAX / 2;        // lanes per row
+  constexpr int RPW = 32 / GS;        // rows per warp pass
+  const int lane = tid & 31, warp = tid >> 5;
+  const int lg = lane % GS, grp = lane / GS;
+  const unsigned gmask = 0xffffffffu;  // every lane runs the same shuffles (uniform loops)
+  const int j0c = lg, j1c = lg + GS;
+  bool bad = false;
+  for (int rbase = warp * RPW; rbase < RP_BM; rbase += 8 * RPW) {
+    const int r = rbase + grp;
+    const int i = i0 + r;
+    const bool active = i < m;
+    T c0[KMAX], c1[KMAX];
+    T d0 = T(1), d1 = T(1);
+    if (active && j0c < k) { const T w = W1[i + (int64_t)j0c * ldw]; d0 = w * w; }
+    if (active && j1c < k) { const T w = W1[i + (int64_t)j1c * ldw]; d1 = w * w; }
+#pragma unroll
+    for (int q = 0; q < KMAX; ++q) {
+      c0[q] = (q < k && j0c < k) ? Gs[q + j0c * k] + (q == j0c ? d0 : T(0)) : (q == j0c ? T(1) : T(0));
+      c1[q] = (q < k && j1c < k) ? Gs[q + j1c * k] + (q == j1c ? d1 : T(0)) : (q == j1c ? T(1) : T(0));
+    }
+    T e0 = (active && j0c < k) ? Ys[r * (NP + 1) + j0c] : T(0);
+    T e1 = (active && j1c < k) ? Ys[r * (NP + 1) + j1c] : T(0);
+    // Cholesky: after step t, c_j[t] holds L(j,t) (row part, t < j), c_t[t] = L(t,t),
+    // c_t[q] = L(q,t) for q > t (column part).
+#pragma unroll
+    for (int t = 0; t < KMAX; ++t) {
+      if (t < k) {
+        const int own = t % GS;
+        const T pv = (t / GS == 0) ? c0[t] : c1[t];
+        T piv = __shfl_sync(gmask, pv, own, GS);
+        if (!(piv > T(0)) || !wfinite(piv)) { bad = bad || active; piv = T(1); }
+        const T ltt = wsqrt(piv);
+        const T rl = T(1) / ltt;
+        T l0 = c0[t] * rl, l1 = c1[t] * rl;
+        if (j0c > t) c0[t] = l0;
+        if (j1c > t) c1[t] = l1;
+        if (j0c == t) c0[t] = ltt;
+        if (j1c == t) c1[t] = ltt;
+#pragma unroll
+        for (int q = t + 1; q < KMAX; ++q) {
+          if (q < k) {
+            const T lq = __shfl_sync(gmask, (q / GS == 0) ? l0 : l1, q % GS, GS);
+            if (j0c > t) c0[q] -= lq * l0;
+            if (j1c > t) c1[q] -= lq * l1;
+            if (j0c == t) c0[q] = lq;
+            if (j1c == t) c1[q] = lq;
+          }
+        }
+      }
+    }
+    // forward: L y = e  (row j of L is c_j[0..j-1], diagonal c_j[j])
+#pragma unroll
+    for (int t = 0; t < KMAX; ++t) {
+      if (t < k) {
+        const T yv = (t / GS == 0) ? e0 / c0[t] : e1 / c1[t];
+        const T yt = __shfl_sync(gmask, yv, t % GS, GS);
+        if (j0c == t) e0 = yt;
+        if (j1c == t) e1 = yt;
+        if (j0c > t) e0 -= c0[t] * yt;
+        if (j1c > t) e1 -= c1[t] * yt;
+      }
+    }
+    // backward: L^T x = y  (column j of L below the diagonal is c_j[j+1..k-1])
+#pragma unroll
+    for (int t = KMAX - 1; t >= 0; --t) {
+      if (t < k) {
+        const T xv = (t / GS == 0) ? e0 / c0[t] : e1 / c1[t];
+        const T xt = __shfl_sync(gmask, xv, t % GS, GS);
+        if (j0c == t) e0 = xt;
+        if (j1c == t) e1 = xt;
+        if (j0c < t) e0 -= c0[t] * xt;
+        if (j1c < t) e1 -= c1[t] * xt;
+      }
+    }
+    if (active && j0c < k) X1new[i + (int64_t)j0c * m] = e0;
+    if (active && j1c < k) X1new[i + (int64_t)j1c * m] = e1;
+  }
+  if (bad) atomicOr(err, ERRBIT_NOT_SPD);
+}
+
+// F_p = w-term + ||A2||^2 - ||B||^2 - sum_{c<s} theta_c, stored in Fhist[*iter], then
+// (*iter)++.  One thread block.
+template <typename T>
+__global__ void finalize_objective(const double* __restrict__ wpart, int nw,
+                                   const double* __restrict__ bpart, int nb,
+                                   const double* __restrict__ normA2, const T* __restrict__ theta,
+                                   int s, double* __restrict__ Fhist, int hist_cap,
+                                   int* __restrict__ iter, double* __restrict__ Fcur) {
+  __shared__ double sh[32];
+  double w = 0.0, bn = 0.0;
+  for (int e = threadIdx.x; e < nw; e += blockDim.x) w += wpart[e];
+  for (int e = threadIdx.x; e < nb; e += blockDim.x) bn += bpart[e];
+  w = block_sum_double(w, sh);
+  __syncthreads();
+  bn = block_sum_double(bn, sh);
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int c = 0; c < s; ++c) t += (double)theta[c];
+    const double F = w + (*normA2 - bn - t);
+    const int p = *iter;
+    if (p < hist_cap) Fhist[p] = F;
+    *Fcur = F;
+    *iter = p + 1;
+  }
+}
+
+// --------------------------------------------------------------------------------
+// X2 pass (exact evaluation).  For the current factors (X1, Z2 = [C^T | V_s], CV) and,
+// optionally, a previous set (X1p, Z2p, CVp), per block of 64 rows:
+//   u = A2 V_s - X1 (C V_s),  X2 = X1 C + u V_s^T   (= X1 C + D)
+//   acc[0] += ||A2 - X2||^2, acc[1] += ||X2 - X2p||^2, acc[2] += ||X2p||^2,
+//   acc[3] += ||X1 - X1p||^2, acc[4] += ||X1p||^2, acc[5] += ||(A1 - X1) o W1||^2
+// and writes X2 (m x n2, ldo) when out != nullptr.  Partials: part[blk*8 + q] (double).
+template <typename T>
+__device__ void x2_rows_uv(const T* __restrict__ A2, int64_t lda, const T* __restrict__ X1,
+                           const T* __restrict__ Z2, const T* __restrict__ CV, int m, int n2,
+                           int k, int s, int NP, int i0, T* As, T* Zs, T* Ws) {
+  // Ws[r][0..k) = X1 rows, Ws[r][k..k+s) = u rows.  Uses As/Zs as GEMM staging.
+  const int tid = threadIdx.x;
+  // GEMM for y_V = A2 rows * V_s (columns k..k+s of Z2)
+  T acc[8];
+  const int r = tid % RP_BM, cg = tid / RP_BM;  // 4 column groups
+#pragma unroll
+  for (int v = 0; v < 8; ++v) acc[v] = T(0);
+  for (int j0 = 0; j0 < n2 && s > 0; j0 += RP_BK) {
+    __syncthreads();
+    for (int e = tid; e < RP_BK * RP_BM; e += 256) {
+      const int rr = e % RP_BM, kk = e / RP_BM;
+      const int i = i0 + rr, j = j0 + kk;
+      As[kk * RP_BM + rr] = (i < m && j < n2) ? A2[i + (int64_t)j * lda] : T(0);
+    }
+    for (int e = tid; e < RP_BK * EIG_BMAX; e += 256) {
+      const int kk = e / EIG_BMAX, c = e % EIG_BMAX;
+      const int j = j0 + kk;
+      Zs[kk * EIG_BMAX + c] = (j < n2 && c < s) ? Z2[(int64_t)j * NP + k + c] : T(0);
+    }
+    __syncthreads();
+    for (int kk = 0; kk < RP_BK; ++kk) {
+      const T a = As[kk * RP_BM + r];
+#pragma unroll
+      for (int v = 0; v < 8; ++v) acc[v] = fma(a, Zs[kk * EIG_BMAX + cg + 4 * v], acc[v]);
+    }
+  }
+  __syncthreads();
+  const int i = i0 + r;
+#pragma unroll
+  for (int v = 0; v < 8; ++v) {
+    const int c = cg + 4 * v;
+    if (c < s) {
+      T u = acc[v];
+      if (i < m)
+        for (int a = 0; a < k; ++a) u -= X1[i + (int64_t)a * m] * CV[a + c * k];
+      Ws[r * (NP + 1) + k + c] = u;
+    }
+  }
+  for (int e = tid; e < RP_BM * k; e += 256) {
+    const int rr = e % RP_BM, a = e / RP_BM;
+    const int ii = i0 + rr;
+    Ws[rr * (NP + 1) + a] = ii < m ? X1[ii + (int64_t)a * m] : T(0);
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+x2_pass(const T* __restrict__ A, int64_t lda, const T* __restrict__ W1, int64_t ldw,
+        const T* __restrict__ X1, const T* __restrict__ Z2, const T* __restrict__ CV,
+        const T* __restrict__ X1p, const T* __restrict__ Z2p, const T* __restrict__ CVp,
+        int m, int n2, int k, int s, int NP, T* __restrict__ out, int64_t ldo,
+        double* __restrict__ part) {
+  extern __shared__ unsigned char smem_raw[];
+  T* As = reinterpret_cast<T*>(smem_raw);          // [RP_BK][RP_BM]
+  T* Zs = As + RP_BK * RP_BM;                      // [RP_BK][max(NP, EIG_BMAX)]
+  const int ZW = NP > EIG_BMAX ? NP : EIG_BMAX;
+  T* Ws = Zs + RP_BK * ZW;                         // [RP_BM][NP+1]
+  T* Wp = Ws + RP_BM * (NP + 1);                   // [RP_BM][NP+1]
+  __shared__ double sh[32];
+  const int tid = threadIdx.x;
+  const int i0 = blockIdx.x * RP_BM;
+  const T* A2 = A + (int64_t)k * lda;
+  const bool prev = X1p != nullptr;
+  x2_rows_uv(A2, lda, X1, Z2, CV, m, n2, k, s, NP, i0, As, Zs, Ws);
+  if (prev) x2_rows_uv(A2, lda, X1p, Z2p, CVp, m, n2, k, s, NP, i0, As, Zs, Wp);
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  const int ks = k + s;
+  for (int j0 = 0; j0 < n2; j0 += RP_BK) {
+    __syncthreads();
+    // Zs[jj][e] = Z2[(j0+jj)*NP + e] for e < ks
+    for (int e = tid; e < RP_BK * ks; e += 256) {
+      const int jj = e / ks, c = e % ks;
+      const int j = j0 + jj;
+      Zs[jj * ZW + c] = j < n2 ? Z2[(int64_t)j * NP + c] : T(0);
+    }
+    __syncthreads();
+    // each thread: row r = tid % 64, columns jj = tid/64 + 4q
+    const int r = tid % RP_BM, i = i0 + r;
+    T x2v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int jj = tid / RP_BM + 4 * q;
+      T v = T(0);
+      for (int c = 0; c < ks; ++c) v = fma(Ws[r * (NP + 1) + c], Zs[jj * ZW + c], v);
+      x2v[q] = v;
+    }
+    if (prev) {
+      __syncthreads();
+      for (int e = tid; e < RP_BK * ks; e += 256) {
+        const int jj = e / ks, c = e % ks;
+        const int j = j0 + jj;
+        Zs[jj * ZW + c] = j < n2 ? Z2p[(int64_t)j * NP + c] : T(0);
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int jj = tid / RP_BM + 4 * q;
+      const int j = j0 + jj;
+      if (i < m && j < n2) {
+        const double a2 = (double)A2[i + (int64_t)j * lda];
+        const double d = a2 - (double)x2v[q];
+        acc[0] += d * d;
+        if (out) out[i + (int64_t)j * ldo] = x2v[q];
+        if (prev) {
+          T v = T(0);
+          for (int c = 0; c < ks; ++c) v = fma(Wp[r * (NP + 1) + c], Zs[jj * ZW + c], v);
+          const double dd = (double)x2v[q] - (double)v;
+          acc[1] += dd * dd;
+          acc[2] += (double)v * (double)v;
+        }
+      }
+    }
+  }
+  for (int e = tid; e < RP_BM * k; e += 256) {
+    const int r = e % RP_BM, a = e / RP_BM;
+    const int i = i0 + r;
+    if (i >= m) continue;
+    const double x = (double)X1[i + (int64_t)a * m];
+    const double w = (double)W1[i + (int64_t)a * ldw];
+    const double a1 = (double)A[i + (int64_t)a * lda];
+    acc[5] += (a1 - x) * (a1 - x) * w * w;
+    if (prev) {
+      const double xp = (double)X1p[i + (int64_t)a * m];
+      acc[3] += (x - xp) * (x - xp);
+      acc[4] += xp * xp;
+    }
+  }
+  for (int q = 0; q < 6; ++q) {
+    const double v = block_sum_double(acc[q], sh);
+    if (tid == 0) part[(int64_t)blockIdx.x * 8 + q] = v;
+    __syncthreads();
+  }
+}
+
+}  // namespace wlr

@@ -1,0 +1,64 @@
+// Host-side driver of the sWLR iteration: workspace, kernel sequence, CUDA graphs.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/wlr.h"
+
+namespace wlr {
+
+// Status-carrying error for the host driver; converted to wlr_status at the ABI.
+struct Fail {
+  wlr_status st;
+  std::string msg;
+};
+
+#define WLR_CUDA(call)                                                                 \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      throw ::wlr::Fail{e_ == cudaErrorMemoryAllocation ? WLR_ERR_OOM : WLR_ERR_CUDA,  \
+                        std::string(#call) + ": " + cudaGetErrorString(e_)};           \
+  } while (0)
+
+struct Dims {
+  int m, n, k, r, s, n2, b, NP;
+};
+
+struct ProfEntry {
+  std::string name;
+  double ms;
+  int launches;
+};
+
+// Interface shared by the float and double solvers.
+class SolverBase {
+ public:
+  virtual ~SolverBase() {}
+  virtual void set_data(const void* A, int64_t lda, const void* W1, int64_t ldw, wlr_dtype dt,
+                        wlr_memory mem) = 0;
+  virtual void set_init(wlr_init kind, const void* X1_0, int64_t ldx, wlr_dtype dt,
+                        wlr_memory mem, uint64_t seed) = 0;
+  virtual void step(double* F) = 0;
+  virtual wlr_status solve(double tol, int max_iter, int* iters, double* F) = 0;
+  virtual double objective_exact() = 0;
+  virtual void get_result(void* X1, int64_t ldx, void* X2, int64_t ldx2, wlr_dtype dt,
+                          wlr_memory mem) = 0;
+  virtual void get_factors(double* C, double* Vs, double* sigma2) = 0;
+  virtual int get_history(double* F, double* rel_err, int cap) = 0;
+  virtual int iteration() = 0;
+  virtual int64_t launches() const = 0;
+  virtual std::vector<ProfEntry> profile(int reps) = 0;
+};
+
+SolverBase* make_solver_f32(const Dims& d, const wlr_options& o, cudaStream_t user_stream);
+SolverBase* make_solver_f64(const Dims& d, const wlr_options& o, cudaStream_t user_stream);
+
+}  // namespace wlr

@@ -1,0 +1,8 @@
+// float instantiation of the sWLR solver.
+#include "wlr_solver_impl.cuh"
+
+namespace wlr {
+SolverBase* make_solver_f32(const Dims& d, const wlr_options& o, cudaStream_t us) {
+  return new Solver<float>(d, o, us);
+}
+}  // namespace wlr

@@ -1,0 +1,800 @@
+// Solver<T>: the sWLR iteration (Algorithm 1 of Dutta & Li) on one CUDA stream.
+// Included by wlr_solver_f32.cu and wlr_solver_f64.cu, one instantiation each.
+#pragma once
+
+#include <algorithm>
+#include <type_traits>
+
+#include "wlr_kernels.cuh"
+#include "wlr_solver.cuh"
+
+namespace wlr {
+
+template <typename T>
+constexpr wlr_dtype dtype_of() {
+  return std::is_same<T, float>::value ? WLR_F32 : WLR_F64;
+}
+
+static inline int cdiv(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+template <typename T>
+class Solver final : public SolverBase {
+ public:
+  Solver(const Dims& d, const wlr_options& o, cudaStream_t us) : d_(d), o_(o), ustream_(us) {
+    WLR_CUDA(cudaStreamCreateWithFlags(&stream_, cudaStreamNonBlocking));
+    WLR_CUDA(cudaEventCreateWithFlags(&ev_in_, cudaEventDisableTiming));
+    WLR_CUDA(cudaEventCreateWithFlags(&ev_out_, cudaEventDisableTiming));
+    WLR_CUDA(cudaHostAlloc((void**)&hbuf_, 4096, cudaHostAllocDefault));
+    const int m = d_.m, k = d_.k, n2 = d_.n2, s = d_.s, b = d_.b, NP = d_.NP;
+    for (int q = 0; q < 3; ++q) X1buf_[q] = dalloc<T>((size_t)m * k);
+    Q1_ = dalloc<T>((size_t)m * k);
+    // chunking of the split-m Gram products
+    ch_S1_ = chunking(m, 1);
+    ch_T_ = chunking(m, 1 * std::max(1, cdiv(n2, 64)));
+    ch_K_ = chunking(m, (size_t)std::max(1, cdiv(n2, 64)) * std::max(1, cdiv(n2, 64)));
+    const size_t L = (size_t)k * k + (size_t)k * n2;
+    size_t part_elems = std::max((size_t)ch_S1_.nch * k * k, (size_t)ch_T_.nch * L);
+    part_elems = std::max(part_elems, (size_t)ch_K_.nch * n2 * n2);
+    part_ = dalloc<T>(std::max<size_t>(part_elems, 1));
+    S1_ = dalloc<double>((size_t)k * k);
+    S2T_ = dalloc<double>(L);
+    R1_ = dalloc<T>((size_t)k * k);
+    R1inv_ = dalloc<T>((size_t)k * k);
+    C_ = dalloc<T>(std::max<size_t>((size_t)k * n2, 1));
+    B_ = dalloc<T>(std::max<size_t>((size_t)k * n2, 1));
+    Z2_ = dalloc<T>(std::max<size_t>((size_t)n2 * NP, 1));
+    Z2prev_ = dalloc<T>(std::max<size_t>((size_t)n2 * NP, 1));
+    nblk_coef_ = cdiv(n2, 64);
+    bpart_ = dalloc<double>(std::max(nblk_coef_, 1));
+    K_ = dalloc<T>(std::max<size_t>((size_t)n2 * n2, 1));
+    G2_ = dalloc<T>(std::max<size_t>((size_t)n2 * n2, 1));
+    normA2_ = dalloc<double>(1);
+    nblk_eig_ = cdiv(n2, 32);
+    const int bb = std::max(b, 1);
+    V_ = dalloc<T>((size_t)std::max(n2, 1) * bb);
+    Zeig_ = dalloc<T>((size_t)std::max(n2, 1) * bb);
+    eigpart_ = dalloc<T>((size_t)std::max(nblk_eig_, 1) * 2 * bb * bb);
+    Y_ = dalloc<T>((size_t)bb * bb);
+    Mv_ = dalloc<T>((size_t)bb * bb);
+    Mz_ = dalloc<T>((size_t)bb * bb);
+    theta_ = dalloc<T>(bb);
+    resid_ = dalloc<T>(bb);
+    Vs_ = dalloc<T>((size_t)std::max(n2, 1) * std::max(s, 1));
+    G_ = dalloc<T>((size_t)k * k);
+    CV_ = dalloc<T>((size_t)k * std::max(s, 1));
+    CVprev_ = dalloc<T>((size_t)k * std::max(s, 1));
+    nblk_row_ = cdiv(m, RP_BM);
+    wpart_ = dalloc<double>(nblk_row_);
+    x2part_ = dalloc<double>((size_t)nblk_row_ * 8);
+    x2sum_ = dalloc<double>(8);
+    hist_cap_ = 1 << 16;
+    Fhist_ = dalloc<double>(hist_cap_);
+    Fcur_ = dalloc<double>(1);
+    iter_ = dalloc<int>(1);
+    err_ = dalloc<int>(1);
+    WLR_CUDA(cudaMemsetAsync(Z2_, 0, sizeof(T) * std::max<size_t>((size_t)n2 * NP, 1), stream_));
+    WLR_CUDA(cudaMemsetAsync(Z2prev_, 0, sizeof(T) * std::max<size_t>((size_t)n2 * NP, 1), stream_));
+    WLR_CUDA(cudaMemsetAsync(err_, 0, sizeof(int), stream_));
+    WLR_CUDA(cudaMemsetAsync(iter_, 0, sizeof(int), stream_));
+    WLR_CUDA(cudaMemsetAsync(CV_, 0, sizeof(T) * k * std::max(s, 1), stream_));
+    WLR_CUDA(cudaMemsetAsync(CVprev_, 0, sizeof(T) * k * std::max(s, 1), stream_));
+    WLR_CUDA(cudaMemsetAsync(bpart_, 0, sizeof(double) * std::max(nblk_coef_, 1), stream_));
+    // dynamic shared memory limits
+    set_smem((const void*)row_pass<T, 8>, RowPassSmem<T>::bytes(NP, k, s));
+    set_smem((const void*)row_pass<T, 16>, RowPassSmem<T>::bytes(NP, k, s));
+    set_smem((const void*)row_pass<T, 32>, RowPassSmem<T>::bytes(NP, k, s));
+    set_smem((const void*)row_pass<T, 64>, RowPassSmem<T>::bytes(NP, k, s));
+    set_smem((const void*)x2_pass<T>, x2_smem());
+    set_smem((const void*)coef_kernel<T>, 2 * sizeof(T) * k * k);
+    WLR_CUDA(cudaStreamSynchronize(stream_));
+  }
+
+  ~Solver() override {
+    for (auto& g : graphs_) cudaGraphExecDestroy(g.second);
+    for (auto e : ev_pool_) cudaEventDestroy(e);
+    if (scorer_) delete scorer_;
+    for (void* p : allocs_) cudaFree(p);
+    if (hbuf_) cudaFreeHost(hbuf_);
+    cudaEventDestroy(ev_in_);
+    cudaEventDestroy(ev_out_);
+    cudaStreamDestroy(stream_);
+  }
+
+  // ------------------------------------------------------------------ ABI methods
+  void set_data(const void* A, int64_t lda, const void* W1, int64_t ldw, wlr_dtype dt,
+                wlr_memory mem) override {
+    const int m = d_.m, n = d_.n, k = d_.k;
+    if (!A || !W1) throw Fail{WLR_ERR_INVALID_ARG, "A and W1 must be non-NULL"};
+    if (lda < m || ldw < m) throw Fail{WLR_ERR_INVALID_ARG, "lda and ldw must be >= m"};
+    begin();
+    A_ = adopt_or_copy(A, lda, m, n, dt, mem, &A_own_, &lda_);
+    W1_ = adopt_or_copy(W1, ldw, m, k, dt, mem, &W1_own_, &ldw_);
+    WLR_CUDA(cudaMemsetAsync(err_, 0, sizeof(int), stream_));
+    check_weights<T><<<grid1d((int64_t)m * k), 256, 0, stream_>>>(W1_, ldw_, m, k, err_);
+    count(1);
+    setup();
+    have_data_ = true;
+    cd_valid_ = false;
+    graphs_clear();
+    end();
+    const int e = read_err();
+    if (e & ERRBIT_BAD_WEIGHT) {
+      have_data_ = false;
+      throw Fail{WLR_ERR_NONPOSITIVE_WEIGHT, "W1 has an entry <= 0 or not finite (Theorem 2 needs W1 > 0)"};
+    }
+  }
+
+  void set_init(wlr_init kind, const void* X1_0, int64_t ldx, wlr_dtype dt, wlr_memory mem,
+                uint64_t seed) override {
+    need_data();
+    const int m = d_.m, k = d_.k;
+    begin();
+    T* X = X1buf_[0];
+    if (kind == WLR_INIT_A1) {
+      WLR_CUDA(cudaMemcpy2DAsync(X, sizeof(T) * m, A_, sizeof(T) * lda_, sizeof(T) * m, k,
+                                 cudaMemcpyDeviceToDevice, stream_));
+    } else if (kind == WLR_INIT_RANDOM) {
+      random_normal_fill<T><<<grid1d((int64_t)m * k), 256, 0, stream_>>>(X, m, m, k, seed);
+      count(1);
+    } else if (kind == WLR_INIT_USER) {
+      if (!X1_0) throw Fail{WLR_ERR_INVALID_ARG, "X1_0 must be non-NULL for WLR_INIT_USER"};
+      if (ldx < m) throw Fail{WLR_ERR_INVALID_ARG, "ldx must be >= m"};
+      load_matrix(X, m, X1_0, ldx, m, k, dt, mem);
+    } else {
+      throw Fail{WLR_ERR_INVALID_ARG, "unknown init kind"};
+    }
+    cur_ = 0;
+    prev_ = -1;
+    WLR_CUDA(cudaMemsetAsync(iter_, 0, sizeof(int), stream_));
+    WLR_CUDA(cudaMemsetAsync(err_, 0, sizeof(int), stream_));
+    eig_cold_ = true;
+    cd_valid_ = false;
+    iters_host_ = 0;
+    rel_err_hist_.clear();
+    have_init_ = true;
+    end();
+  }
+
+  void step(double* F) override {
+    need_init();
+    begin();
+    if (!cd_valid_) compute_cd(cur_, false);
+    iterate_once();
+    end();
+    if (F) {
+      WLR_CUDA(cudaMemcpyAsync(hbuf_, Fcur_, sizeof(double), cudaMemcpyDeviceToHost, stream_));
+      WLR_CUDA(cudaStreamSynchronize(stream_));
+      *F = *(double*)hbuf_;
+      raise_err();
+    }
+  }
+
+  wlr_status solve(double tol, int max_iter, int* iters, double* F) override {
+    need_init();
+    if (max_iter < 0) throw Fail{WLR_ERR_INVALID_ARG, "max_iter must be >= 0"};
+    begin();
+    if (!cd_valid_) compute_cd(cur_, false);
+    const int stop = o_.stop;
+    bool converged = false;
+    double Fprev = NAN;
+    int it = 0;
+    for (; it < max_iter; ++it) {
+      iterate_once();
+      if (stop == WLR_STOP_NONE) continue;
+      if (stop == WLR_STOP_OBJECTIVE) {
+        WLR_CUDA(cudaMemcpyAsync(hbuf_, Fcur_, sizeof(double), cudaMemcpyDeviceToHost, stream_));
+        WLR_CUDA(cudaStreamSynchronize(stream_));
+        const double Fp = *(double*)hbuf_;
+        if (std::isfinite(Fprev) && std::fabs(Fprev - Fp) <= tol * std::fabs(Fp)) {
+          converged = true;
+          ++it;
+          break;
+        }
+        Fprev = Fp;
+        continue;
+      }
+      // paper / relative: Error_p = ||X_{p+1} - X_p||_F from the exact X2 pass
+      double e6[6];
+      x2_eval(cur_, prev_, nullptr, 0, e6);
+      const double err = std::sqrt(std::max(0.0, e6[1] + e6[3]));
+      const double nrm = std::sqrt(std::max(0.0, e6[2] + e6[4]));
+      const double rel = nrm > 0 ? err / nrm : INFINITY;
+      rel_err_hist_.push_back(rel);
+      if ((stop == WLR_STOP_PAPER && (err < tol || rel < tol)) || rel < tol) {
+        converged = true;
+        ++it;
+        break;
+      }
+    }
+    end();
+    WLR_CUDA(cudaMemcpyAsync(hbuf_, Fcur_, sizeof(double), cudaMemcpyDeviceToHost, stream_));
+    WLR_CUDA(cudaStreamSynchronize(stream_));
+    if (iters) *iters = it;
+    if (F) *F = *(double*)hbuf_;
+    raise_err();
+    if (stop != WLR_STOP_NONE && !converged) return WLR_ERR_NO_CONVERGENCE;
+    return WLR_OK;
+  }
+
+  double objective_exact() override {
+    need_init();
+    if (std::is_same<T, double>::value) {
+      begin();
+      qr_coef(cur_);
+      if (d_.s > 0) {
+        form_g2_launch();
+        converge_eig();
+      }
+      prep();
+      cd_valid_ = true;
+      double e6[6];
+      x2_eval(cur_, -1, nullptr, 0, e6);
+      end();
+      raise_err();
+      return e6[0] + e6[5];
+    }
+    // FP32 handle: score with an FP64 copy of the problem
+    if (!scorer_) {
+      wlr_options so = o_;
+      so.precision = WLR_PREC_FP64;
+      so.use_graph = 0;
+      so.eig_block = std::min(d_.n2, EIG_BMAX);
+      Dims sd = d_;
+      sd.b = std::max(d_.s, std::min(d_.n2, EIG_BMAX));
+      scorer_ = make_solver_f64(sd, so, stream_);
+      scorer_->set_data(A_, lda_, W1_, ldw_, dtype_of<T>(), WLR_MEM_DEVICE);
+    }
+    // the scorer's stream waits on this stream, so the current X1 is complete
+    scorer_->set_init(WLR_INIT_USER, X1buf_[cur_], d_.m, dtype_of<T>(), WLR_MEM_DEVICE, 0);
+    return scorer_->objective_exact();
+  }
+
+  void get_result(void* X1, int64_t ldx, void* X2, int64_t ldx2, wlr_dtype dt,
+                  wlr_memory mem) override {
+    need_init();
+    const int m = d_.m, k = d_.k, n2 = d_.n2;
+    if (X1 && ldx < m) throw Fail{WLR_ERR_INVALID_ARG, "ldx must be >= m"};
+    if (X2 && ldx2 < m) throw Fail{WLR_ERR_INVALID_ARG, "ldx2 must be >= m"};
+    begin();
+    if (!cd_valid_) compute_cd(cur_, false);
+    if (X1) store_matrix(X1, ldx, X1buf_[cur_], m, m, k, dt, mem);
+    if (X2 && n2 > 0) {
+      const bool direct = (mem == WLR_MEM_DEVICE && dt == dtype_of<T>());
+      T* out = direct ? (T*)X2 : scratch_out((size_t)m * n2);
+      const int64_t ldo = direct ? ldx2 : m;
+      double e6[6];
+      x2_eval(cur_, -1, out, ldo, e6);
+      if (!direct) store_matrix(X2, ldx2, out, m, m, n2, dt, mem);
+    }
+    end();
+    if (mem == WLR_MEM_HOST) WLR_CUDA(cudaStreamSynchronize(stream_));
+    raise_err_async();
+  }
+
+  void get_factors(double* C, double* Vs, double* sigma2) override {
+    need_init();
+    const int k = d_.k, n2 = d_.n2, s = d_.s;
+    begin();
+    if (!cd_valid_) compute_cd(cur_, false);
+    end();
+    WLR_CUDA(cudaStreamSynchronize(stream_));
+    if (C && k * n2 > 0) copy_to_host_double(C, C_, (size_t)k * n2);
+    if (Vs && n2 * s > 0) copy_to_host_double(Vs, Vs_, (size_t)n2 * s);
+    if (sigma2 && s > 0) copy_to_host_double(sigma2, theta_, (size_t)s);
+    raise_err();
+  }
+
+  int get_history(double* F, double* rel_err, int cap) override {
+    WLR_CUDA(cudaStreamSynchronize(stream_));
+    int p = 0;
+    WLR_CUDA(cudaMemcpy(&p, iter_, sizeof(int), cudaMemcpyDeviceToHost));
+    const int n = std::min(p, hist_cap_);
+    if (F && cap > 0) WLR_CUDA(cudaMemcpy(F, Fhist_, sizeof(double) * std::min(n, cap), cudaMemcpyDeviceToHost));
+    if (rel_err) {
+      for (int q = 0; q < std::min(n, cap); ++q)
+        rel_err[q] = q < (int)rel_err_hist_.size() ? rel_err_hist_[q] : NAN;
+    }
+    return n;
+  }
+
+  int iteration() override {
+    WLR_CUDA(cudaStreamSynchronize(stream_));
+    int p = 0;
+    WLR_CUDA(cudaMemcpy(&p, iter_, sizeof(int), cudaMemcpyDeviceToHost));
+    return p;
+  }
+
+  int64_t launches() const override { return launches_; }
+
+  // Run reps iterations without graphs, each kernel bracketed by CUDA events on the
+  // solver's stream; per kernel name: total milliseconds and launch count.
+  std::vector<ProfEntry> profile(int reps) override {
+    need_init();
+    begin();
+    if (!cd_valid_) compute_cd(cur_, false);
+    WLR_CUDA(cudaStreamSynchronize(stream_));
+    prof_ = true;
+    prof_recs_.clear();
+    ev_used_ = 0;
+    const int saved_graph = o_.use_graph;
+    o_.use_graph = 0;
+    try {
+      for (int q = 0; q < reps; ++q) iterate_once();
+    } catch (...) {
+      prof_ = false;
+      o_.use_graph = saved_graph;
+      throw;
+    }
+    prof_ = false;
+    o_.use_graph = saved_graph;
+    end();
+    WLR_CUDA(cudaStreamSynchronize(stream_));
+    std::vector<ProfEntry> out;
+    for (auto& r : prof_recs_) {
+      float ms = 0.f;
+      WLR_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
+      auto it = std::find_if(out.begin(), out.end(), [&](const ProfEntry& e) { return e.name == r.name; });
+      if (it == out.end()) out.push_back(ProfEntry{r.name, (double)ms, 1});
+      else { it->ms += ms; it->launches += 1; }
+    }
+    raise_err();
+    return out;
+  }
+
+ private:
+  struct Chunk {
+    int nch, rows;
+  };
+
+  // ------------------------------------------------------------------ plumbing
+  template <typename U>
+  U* dalloc(size_t n) {
+    void* p = nullptr;
+    WLR_CUDA(cudaMalloc(&p, sizeof(U) * std::max<size_t>(n, 1)));
+    allocs_.push_back(p);
+    return (U*)p;
+  }
+  static void set_smem(const void* fn, size_t bytes) {
+    if (bytes > 48 * 1024)
+      WLR_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  }
+  static Chunk chunking(int m, size_t tiles) {
+    const int target = 304;
+    int nch = std::max<int>(1, (int)((target + tiles - 1) / std::max<size_t>(tiles, 1)));
+    int rows = cdiv(m, nch);
+    rows = std::max(32, ((rows + 31) / 32) * 32);
+    nch = std::max(1, cdiv(m, rows));
+    return {nch, rows};
+  }
+  static int grid1d(int64_t total) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 152 * 16));
+  }
+  void count(int n) { launches_ += n; }
+  cudaEvent_t next_event() {
+    if (ev_used_ == ev_pool_.size()) {
+      cudaEvent_t e;
+      WLR_CUDA(cudaEventCreate(&e));
+      ev_pool_.push_back(e);
+    }
+    return ev_pool_[ev_used_++];
+  }
+  // Brackets the launches of its lifetime with events when profiling.
+  struct Prof {
+    Solver* s;
+    const char* name;
+    cudaEvent_t a = nullptr;
+    Prof(Solver* sv, const char* nm) : s(sv), name(nm) {
+      if (s->prof_) {
+        a = s->next_event();
+        cudaEventRecord(a, s->stream_);
+      }
+    }
+    ~Prof() {
+      if (s->prof_) {
+        cudaEvent_t b = s->next_event();
+        cudaEventRecord(b, s->stream_);
+        s->prof_recs_.push_back({name, a, b});
+      }
+    }
+  };
+  size_t x2_smem() const {
+    const int NP = d_.NP;
+    return sizeof(T) * ((size_t)RP_BK * RP_BM + (size_t)RP_BK * std::max(NP, EIG_BMAX) +
+                        2 * (size_t)RP_BM * (NP + 1));
+  }
+  void begin() {
+    WLR_CUDA(cudaEventRecord(ev_in_, ustream_));
+    WLR_CUDA(cudaStreamWaitEvent(stream_, ev_in_, 0));
+  }
+  void end() {
+    WLR_CUDA(cudaEventRecord(ev_out_, stream_));
+    WLR_CUDA(cudaStreamWaitEvent(ustream_, ev_out_, 0));
+  }
+  void need_data() {
+    if (!have_data_) throw Fail{WLR_ERR_NOT_READY, "call wlr_set_data first"};
+  }
+  void need_init() {
+    need_data();
+    if (!have_init_) throw Fail{WLR_ERR_NOT_READY, "call wlr_set_init first"};
+  }
+  int read_err() {
+    WLR_CUDA(cudaMemcpyAsync(hbuf_ + 64, err_, sizeof(int), cudaMemcpyDeviceToHost, stream_));
+    WLR_CUDA(cudaStreamSynchronize(stream_));
+    return *(int*)(hbuf_ + 64);
+  }
+  void raise_err() {
+    const int e = read_err();
+    // root causes first: a rank-deficient X1 also spoils the row systems downstream
+    if (e & ERRBIT_BAD_WEIGHT) throw Fail{WLR_ERR_NONPOSITIVE_WEIGHT, "W1 has an entry <= 0 or not finite"};
+    if (e & ERRBIT_RANK_DEFICIENT) throw Fail{WLR_ERR_RANK_DEFICIENT, "Cholesky of X1^T X1 broke down: X1 is not of rank k (Eq. 8 assumes rank k)"};
+    if (e & ERRBIT_NOT_SPD) throw Fail{WLR_ERR_NOT_SPD, "a row system diag(W1(i,:)^2) + C C^T was not positive definite"};
+    if (e & ERRBIT_EIG) throw Fail{WLR_ERR_RANK_DEFICIENT, "the subspace basis for the rank-(r-k) SVD step lost rank"};
+  }
+  void raise_err_async() {}
+
+  // A device pointer of type T with leading dimension ld, borrowed when possible.
+  const T* adopt_or_copy(const void* src, int64_t ld, int rows, int cols, wlr_dtype dt,
+                         wlr_memory mem, T** own, int64_t* ld_out) {
+    if (mem == WLR_MEM_DEVICE && dt == dtype_of<T>()) {
+      *ld_out = ld;
+      return (const T*)src;
+    }
+    if (!*own) *own = dalloc<T>((size_t)rows * cols);
+    load_matrix(*own, rows, src, ld, rows, cols, dt, mem);
+    *ld_out = rows;
+    return *own;
+  }
+
+  // dst (device, T, ld_dst) <- src (dt, mem, ld_src)
+  void load_matrix(T* dst, int64_t ld_dst, const void* src, int64_t ld_src, int rows, int cols,
+                   wlr_dtype dt, wlr_memory mem) {
+    const size_t es = dt == WLR_F32 ? 4 : 8;
+    const void* dsrc = src;
+    int64_t ld_dsrc = ld_src;
+    if (mem == WLR_MEM_HOST) {
+      void* stage = staging((size_t)rows * cols * es);
+      WLR_CUDA(cudaMemcpy2DAsync(stage, es * rows, src, es * ld_src, es * rows, cols,
+                                 cudaMemcpyHostToDevice, stream_));
+      dsrc = stage;
+      ld_dsrc = rows;
+    }
+    if (dt == dtype_of<T>()) {
+      WLR_CUDA(cudaMemcpy2DAsync(dst, sizeof(T) * ld_dst, dsrc, sizeof(T) * ld_dsrc,
+                                 sizeof(T) * rows, cols, cudaMemcpyDeviceToDevice, stream_));
+    } else if (dt == WLR_F32) {
+      convert_copy<T, float><<<grid1d((int64_t)rows * cols), 256, 0, stream_>>>(
+          dst, ld_dst, (const float*)dsrc, ld_dsrc, rows, cols);
+      count(1);
+    } else {
+      convert_copy<T, double><<<grid1d((int64_t)rows * cols), 256, 0, stream_>>>(
+          dst, ld_dst, (const double*)dsrc, ld_dsrc, rows, cols);
+      count(1);
+    }
+  }
+
+  // dst (dt, mem, ld_dst) <- src (device, T, ld_src)
+  void store_matrix(void* dst, int64_t ld_dst, const T* src, int64_t ld_src, int rows, int cols,
+                    wlr_dtype dt, wlr_memory mem) {
+    const size_t es = dt == WLR_F32 ? 4 : 8;
+    const void* dsrc = src;
+    int64_t ld_dsrc = ld_src;
+    if (dt != dtype_of<T>()) {
+      void* stage = staging((size_t)rows * cols * es);
+      if (dt == WLR_F32)
+        convert_copy<float, T><<<grid1d((int64_t)rows * cols), 256, 0, stream_>>>(
+            (float*)stage, rows, src, ld_src, rows, cols);
+      else
+        convert_copy<double, T><<<grid1d((int64_t)rows * cols), 256, 0, stream_>>>(
+            (double*)stage, rows, src, ld_src, rows, cols);
+      count(1);
+      dsrc = stage;
+      ld_dsrc = rows;
+    }
+    WLR_CUDA(cudaMemcpy2DAsync(dst, es * ld_dst, dsrc, es * ld_dsrc, es * rows, cols,
+                               mem == WLR_MEM_HOST ? cudaMemcpyDeviceToHost
+                                                   : cudaMemcpyDeviceToDevice,
+                               stream_));
+  }
+
+  void* staging(size_t bytes) {
+    if (bytes > stage_bytes_) {
+      if (stage_) {
+        WLR_CUDA(cudaStreamSynchronize(stream_));
+        cudaFree(stage_);
+        allocs_.erase(std::find(allocs_.begin(), allocs_.end(), stage_));
+      }
+      stage_ = dalloc<unsigned char>(bytes);
+      stage_bytes_ = bytes;
+    }
+    return stage_;
+  }
+  T* scratch_out(size_t n) { return (T*)staging2(n * sizeof(T)); }
+  void* staging2(size_t bytes) {
+    if (bytes > stage2_bytes_) {
+      if (stage2_) {
+        WLR_CUDA(cudaStreamSynchronize(stream_));
+        cudaFree(stage2_);
+        allocs_.erase(std::find(allocs_.begin(), allocs_.end(), stage2_));
+      }
+      stage2_ = dalloc<unsigned char>(bytes);
+      stage2_bytes_ = bytes;
+    }
+    return stage2_;
+  }
+  void copy_to_host_double(double* dst, const T* src, size_t n) {
+    std::vector<T> tmp(n);
+    WLR_CUDA(cudaMemcpy(tmp.data(), src, sizeof(T) * n, cudaMemcpyDeviceToHost));
+    for (size_t q = 0; q < n; ++q) dst[q] = (double)tmp[q];
+  }
+
+  // ------------------------------------------------------------------ kernels
+  void gemm_tn(const T* X, int64_t ldx, const T* Y, int64_t ldy, int P, int Q, T* part,
+               int64_t stride, int64_t offset, const Chunk& ch) {
+    if (P <= 0 || Q <= 0) return;
+    const int m = d_.m;
+    Prof pf(this, "gemm_tn_partial");
+    if (P <= 32 && Q <= 32) {
+      dim3 g(cdiv(P, 32), cdiv(Q, 32), ch.nch);
+      gemm_tn_partial<T, 32, 32><<<g, 64, 0, stream_>>>(X, ldx, Y, ldy, m, P, Q, ch.rows, part, stride, offset);
+    } else if (P <= 32) {
+      dim3 g(cdiv(P, 32), cdiv(Q, 64), ch.nch);
+      gemm_tn_partial<T, 32, 64><<<g, 128, 0, stream_>>>(X, ldx, Y, ldy, m, P, Q, ch.rows, part, stride, offset);
+    } else {
+      dim3 g(cdiv(P, 64), cdiv(Q, 64), ch.nch);
+      gemm_tn_partial<T, 64, 64><<<g, 256, 0, stream_>>>(X, ldx, Y, ldy, m, P, Q, ch.rows, part, stride, offset);
+    }
+    count(1);
+  }
+  void reduce(const T* part, int64_t stride, int nch, int64_t len, double* out64, T* outT) {
+    if (len <= 0) return;
+    Prof pf(this, "reduce_partials");
+    reduce_partials<T><<<grid1d(len), 256, 0, stream_>>>(part, stride, nch, len, out64, outT);
+    count(1);
+  }
+
+  // once per problem (step a0): ||A2||^2 and K = A2^T A2
+  void setup() {
+    const int m = d_.m, k = d_.k, n2 = d_.n2;
+    const T* A2 = A_ + (int64_t)k * lda_;
+    if (n2 == 0) {
+      WLR_CUDA(cudaMemsetAsync(normA2_, 0, sizeof(double), stream_));
+      return;
+    }
+    const int nb = 304;
+    sumsq_partial<T><<<nb, 256, 0, stream_>>>(A2, lda_, m, n2, wpart_scratch(nb));
+    reduce_partials<double><<<1, 32, 0, stream_>>>(wpart_scratch(nb), 1, nb, 1, normA2_, nullptr);
+    count(2);
+    gemm_tn(A2, lda_, A2, lda_, n2, n2, part_, (int64_t)n2 * n2, 0, ch_K_);
+    reduce(part_, (int64_t)n2 * n2, ch_K_.nch, (int64_t)n2 * n2, nullptr, K_);
+  }
+  double* wpart_scratch(int n) {
+    if (!sumsq_part_) sumsq_part_ = dalloc<double>(std::max(n, 304));
+    return sumsq_part_;
+  }
+
+  // steps a1 + a2 for X1 = X1buf_[xi]
+  void qr_coef(int xi) {
+    const int m = d_.m, k = d_.k, n2 = d_.n2, NP = d_.NP;
+    const T* X1 = X1buf_[xi];
+    const T* A2 = A_ + (int64_t)k * lda_;
+    gemm_tn(X1, m, X1, m, k, k, part_, (int64_t)k * k, 0, ch_S1_);
+    reduce(part_, (int64_t)k * k, ch_S1_.nch, (int64_t)k * k, S1_, nullptr);
+    {
+      Prof pf(this, "chol_small");
+      chol_small<T><<<1, 64, sizeof(T) * k * k, stream_>>>(S1_, k, R1_, R1inv_, err_);
+    }
+    {
+      Prof pf(this, "form_q");
+      form_q<T><<<grid1d((int64_t)m * k), 256, sizeof(T) * k * k, stream_>>>(X1, m, R1inv_, m, k, Q1_);
+    }
+    count(2);
+    const int64_t L = (int64_t)k * k + (int64_t)k * n2;
+    gemm_tn(Q1_, m, Q1_, m, k, k, part_, L, 0, ch_T_);
+    gemm_tn(Q1_, m, A2, lda_, k, n2, part_, L, (int64_t)k * k, ch_T_);
+    reduce(part_, L, ch_T_.nch, L, S2T_, nullptr);
+    if (n2 > 0) {
+      Prof pf(this, "coef_kernel");
+      coef_kernel<T><<<nblk_coef_, 64, 2 * sizeof(T) * k * k, stream_>>>(
+          S2T_, S2T_ + (int64_t)k * k, R1_, k, n2, NP, C_, B_, Z2_, bpart_, err_);
+      count(1);
+    }
+  }
+  void form_g2_launch() {
+    const int n2 = d_.n2;
+    dim3 g(cdiv(n2, 32), cdiv(n2, 32));
+    Prof pf(this, "form_g2");
+    form_g2<T><<<g, 256, 0, stream_>>>(K_, B_, d_.k, n2, G2_);
+    count(1);
+  }
+  void eig_iteration() {
+    const int n2 = d_.n2, b = d_.b, s = d_.s;
+    {
+      Prof pf(this, "eig_mult");
+      eig_mult<T><<<nblk_eig_, 256, 0, stream_>>>(G2_, V_, n2, b, Zeig_, eigpart_);
+    }
+    {
+      Prof pf(this, "eig_small");
+      eig_small<T><<<1, 512, 0, stream_>>>(eigpart_, nblk_eig_, b, sizeof(T) == 4 ? 12 : 24, Y_, Mv_, Mz_,
+                                          theta_, resid_, err_);
+    }
+    Prof pf(this, "eig_update");
+    eig_update<T><<<cdiv(n2, 8), 256, 0, stream_>>>(V_, Zeig_, Y_, Mv_, Mz_, n2, b, s, d_.k,
+                                                    d_.NP, Vs_, Z2_);
+    count(3);
+  }
+  void eig_start() {
+    eig_random_start<T><<<grid1d((int64_t)d_.n2 * d_.b), 256, 0, stream_>>>(V_, d_.n2, d_.b, o_.seed);
+    count(1);
+  }
+  void prep() {
+    Prof pf(this, "prep_rowpass");
+    prep_rowpass<T><<<d_.k, 128, 0, stream_>>>(C_, Vs_, d_.k, d_.n2, d_.s, G_, CV_);
+    count(1);
+  }
+  // steps a1..a3 (+ the small products for a4/a5) for X1 = X1buf_[xi]
+  void compute_cd(int xi, bool warm) {
+    qr_coef(xi);
+    if (d_.s > 0) {
+      form_g2_launch();
+      int q = warm ? o_.eig_iters : o_.eig_iters_cold;
+      if (eig_cold_) {
+        eig_start();
+        q = o_.eig_iters_cold;
+        eig_cold_ = false;
+      }
+      for (int t = 0; t < q; ++t) eig_iteration();
+    }
+    prep();
+    cd_valid_ = true;
+  }
+  // iterate the subspace step until the wanted Ritz values settle (FP64 scoring)
+  void converge_eig() {
+    if (eig_cold_) {
+      eig_start();
+      eig_cold_ = false;
+    }
+    const int s = d_.s;
+    std::vector<T> prev(s, (T)0), now(s);
+    for (int round = 0; round < 400; ++round) {
+      for (int t = 0; t < 10; ++t) eig_iteration();
+      WLR_CUDA(cudaMemcpyAsync(hbuf_ + 128, theta_, sizeof(T) * s, cudaMemcpyDeviceToHost, stream_));
+      WLR_CUDA(cudaStreamSynchronize(stream_));
+      std::memcpy(now.data(), hbuf_ + 128, sizeof(T) * s);
+      double diff = 0, top = std::fabs((double)now[0]);
+      for (int c = 0; c < s; ++c) diff = std::max(diff, std::fabs((double)now[c] - (double)prev[c]));
+      prev = now;
+      if (round > 0 && diff <= 1e-15 * std::max(top, 1e-300)) break;
+    }
+  }
+
+  // step a4 + a5 + objective, then a1..a3 for the new X1 (one loop body of Algorithm 1)
+  void iteration_body(int xi, int xo) {
+    const int m = d_.m, k = d_.k, n2 = d_.n2, s = d_.s, NP = d_.NP;
+    const size_t smem = RowPassSmem<T>::bytes(NP, k, s);
+    const int g = nblk_row_;
+    {
+    Prof pf(this, "row_pass");
+    if (k <= 8)
+      row_pass<T, 8><<<g, 256, smem, stream_>>>(A_, lda_, W1_, ldw_, X1buf_[xi], Z2_, G_, CV_, m, n2, k, s, NP, X1buf_[xo], wpart_, err_);
+    else if (k <= 16)
+      row_pass<T, 16><<<g, 256, smem, stream_>>>(A_, lda_, W1_, ldw_, X1buf_[xi], Z2_, G_, CV_, m, n2, k, s, NP, X1buf_[xo], wpart_, err_);
+    else if (k <= 32)
+      row_pass<T, 32><<<g, 256, smem, stream_>>>(A_, lda_, W1_, ldw_, X1buf_[xi], Z2_, G_, CV_, m, n2, k, s, NP, X1buf_[xo], wpart_, err_);
+    else
+      row_pass<T, 64><<<g, 256, smem, stream_>>>(A_, lda_, W1_, ldw_, X1buf_[xi], Z2_, G_, CV_, m, n2, k, s, NP, X1buf_[xo], wpart_, err_);
+    }
+    {
+    Prof pf(this, "finalize_objective");
+    finalize_objective<T><<<1, 256, 0, stream_>>>(wpart_, g, bpart_, n2 > 0 ? nblk_coef_ : 0, normA2_, theta_,
+                                                  s, Fhist_, hist_cap_, iter_, Fcur_);
+    }
+    count(2);
+    // keep the factors of X1_p for Error_p
+    if (n2 > 0)
+      WLR_CUDA(cudaMemcpyAsync(Z2prev_, Z2_, sizeof(T) * (size_t)n2 * NP, cudaMemcpyDeviceToDevice, stream_));
+    if (s > 0)
+      WLR_CUDA(cudaMemcpyAsync(CVprev_, CV_, sizeof(T) * (size_t)k * s, cudaMemcpyDeviceToDevice, stream_));
+    compute_cd(xo, true);
+  }
+
+  void iterate_once() {
+    const int xi = cur_, xo = (cur_ + 1) % 3;
+    if (o_.use_graph && !eig_cold_) {
+      auto it = graphs_.find(xi);
+      if (it == graphs_.end()) {
+        cudaGraph_t graph;
+        const int64_t before = launches_;
+        WLR_CUDA(cudaStreamBeginCapture(stream_, cudaStreamCaptureModeThreadLocal));
+        try {
+          iteration_body(xi, xo);
+        } catch (...) {
+          cudaStreamEndCapture(stream_, &graph);
+          throw;
+        }
+        WLR_CUDA(cudaStreamEndCapture(stream_, &graph));
+        cudaGraphExec_t exec;
+        WLR_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+        cudaGraphDestroy(graph);
+        graph_launch_count_ = launches_ - before;
+        launches_ = before;
+        it = graphs_.emplace(xi, exec).first;
+      }
+      WLR_CUDA(cudaGraphLaunch(it->second, stream_));
+      launches_ += graph_launch_count_;
+    } else {
+      iteration_body(xi, xo);
+    }
+    prev_ = xi;
+    cur_ = xo;
+    ++iters_host_;
+  }
+  void graphs_clear() {
+    for (auto& g : graphs_) cudaGraphExecDestroy(g.second);
+    graphs_.clear();
+  }
+
+  // exact evaluation of the current (and previous) iterate; result sums in e6
+  void x2_eval(int xi, int xp, T* out, int64_t ldo, double* e6) {
+    const int m = d_.m, k = d_.k, n2 = d_.n2, s = d_.s, NP = d_.NP;
+    const T* X1p = xp >= 0 ? X1buf_[xp] : nullptr;
+    x2_pass<T><<<nblk_row_, 256, x2_smem(), stream_>>>(A_, lda_, W1_, ldw_, X1buf_[xi], Z2_, CV_, X1p,
+                                                      X1p ? Z2prev_ : nullptr, X1p ? CVprev_ : nullptr,
+                                                      m, n2, k, s, NP, out, ldo, x2part_);
+    reduce_partials<double><<<1, 32, 0, stream_>>>(x2part_, 8, nblk_row_, 6, x2sum_, nullptr);
+    count(2);
+    WLR_CUDA(cudaMemcpyAsync(hbuf_ + 256, x2sum_, sizeof(double) * 6, cudaMemcpyDeviceToHost, stream_));
+    WLR_CUDA(cudaStreamSynchronize(stream_));
+    std::memcpy(e6, hbuf_ + 256, sizeof(double) * 6);
+  }
+
+  // ------------------------------------------------------------------ state
+  Dims d_;
+  wlr_options o_;
+  cudaStream_t ustream_ = nullptr, stream_ = nullptr;
+  cudaEvent_t ev_in_ = nullptr, ev_out_ = nullptr;
+  unsigned char* hbuf_ = nullptr;
+  std::vector<void*> allocs_;
+  int64_t launches_ = 0, graph_launch_count_ = 0;
+
+  const T* A_ = nullptr;
+  int64_t lda_ = 0;
+  T* A_own_ = nullptr;
+  const T* W1_ = nullptr;
+  int64_t ldw_ = 0;
+  T* W1_own_ = nullptr;
+  bool have_data_ = false, have_init_ = false, cd_valid_ = false, eig_cold_ = true;
+  int cur_ = 0, prev_ = -1, iters_host_ = 0;
+  std::vector<double> rel_err_hist_;
+
+  T* X1buf_[3] = {nullptr, nullptr, nullptr};
+  T *Q1_ = nullptr, *part_ = nullptr, *R1_ = nullptr, *R1inv_ = nullptr;
+  double *S1_ = nullptr, *S2T_ = nullptr;
+  T *C_ = nullptr, *B_ = nullptr, *Z2_ = nullptr, *Z2prev_ = nullptr;
+  double* bpart_ = nullptr;
+  T *K_ = nullptr, *G2_ = nullptr;
+  double* normA2_ = nullptr;
+  T *V_ = nullptr, *Zeig_ = nullptr, *eigpart_ = nullptr, *Y_ = nullptr, *Mv_ = nullptr, *Mz_ = nullptr;
+  T *theta_ = nullptr, *resid_ = nullptr, *Vs_ = nullptr;
+  T *G_ = nullptr, *CV_ = nullptr, *CVprev_ = nullptr;
+  double *wpart_ = nullptr, *x2part_ = nullptr, *x2sum_ = nullptr, *Fhist_ = nullptr, *Fcur_ = nullptr;
+  double* sumsq_part_ = nullptr;
+  int *iter_ = nullptr, *err_ = nullptr;
+  int hist_cap_ = 0, nblk_coef_ = 0, nblk_eig_ = 0, nblk_row_ = 0;
+  Chunk ch_S1_{1, 32}, ch_T_{1, 32}, ch_K_{1, 32};
+  void* stage_ = nullptr;
+  size_t stage_bytes_ = 0;
+  void* stage2_ = nullptr;
+  size_t stage2_bytes_ = 0;
+  std::map<int, cudaGraphExec_t> graphs_;
+  SolverBase* scorer_ = nullptr;
+  struct ProfRec {
+    const char* name;
+    cudaEvent_t a, b;
+  };
+  bool prof_ = false;
+  std::vector<ProfRec> prof_recs_;
+  std::vector<cudaEvent_t> ev_pool_;
+  size_t ev_used_ = 0;
+};
+
+}  // namespace wlr

@@ -1,0 +1,342 @@
+"""Thin ctypes binding of libwlr.so (the C ABI in include/wlr.h).
+
+Argument marshalling only: every step of the sWLR iteration runs in the library's
+CUDA kernels.  Functions keep the C names (wlr_create, wlr_set_data, ...).  Matrix
+arguments may be torch tensors (device or host) or NumPy arrays (host); they must be
+column-major (Fortran order; a torch tensor ``t`` qualifies when ``t.T`` is
+contiguous) or have column stride 1 with a leading dimension.
+
+There is no fallback: if the shared library is missing or fails to load, importing
+this module raises, so nothing silently runs elsewhere.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libwlr.so")
+
+WLR_OK = 0
+WLR_ERR_INVALID_ARG = 1
+WLR_ERR_NONPOSITIVE_WEIGHT = 2
+WLR_ERR_RANK_DEFICIENT = 3
+WLR_ERR_NOT_SPD = 4
+WLR_ERR_NO_CONVERGENCE = 5
+WLR_ERR_DEVICE_TIMEOUT = 6
+WLR_ERR_CUDA = 7
+WLR_ERR_OOM = 8
+WLR_ERR_NOT_READY = 9
+WLR_ERR_UNSUPPORTED = 10
+
+WLR_F32, WLR_F64 = 0, 1
+WLR_MEM_DEVICE, WLR_MEM_HOST = 0, 1
+WLR_PREC_FP64, WLR_PREC_FP32 = 0, 1
+WLR_INIT_A1, WLR_INIT_RANDOM, WLR_INIT_USER = 0, 1, 2
+WLR_STOP_PAPER, WLR_STOP_RELATIVE, WLR_STOP_NONE, WLR_STOP_OBJECTIVE = 0, 1, 2, 3
+
+
+class wlr_options(ct.Structure):
+    _fields_ = [
+        ("precision", ct.c_int32),
+        ("stop", ct.c_int32),
+        ("eig_block", ct.c_int32),
+        ("eig_iters", ct.c_int32),
+        ("eig_iters_cold", ct.c_int32),
+        ("use_graph", ct.c_int32),
+        ("seed", ct.c_uint64),
+    ]
+
+
+class WlrError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{status_string(status)}: {message}")
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"libwlr.so not built at {_LIB_PATH}; run __graft_entry__.build()")
+    lib = ct.CDLL(_LIB_PATH)
+    H = ct.c_void_p
+    P = ct.c_void_p
+    i64, i32, u64, dbl = ct.c_int64, ct.c_int32, ct.c_uint64, ct.c_double
+    sig = {
+        "wlr_default_options": (None, [ct.POINTER(wlr_options)]),
+        "wlr_create": (i32, [ct.POINTER(H), i64, i64, i64, i64, ct.POINTER(wlr_options), P]),
+        "wlr_set_data": (i32, [H, P, i64, P, i64, i32, i32]),
+        "wlr_set_init": (i32, [H, i32, P, i64, i32, i32, u64]),
+        "wlr_step": (i32, [H, ct.POINTER(dbl)]),
+        "wlr_solve": (i32, [H, dbl, i32, ct.POINTER(i32), ct.POINTER(dbl)]),
+        "wlr_objective": (i32, [H, ct.POINTER(dbl)]),
+        "wlr_get_result": (i32, [H, P, i64, P, i64, i32, i32]),
+        "wlr_get_factors": (i32, [H, P, P, P]),
+        "wlr_get_history": (i32, [H, P, P, i32, ct.POINTER(i32)]),
+        "wlr_get_iteration": (i32, [H, ct.POINTER(i32)]),
+        "wlr_destroy": (i32, [H]),
+        "wlr_status_string": (ct.c_char_p, [i32]),
+        "wlr_last_error": (ct.c_char_p, [H]),
+        "wlr_kernel_launches": (i64, [H]),
+        "wlr_profile": (i32, [H, i32, ct.c_char_p, i32, P, P, i32, ct.POINTER(i32)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = _load()
+EXPORTED = (
+    "wlr_default_options", "wlr_create", "wlr_set_data", "wlr_set_init", "wlr_step",
+    "wlr_solve", "wlr_objective", "wlr_get_result", "wlr_get_factors", "wlr_get_history",
+    "wlr_get_iteration", "wlr_destroy", "wlr_status_string", "wlr_last_error",
+    "wlr_kernel_launches", "wlr_profile",
+)
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def status_string(st: int) -> str:
+    return _lib.wlr_status_string(int(st)).decode()
+
+
+def _check(st: int, h=None, ok=(WLR_OK,)):
+    if st not in ok:
+        msg = _lib.wlr_last_error(h).decode() if h is not None else _lib.wlr_last_error(None).decode()
+        raise WlrError(st, msg)
+    return st
+
+
+# ------------------------------------------------------------------ marshalling
+def _matrix(x):
+    """(pointer, leading dimension, dtype code, memory code, keepalive) of a column-major
+    matrix given as a torch tensor or a NumPy array."""
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        torch = None
+    if torch is not None and isinstance(x, torch.Tensor):
+        if x.dtype == torch.float32:
+            dt = WLR_F32
+        elif x.dtype == torch.float64:
+            dt = WLR_F64
+        else:
+            raise TypeError("float32 or float64 tensors only")
+        if x.dim() != 2 or x.stride(0) != 1:
+            raise ValueError("need a 2-D column-major tensor (stride(0) == 1)")
+        ld = max(x.stride(1), x.shape[0]) if x.shape[1] > 1 else x.shape[0]
+        mem = WLR_MEM_DEVICE if x.is_cuda else WLR_MEM_HOST
+        return x.data_ptr(), ld, dt, mem, x
+    a = np.asarray(x)
+    if a.dtype == np.float32:
+        dt = WLR_F32
+    elif a.dtype == np.float64:
+        dt = WLR_F64
+    else:
+        raise TypeError("float32 or float64 arrays only")
+    if a.ndim != 2:
+        raise ValueError("need a 2-D array")
+    if not a.flags.f_contiguous:
+        a = np.asfortranarray(a)
+    return a.ctypes.data, a.shape[0], dt, WLR_MEM_HOST, a
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+# ------------------------------------------------------------------ C names
+def wlr_default_options() -> wlr_options:
+    o = wlr_options()
+    _lib.wlr_default_options(ct.byref(o))
+    return o
+
+
+def wlr_create(m, n, k, r, options: wlr_options | None = None, stream=None):
+    h = ct.c_void_p()
+    st = _lib.wlr_create(ct.byref(h), int(m), int(n), int(k), int(r),
+                         ct.byref(options) if options is not None else None, _stream_ptr(stream))
+    if st != WLR_OK:
+        raise WlrError(st, _lib.wlr_last_error(None).decode())
+    return h
+
+
+def wlr_set_data(h, A, W1):
+    pa, lda, dta, mema, ka = _matrix(A)
+    pw, ldw, dtw, memw, kw = _matrix(W1)
+    if dta != dtw or mema != memw:
+        raise ValueError("A and W1 must share dtype and memory kind")
+    return _check(_lib.wlr_set_data(h, pa, lda, pw, ldw, dta, mema), h)
+
+
+def wlr_set_init(h, kind=WLR_INIT_A1, X1_0=None, seed=0):
+    if X1_0 is None:
+        return _check(_lib.wlr_set_init(h, kind, None, 0, WLR_F64, WLR_MEM_HOST, int(seed)), h)
+    p, ld, dt, mem, keep = _matrix(X1_0)
+    return _check(_lib.wlr_set_init(h, kind, p, ld, dt, mem, int(seed)), h)
+
+
+def wlr_step(h, want_objective=True):
+    F = ct.c_double(np.nan)
+    _check(_lib.wlr_step(h, ct.byref(F) if want_objective else None), h)
+    return F.value if want_objective else None
+
+
+def wlr_solve(h, tol=1e-7, max_iter=100):
+    it = ct.c_int32(0)
+    F = ct.c_double(np.nan)
+    st = _check(_lib.wlr_solve(h, float(tol), int(max_iter), ct.byref(it), ct.byref(F)), h,
+                ok=(WLR_OK, WLR_ERR_NO_CONVERGENCE))
+    return it.value, F.value, st == WLR_OK
+
+
+def wlr_objective(h):
+    F = ct.c_double(np.nan)
+    _check(_lib.wlr_objective(h, ct.byref(F)), h)
+    return F.value
+
+
+def wlr_get_result(h, X1=None, X2=None):
+    """Copy X1 (and X2 = X1 C + D) into caller buffers (torch tensors or NumPy arrays,
+    column-major, float32/float64, same dtype and memory kind)."""
+    p1 = ld1 = 0
+    p2 = ld2 = 0
+    dt = mem = None
+    keep = []
+    if X1 is not None:
+        p1, ld1, dt, mem, k1 = _matrix(X1)
+        keep.append(k1)
+    if X2 is not None:
+        p2, ld2, dt2, mem2, k2 = _matrix(X2)
+        keep.append(k2)
+        if dt is not None and (dt2 != dt or mem2 != mem):
+            raise ValueError("X1 and X2 must share dtype and memory kind")
+        dt, mem = dt2, mem2
+    if dt is None:
+        return
+    if isinstance(X1, np.ndarray) and not X1.flags.f_contiguous:
+        raise ValueError("NumPy outputs must be Fortran-ordered")
+    if isinstance(X2, np.ndarray) and not X2.flags.f_contiguous:
+        raise ValueError("NumPy outputs must be Fortran-ordered")
+    _check(_lib.wlr_get_result(h, p1 or None, ld1, p2 or None, ld2, dt, mem), h)
+
+
+def wlr_get_factors(h, k, n2, s):
+    C = np.zeros((k, n2), order="F")
+    Vs = np.zeros((n2, s), order="F")
+    sig2 = np.zeros(max(s, 0))
+    _check(_lib.wlr_get_factors(h, C.ctypes.data if C.size else None,
+                                Vs.ctypes.data if Vs.size else None,
+                                sig2.ctypes.data if sig2.size else None), h)
+    return C, Vs, sig2
+
+
+def wlr_get_history(h, cap=65536):
+    n = ct.c_int32(0)
+    _check(_lib.wlr_get_history(h, None, None, 0, ct.byref(n)), h)
+    F = np.zeros(max(n.value, 1))
+    E = np.zeros(max(n.value, 1))
+    _check(_lib.wlr_get_history(h, F.ctypes.data, E.ctypes.data, n.value, ct.byref(n)), h)
+    return F[:n.value], E[:n.value]
+
+
+def wlr_get_iteration(h):
+    p = ct.c_int32(0)
+    _check(_lib.wlr_get_iteration(h, ct.byref(p)), h)
+    return p.value
+
+
+def wlr_destroy(h):
+    if h:
+        _lib.wlr_destroy(h)
+
+
+def wlr_status_string(st):
+    return status_string(st)
+
+
+def wlr_last_error(h=None):
+    return _lib.wlr_last_error(h).decode()
+
+
+def wlr_kernel_launches(h):
+    return int(_lib.wlr_kernel_launches(h))
+
+
+def wlr_profile(h, reps=20, max_kernels=64):
+    """{kernel name: (total ms, launches)} over reps further iterations."""
+    buf = ct.create_string_buffer(8192)
+    ms = np.zeros(max_kernels)
+    ln = np.zeros(max_kernels, dtype=np.int32)
+    n = ct.c_int32(0)
+    _check(_lib.wlr_profile(h, int(reps), buf, 8192, ms.ctypes.data, ln.ctypes.data, max_kernels,
+                            ct.byref(n)), h)
+    names = buf.value.decode().split("\n")[:n.value]
+    return {nm: (float(ms[q]), int(ln[q])) for q, nm in enumerate(names)}
+
+
+class Solver:
+    """Convenience owner of one handle (destroyed with the object)."""
+
+    def __init__(self, m, n, k, r, precision=WLR_PREC_FP32, stop=WLR_STOP_RELATIVE,
+                 eig_block=0, eig_iters=0, eig_iters_cold=0, use_graph=1, seed=None, stream=None):
+        o = wlr_default_options()
+        o.precision, o.stop = precision, stop
+        o.eig_block, o.eig_iters, o.eig_iters_cold, o.use_graph = eig_block, eig_iters, eig_iters_cold, use_graph
+        if seed is not None:
+            o.seed = seed
+        self.m, self.n, self.k, self.r = int(m), int(n), int(k), int(r)
+        self.h = wlr_create(m, n, k, r, o, stream)
+
+    def set_data(self, A, W1):
+        self._data = (A, W1)  # borrowed device buffers must outlive the handle's use
+        return wlr_set_data(self.h, A, W1)
+
+    def set_init(self, kind=WLR_INIT_A1, X1_0=None, seed=0):
+        return wlr_set_init(self.h, kind, X1_0, seed)
+
+    def step(self, want_objective=True):
+        return wlr_step(self.h, want_objective)
+
+    def solve(self, tol=1e-7, max_iter=100):
+        return wlr_solve(self.h, tol, max_iter)
+
+    def objective(self):
+        return wlr_objective(self.h)
+
+    def result(self, X1=None, X2=None):
+        return wlr_get_result(self.h, X1, X2)
+
+    def factors(self):
+        return wlr_get_factors(self.h, self.k, self.n - self.k, self.r - self.k)
+
+    def history(self):
+        return wlr_get_history(self.h)
+
+    def iteration(self):
+        return wlr_get_iteration(self.h)
+
+    def launches(self):
+        return wlr_kernel_launches(self.h)
+
+    def profile(self, reps=20):
+        return wlr_profile(self.h, reps)
+
+    def close(self):
+        if getattr(self, "h", None):
+            wlr_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,274 @@
+"""CUDA path against the FP64 oracle, through the C ABI (libwlr.so).
+
+Tolerances:
+  * FP64 path: 1e-10 relative (per result, max-abs error over max-abs value).
+  * FP32 path: objective within 1e-4 relative of the oracle's value for the same X1;
+    per-step X1 within 2e-3 relative (FP32 arithmetic with a cond(X1) ~ 1e2..1e3
+    least-squares step: u * cond ~ 6e-8 * 1e3 * a few).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1703_06303_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def wlr():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    from paper_1703_06303_gb300 import wlr as w
+    return w
+
+
+DEV = "cuda:0"
+
+
+def _dev(a):
+    return torch.from_numpy(np.asfortranarray(a)).to(DEV)
+
+
+def _rel(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def _solver(wlr, spec_or_dims, precision, **kw):
+    m, n, k, r = spec_or_dims
+    return wlr.Solver(m, n, k, r, precision=precision, **kw)
+
+
+def _x1(s, m, k, dtype=np.float64):
+    X = np.zeros((m, k), dtype=dtype, order="F")
+    s.result(X)
+    return X
+
+
+def _problem(seed, m, n, k, r, w=(5.0, 50.0), rank=3):
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((m, rank)) @ rng.standard_normal((rank, n))
+    A += 0.1 * rng.standard_normal((m, n))
+    W1 = rng.uniform(w[0], w[1], size=(m, k))
+    X0 = rng.standard_normal((m, k))
+    return np.asfortranarray(A), np.asfortranarray(W1), np.asfortranarray(X0)
+
+
+# ------------------------------------------------------------------ FP64 parity
+def _fp64_step_parity(wlr, A, W1, X0, r, tol=1e-10):
+    m, n = A.shape
+    k = W1.shape[1]
+    n2 = n - k
+    s = _solver(wlr, (m, n, k, r), wlr.WLR_PREC_FP64, eig_block=min(32, max(n2, 1)),
+                eig_iters_cold=400, eig_iters=400)
+    s.set_data(_dev(A), _dev(W1))
+    s.set_init(wlr.WLR_INIT_USER, X0)
+    F = s.step()
+    X1 = _x1(s, m, k)
+    st = oracle.swlr_step(A, W1, X0, r)
+    assert _rel(X1, st.X1_next) < tol
+    assert abs(F - st.F) <= tol * abs(st.F)
+    s.close()
+
+
+def test_fp64_step_config1(wlr):
+    spec = synth.CONFIGS[1]
+    clip = synth.make_clip(spec)
+    X0 = synth.initial_x1(spec.m, spec.k, 0)
+    _fp64_step_parity(wlr, clip["A"], clip["W1"], X0, spec.r)
+
+
+@pytest.mark.parametrize("dims", [
+    (37, 9, 1, 2),        # k = 1, ragged m, tiny n2
+    (130, 20, 3, 3),      # r = k: D = 0
+    (200, 17, 4, 16),     # s = n2 - 1
+    (301, 40, 9, 14),     # k in the 16-lane path
+    (257, 70, 20, 26),    # k in the 32-lane path
+    (190, 80, 40, 45),    # k in the 64-lane path (two columns per lane)
+    (100, 70, 64, 66),    # k = 64
+])
+def test_fp64_step_ragged(wlr, dims):
+    m, n, k, r = dims
+    A, W1, X0 = _problem(sum(dims), m, n, k, r)
+    _fp64_step_parity(wlr, A, W1, X0, r)
+
+
+def test_fp64_trajectory_config1(wlr):
+    spec = synth.CONFIGS[1]
+    clip = synth.make_clip(spec)
+    A, W1 = clip["A"], clip["W1"]
+    X0 = synth.initial_x1(spec.m, spec.k, 0)
+    iters = 20
+    ref = oracle.swlr(A, W1, spec.r, X0, max_iter=iters, stop="none")
+    s = _solver(wlr, (spec.m, spec.n, spec.k, spec.r), wlr.WLR_PREC_FP64, eig_block=32,
+                eig_iters_cold=400, eig_iters=60, stop=wlr.WLR_STOP_NONE)
+    s.set_data(_dev(A), _dev(W1))
+    s.set_init(wlr.WLR_INIT_USER, X0)
+    it, F, _ = s.solve(0.0, iters)
+    assert it == iters
+    Fh, _ = s.history()
+    assert len(Fh) == iters
+    assert np.allclose(Fh, ref.F[:iters], rtol=1e-9, atol=0)
+    X1 = _x1(s, spec.m, spec.k)
+    assert _rel(X1, ref.X1) < 1e-8
+    # output of Algorithm 1: X2 = X1 C + D recomputed for the final X1
+    X2 = np.zeros((spec.m, spec.n - spec.k), order="F")
+    s.result(None, X2)
+    assert _rel(X2, ref.X2) < 1e-8
+    # exact objective of the final iterate
+    assert abs(s.objective() - ref.F[-1]) <= 1e-9 * ref.F[-1]
+    s.close()
+
+
+def test_fp64_objective_exact(wlr):
+    A, W1, X0 = _problem(5, 150, 30, 4, 7)
+    s = _solver(wlr, (150, 30, 4, 7), wlr.WLR_PREC_FP64)
+    s.set_data(_dev(A), _dev(W1))
+    s.set_init(wlr.WLR_INIT_USER, X0)
+    assert abs(s.objective() - oracle.objective_tilde(A, W1, X0, 7)) <= 1e-10 * oracle.objective_tilde(A, W1, X0, 7)
+    s.close()
+
+
+def test_n_equals_k_gives_A1(wlr):
+    A, W1, X0 = _problem(6, 50, 6, 6, 6)
+    s = _solver(wlr, (50, 6, 6, 6), wlr.WLR_PREC_FP64)
+    s.set_data(_dev(A), _dev(W1))
+    s.set_init(wlr.WLR_INIT_USER, X0)
+    s.step()
+    assert _rel(_x1(s, 50, 6), A) < 1e-13
+    s.close()
+
+
+def test_random_init_matches_counter_generator(wlr):
+    A, W1, _ = _problem(7, 300, 12, 5, 7)
+    for prec, tol in ((wlr.WLR_PREC_FP64, 1e-12), (wlr.WLR_PREC_FP32, 1e-6)):
+        s = _solver(wlr, (300, 12, 5, 7), prec)
+        if prec == wlr.WLR_PREC_FP64:
+            s.set_data(_dev(A), _dev(W1))
+        else:
+            s.set_data(_dev(A.astype(np.float32)), _dev(W1.astype(np.float32)))
+        s.set_init(wlr.WLR_INIT_RANDOM, None, seed=424242)
+        X = _x1(s, 300, 5)
+        assert _rel(X, oracle.random_normal_init(300, 5, 424242)) < tol
+        s.close()
+
+
+# ------------------------------------------------------------------ FP32 parity
+def test_fp32_step_config2_full_size(wlr):
+    """Full-size FP32 step at the 160x120, n=400, k=20, r=25 workload: every entry of
+    X1_{p+1} and F_p against one FP64 oracle step from the same X1_p."""
+    spec = synth.CONFIGS[2]
+    clip = synth.make_clip(spec)
+    A = clip["A"].astype(np.float32).astype(np.float64)
+    W1 = clip["W1"].astype(np.float32).astype(np.float64)
+    # a representative iterate: a few oracle steps from A1
+    X = A[:, :spec.k].copy()
+    for _ in range(2):
+        X = oracle.swlr_step(A, W1, X, spec.r).X1_next
+    X = X.astype(np.float32).astype(np.float64)
+    st = oracle.swlr_step(A, W1, X, spec.r)
+    s = _solver(wlr, (spec.m, spec.n, spec.k, spec.r), wlr.WLR_PREC_FP32, eig_iters_cold=200)
+    s.set_data(_dev(A.astype(np.float32)), _dev(W1.astype(np.float32)))
+    s.set_init(wlr.WLR_INIT_USER, X.astype(np.float32))
+    F = s.step()
+    X1 = _x1(s, spec.m, spec.k)
+    assert abs(F - st.F) <= 1e-4 * st.F
+    assert _rel(X1, st.X1_next) < 2e-3
+    s.close()
+
+
+def test_fp32_solve_objective_config2(wlr):
+    """FP32 solve: the FP64 objective of the GPU's final iterate (library scorer)
+    equals the oracle's objective of that same iterate, and is no worse than the
+    oracle's own trajectory after the same number of iterations (to 1e-4)."""
+    spec = synth.CONFIGS[2]
+    clip = synth.make_clip(spec)
+    A32 = clip["A"].astype(np.float32)
+    W32 = clip["W1"].astype(np.float32)
+    A, W1 = A32.astype(np.float64), W32.astype(np.float64)
+    iters = 8
+    s = _solver(wlr, (spec.m, spec.n, spec.k, spec.r), wlr.WLR_PREC_FP32, stop=wlr.WLR_STOP_NONE,
+                eig_iters=4)
+    s.set_data(_dev(A32), _dev(W32))
+    s.set_init(wlr.WLR_INIT_A1)
+    s.solve(0.0, iters)
+    X1 = _x1(s, spec.m, spec.k)
+    Fgpu = s.objective()
+    Fora = oracle.objective_tilde(A, W1, X1, spec.r)
+    assert abs(Fgpu - Fora) <= 1e-8 * Fora
+    ref = oracle.swlr(A, W1, spec.r, A[:, :spec.k].copy(), max_iter=iters, stop="none")
+    assert Fora <= ref.F[-1] * (1 + 1e-4)
+    s.close()
+
+
+def test_host_memory_path(wlr):
+    A, W1, X0 = _problem(8, 129, 21, 3, 6)
+    s = _solver(wlr, (129, 21, 3, 6), wlr.WLR_PREC_FP64, eig_block=18, eig_iters_cold=300)
+    s.set_data(A, W1)                   # NumPy host arrays: the library copies
+    s.set_init(wlr.WLR_INIT_USER, X0)
+    s.step()
+    X1 = np.zeros((129, 3), order="F")
+    s.result(X1)
+    assert _rel(X1, oracle.swlr_step(A, W1, X0, 6).X1_next) < 1e-10
+    # float32 host input into an FP64 handle is converted
+    s.set_data(A.astype(np.float32), W1.astype(np.float32))
+    s.close()
+
+
+# ------------------------------------------------------------------ failure paths
+def test_nonpositive_weight_rejected(wlr):
+    A, W1, X0 = _problem(9, 64, 10, 2, 4)
+    W1[3, 1] = 0.0
+    s = _solver(wlr, (64, 10, 2, 4), wlr.WLR_PREC_FP64)
+    with pytest.raises(wlr.WlrError) as e:
+        s.set_data(_dev(A), _dev(W1))
+    assert e.value.status == wlr.WLR_ERR_NONPOSITIVE_WEIGHT
+    s.close()
+
+
+def test_call_order(wlr):
+    s = _solver(wlr, (64, 10, 2, 4), wlr.WLR_PREC_FP32)
+    with pytest.raises(wlr.WlrError) as e:
+        s.step()
+    assert e.value.status == wlr.WLR_ERR_NOT_READY
+    s.close()
+
+
+def test_rank_deficient_x1(wlr):
+    A, W1, X0 = _problem(10, 64, 10, 3, 5)
+    X0[:, 2] = X0[:, 0]                  # rank(X1) = 2 < k: Eq. 8 needs rank k
+    s = _solver(wlr, (64, 10, 3, 5), wlr.WLR_PREC_FP64)
+    s.set_data(_dev(A), _dev(W1))
+    s.set_init(wlr.WLR_INIT_USER, X0)
+    with pytest.raises(wlr.WlrError) as e:
+        s.step()
+    assert e.value.status == wlr.WLR_ERR_RANK_DEFICIENT
+    s.close()
+
+
+def test_no_convergence_is_a_warning(wlr):
+    A, W1, X0 = _problem(11, 100, 20, 3, 5)
+    s = _solver(wlr, (100, 20, 3, 5), wlr.WLR_PREC_FP64, stop=wlr.WLR_STOP_RELATIVE)
+    s.set_data(_dev(A), _dev(W1))
+    s.set_init(wlr.WLR_INIT_USER, X0)
+    it, F, ok = s.solve(1e-30, 3)
+    assert it == 3 and not ok and np.isfinite(F)
+    s.close()
+
+
+def test_relative_stop_matches_oracle(wlr):
+    A, W1, X0 = _problem(12, 120, 24, 3, 6)
+    ref = oracle.swlr(A, W1, 6, X0, eps=1e-4, max_iter=200, stop="relative")
+    s = _solver(wlr, (120, 24, 3, 6), wlr.WLR_PREC_FP64, stop=wlr.WLR_STOP_RELATIVE,
+                eig_block=21, eig_iters_cold=300, eig_iters=100)
+    s.set_data(_dev(A), _dev(W1))
+    s.set_init(wlr.WLR_INIT_USER, X0)
+    it, F, ok = s.solve(1e-4, 200)
+    assert ok and it == ref.iters
+    _, E = s.history()
+    assert np.allclose(E[:it], ref.rel_error, rtol=1e-6)
+    s.close()
