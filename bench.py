@@ -1,0 +1,437 @@
+#!/usr/bin/env python
+"""Benchmark of the sWLR iteration (Dutta & Li, Algorithm 1) on GB300.
+
+Metric: time (seconds) until the relative objective (F~(X1_p) - F*) / F* <= 1e-6 on the
+FP32 GPU path, for the 160x120-pixel, 400-frame clip with k = 20 weighted frames and
+rank r = 25 (seeded synthetic video, see paper_1703_06303_gb300/synth.py), X1_0 = A1.
+
+  * F~(X1) = min over C, D of F(X1, C, D), evaluated in FP64 by the library (wlr_objective).
+  * F* = the lowest F~ known for the clip: the F~ of a long FP32 run (and the FP64 oracle's
+    trajectory fixture in tests/golden when present).
+  * p* = the first iteration with rel-obj <= 1e-6 (found before timing by deterministic
+    replays; the FP32 path has fixed-order reductions, so a replay is bit-identical).
+  * One timed step = wlr_set_data (setup: ||A2||^2, K = A2^T A2) + wlr_set_init(A1) +
+    p* iterations, inputs resident in HBM; L2 (129 MB) is flushed with a 512 MB write
+    before every step, outside the step's events.
+  * e2e: the same work through the C ABI with host buffers: pinned A, W1 copied in and
+    X1 copied out inside the timed region.
+
+--impl reference times the FP64 CPU oracle (the test oracle, as it stands) on the host
+cores: each step runs a bounded number of oracle iterations, projected to p* iterations.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-rel-obj 1e-6 (s), FP32 GPU path"
+UNIT = "s"
+TARGET = 1e-6
+GOLDEN = os.path.join(ROOT, "tests", "golden", "config2_trajectory.json")
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--calib-iters", type=int, default=20000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--p-star", type=int, default=0,
+                    help="use this iteration count instead of calibrating it (profiling runs)")
+    return ap.parse_args()
+
+
+def _workload():
+    from paper_1703_06303_gb300 import synth
+    spec = synth.CONFIGS[2]
+    return spec, {"workload": f"sWLR clip {spec.H}x{spec.W} px, n={spec.n} frames, k={spec.k}, r={spec.r}",
+                  "m": spec.m, "n": spec.n, "k": spec.k, "r": spec.r, "init": "X1_0 = A1",
+                  "precision": "fp32 (FP64 block-partial sums and objective)",
+                  "l2": "flushed (512 MB write) before every step",
+                  "data": "synthetic video: rank-5 background, 6% moving squares/discs, noise 0.02, W1~U[5,50]"}
+
+
+def _golden_fstar():
+    try:
+        with open(GOLDEN) as f:
+            g = json.load(f)
+        return min(g["F"]), g
+    except (OSError, ValueError, KeyError):
+        return None, None
+
+
+# --------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------- CPU oracle
+def _oracle_iteration_time(n_iter: int, threads: int):
+    """Seconds per Algorithm-1 iteration of the FP64 oracle on this workload, measured
+    in a fresh process (spawned: no CUDA state) using `threads` BLAS threads."""
+    code = f"""
+import os, sys, time, json
+sys.path.insert(0, {ROOT!r})
+import numpy as np
+import oracle
+from paper_1703_06303_gb300 import synth
+spec = synth.CONFIGS[2]
+clip = synth.make_clip(spec)
+A = clip["A"].astype(np.float32).astype(np.float64)
+W1 = clip["W1"].astype(np.float32).astype(np.float64)
+X = A[:, :spec.k].copy()
+oracle.swlr_step(A, W1, X, spec.r)          # warm-up
+t = time.perf_counter()
+for _ in range({n_iter}):
+    X = oracle.swlr_step(A, W1, X, spec.r).X1_next
+dt = (time.perf_counter() - t) / {n_iter}
+print(json.dumps({{"sec_per_iter": dt}}))
+"""
+    env = dict(os.environ)
+    for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[v] = str(threads)
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                       timeout=1800)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])["sec_per_iter"]
+
+
+def _reference_p_star():
+    Fstar, g = _golden_fstar()
+    if g is None:
+        return None
+    F = g["F"]
+    for p, v in enumerate(F):
+        if (v - Fstar) / Fstar <= TARGET:
+            return p
+    return len(F) - 1
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    spec, cfg = _workload()
+    p_star = _reference_p_star()
+    if p_star is None:
+        print(json.dumps({"impl": "reference", "unavailable": "oracle trajectory fixture missing"}))
+        return 0
+    threads = os.cpu_count() or 1
+    times = []
+    for step in range(a.warmup + a.steps):
+        t = _oracle_iteration_time(2, threads)
+        if step >= a.warmup:
+            times.append(t)
+    sec_iter = statistics.mean(times)
+    value = sec_iter * p_star
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": value * 1e3,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": cfg,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"per step: 2 FP64 oracle iterations of the full clip "
+                                   f"(+1 warm-up), projected to p*={p_star} iterations "
+                                   f"(p* from the oracle trajectory fixture)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# --------------------------------------------------------------------- GPU arm
+def run_ours(a):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import __graft_entry__ as g
+    if rank == 0:
+        g.build()
+    if world > 1:
+        dist.barrier()
+    g.build()
+    from paper_1703_06303_gb300 import synth, wlr
+
+    spec, cfg = _workload()
+    # each rank solves its own clip (independent replicas: no data-path collective)
+    clip = synth.make_clip(spec, seed=spec.seed + 1000 * rank)
+    A32 = np.asfortranarray(clip["A"].astype(np.float32))
+    W32 = np.asfortranarray(clip["W1"].astype(np.float32))
+    tA = torch.from_numpy(A32).to(dev)
+    tW = torch.from_numpy(W32).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    m, n, k, r = spec.m, spec.n, spec.k, spec.r
+
+    def make():
+        return wlr.Solver(m, n, k, r, precision=wlr.WLR_PREC_FP32, stop=wlr.WLR_STOP_NONE,
+                          stream=stream)
+
+    s = make()
+    s.set_data(tA, tW)
+
+    # ---- calibration: F* and p*
+    def score_after(p):
+        s.set_init(wlr.WLR_INIT_A1)
+        if p > 0:
+            s.solve(0.0, p)
+        return s.objective()
+
+    if a.p_star > 0:
+        p_star = a.p_star
+        Fstar = float("nan")
+        rel_at = float("nan")
+    else:
+        s.set_init(wlr.WLR_INIT_A1)
+        chunk = 250
+        checkpoints = []
+        done = 0
+        while done < a.calib_iters:
+            s.solve(0.0, chunk)
+            done += chunk
+            checkpoints.append((done, s.objective()))
+        Fstar = min(v for _, v in checkpoints)
+        Fg, _ = _golden_fstar()
+        if Fg is not None:
+            Fstar = min(Fstar, Fg)
+        for p, v in checkpoints:
+            print(f"calib p={p} F~={v:.12e} rel={(v - Fstar) / Fstar:.3e}", file=sys.stderr)
+        hi = next((p for p, v in checkpoints if (v - Fstar) / Fstar <= TARGET), None)
+        if hi is None:
+            raise RuntimeError(f"rel-obj {TARGET} not reached in {a.calib_iters} iterations")
+        lo = max(0, hi - chunk)
+        while hi - lo > 1:
+            mid = (lo + hi) // 2
+            if (score_after(mid) - Fstar) / Fstar <= TARGET:
+                hi = mid
+            else:
+                lo = mid
+        p_star = hi
+        F_at = score_after(p_star)
+        rel_at = (F_at - Fstar) / Fstar
+
+    # ---- timed region: W warm-up + K timed steps of (setup + p* iterations)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    vis = [v for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
+    sampler = ClockSampler(vis[local].strip() if local < len(vis) else local)
+
+    def one_step():
+        s.set_data(tA, tW)
+        s.set_init(wlr.WLR_INIT_A1)
+        s.solve(0.0, p_star)
+
+    for _ in range(a.warmup):
+        flush.fill_(1.0)
+        one_step()
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    sampler.start()
+    launches0 = s.launches()
+    times = []
+    for _ in range(a.steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        one_step()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    torch.cuda.synchronize(dev)
+    launches = s.launches() - launches0
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    t_step = statistics.mean(times)
+    if world > 1:
+        tt = torch.tensor([t_step], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_step = float(tt.item())
+
+    # ---- e2e: host buffers through the C ABI (pinned), copies inside the timed region
+    hA = torch.from_numpy(A32).pin_memory()
+    hW = torch.from_numpy(W32).pin_memory()
+    hX = torch.empty((k, m), dtype=torch.float32).pin_memory().T  # column-major m x k
+    se = wlr.Solver(m, n, k, r, precision=wlr.WLR_PREC_FP32, stop=wlr.WLR_STOP_NONE, stream=stream)
+    e2e_times = []
+    for q in range(a.warmup + a.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        se.set_data(hA, hW)
+        se.set_init(wlr.WLR_INIT_A1)
+        se.solve(0.0, p_star)
+        se.result(hX)
+        t1 = time.perf_counter()
+        if q >= a.warmup:
+            e2e_times.append(t1 - t0)
+    e2e = statistics.mean(e2e_times)
+    h2d = 4 * (m * n + m * k)
+    d2h = 4 * m * k
+    se.close()
+
+    # ---- per-kernel durations (CUDA events on the library's launching stream)
+    prof = s.profile(200)
+    tot = sum(v[0] for v in prof.values())
+    top = max(prof.items(), key=lambda kv: kv[1][0])
+    name, (ms_tot, nl) = top
+    ms_launch = ms_tot / nl
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    n2, s_ = n - k, r - k
+    NP = ((k + s_ + 15) // 16) * 16
+    roof = None
+    if name == "row_pass":
+        # bytes: A2, A1, W1, X1 read, X1 write (FP32); flops: the A2 [C^T V_s] product,
+        # the U/E corrections and the per-row Cholesky + two triangular solves
+        bytes_ = 4 * m * (n2 + 4 * k)
+        flops = 2 * m * n2 * (k + s_) + m * (2 * k * s_ * 2 + k ** 3 / 3 + 2 * k * k)
+        fp32_peak = 152 * 128 * 2 * (clocks["sm_mhz"] or 2070.0) * 1e6 / 1e12
+        t_hbm = bytes_ / (hbm_peak * 1e9)
+        t_alu = flops / (fp32_peak * 1e12)
+        if t_alu >= t_hbm:
+            ach = flops / (ms_launch * 1e-3) / 1e12
+            roof = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
+                    "frac": ach / fp32_peak, "traffic": None, "kernel": name,
+                    "peak_source": "152 SMs x 128 FP32 lanes x 2 x median SM clock under load"}
+        else:
+            ach = bytes_ / (ms_launch * 1e-3) / 1e9
+            roof = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": ach / hbm_peak, "traffic": None, "kernel": name,
+                    "peak_source": f"{hbm_src} hbm_gbs"}
+        roof["algorithmic_bytes"] = bytes_
+        roof["algorithmic_flops"] = flops
+        roof["ms_per_launch"] = ms_launch
+    else:
+        roof = {"bound": None, "kernel": name, "ms_per_launch": ms_launch}
+    kernels = {kn: {"share": v[0] / tot, "ms_per_launch": v[0] / v[1], "launches": v[1]}
+               for kn, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}
+
+    # ---- CPU baseline (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        n_s = 6
+        try:
+            sec = _oracle_iteration_time(n_s, threads)
+            cpu = {"value": sec * p_star, "unit": UNIT, "cores": threads, "kind": "oracle",
+                   "sample": f"{n_s} FP64 oracle iterations of the same clip (+1 warm-up), "
+                             f"{sec:.3f} s each, projected to p*={p_star} iterations"}
+        except Exception as e:  # noqa: BLE001
+            cpu = {"value": None, "unit": UNIT, "cores": threads, "kind": "oracle",
+                   "sample": f"failed: {e}"[:200]}
+
+    if rank == 0:
+        cfg = dict(cfg)
+        cfg.update({"p_star": p_star, "F_star": Fstar, "rel_obj_at_p_star": rel_at,
+                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                    "step": "set_data (setup: ||A2||^2, K=A2^T A2) + set_init(A1) + p* iterations",
+                    "seconds_per_iteration": t_step / max(p_star, 1),
+                    "kernel_shares": kernels})
+        line = {
+            "metric": METRIC, "value": t_step, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": cfg,
+            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+        }
+        print(json.dumps(line))
+    s.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    a = _args()
+    if a.warmup < 3:
+        a.warmup = 3
+    if a.impl == "reference":
+        return run_reference(a)
+    return run_ours(a)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

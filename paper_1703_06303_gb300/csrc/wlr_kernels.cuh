@@ -180,31 +180,54 @@ __device__ bool block_cholesky(T* L, int k, int* flag_sh) {
   return *flag_sh == 0;
 }
 
-// One block: R (upper, S = R^T R) and R^{-1} from a reduced k x k Gram S (double).
+// One block: R (upper, S = R^T R) and R^{-1} from a reduced k x k Gram S, factored in
+// double whatever T is (the first CholeskyQR factor meets cond(X1)^2).  A pivot below
+// 1e-13 of its column's original diagonal means X1 is numerically of rank < k.
 template <typename T>
 __global__ void chol_small(const double* __restrict__ S, int k, T* __restrict__ R,
                            T* __restrict__ Rinv, int* __restrict__ err) {
   extern __shared__ unsigned char smem_raw[];
-  T* L = reinterpret_cast<T*>(smem_raw);
+  double* L = reinterpret_cast<double*>(smem_raw);
+  double* Ri = L + k * k;
   __shared__ int flag;
-  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int e = tid; e < k * k; e += nt) {
     const int i = e % k, j = e / k;
-    L[e] = i >= j ? (T)S[i + j * k] : T(0);
+    L[e] = i >= j ? S[i + j * k] : 0.0;
+  }
+  if (tid == 0) flag = 0;
+  __syncthreads();
+  for (int t = 0; t < k; ++t) {
+    if (tid == 0) {
+      double d = L[t + t * k];
+      if (!(d > 1e-13 * S[t + t * k]) || !isfinite(d)) { flag = 1; d = 1.0; }
+      L[t + t * k] = sqrt(d);
+    }
+    __syncthreads();
+    const double piv = L[t + t * k];
+    for (int i = t + 1 + tid; i < k; i += nt) L[i + t * k] /= piv;
+    __syncthreads();
+    const int w = k - t - 1;
+    for (int e = tid; e < w * w; e += nt) {
+      const int i = t + 1 + e % w, j = t + 1 + e / w;
+      if (i >= j) L[i + j * k] -= L[i + t * k] * L[j + t * k];
+    }
+    __syncthreads();
+  }
+  if (flag && tid == 0) atomicOr(err, ERRBIT_RANK_DEFICIENT);
+  // R^{-1}: column c solves R x = e_c by back substitution (R(a,l) = L(l,a)).
+  for (int c = tid; c < k; c += nt) {
+    for (int a = k - 1; a >= 0; --a) {
+      double v = a == c ? 1.0 : 0.0;
+      for (int l = a + 1; l <= c; ++l) v -= L[l + a * k] * Ri[l + c * k];
+      Ri[a + c * k] = a <= c ? v / L[a + a * k] : 0.0;
+    }
   }
   __syncthreads();
-  const bool ok = block_cholesky(L, k, &flag);
-  if (!ok && threadIdx.x == 0) atomicOr(err, ERRBIT_RANK_DEFICIENT);
-  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+  for (int e = tid; e < k * k; e += nt) {
     const int a = e % k, b = e / k;  // R(a, b) = L(b, a)
-    R[e] = a <= b ? L[b + a * k] : T(0);
-  }
-  // R^{-1}: column c solves R x = e_c by back substitution (R(a,l) = L(l,a)).
-  for (int c = threadIdx.x; c < k; c += blockDim.x) {
-    for (int a = k - 1; a >= 0; --a) {
-      T v = a == c ? T(1) : T(0);
-      for (int l = a + 1; l <= c; ++l) v -= L[l + a * k] * Rinv[l + c * k];
-      Rinv[a + c * k] = a <= c ? v / L[a + a * k] : T(0);
-    }
+    R[e] = a <= b ? (T)L[b + a * k] : T(0);
+    Rinv[e] = (T)Ri[e];
   }
 }
 

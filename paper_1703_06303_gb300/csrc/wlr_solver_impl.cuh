@@ -86,6 +86,7 @@ class Solver final : public SolverBase {
     set_smem((const void*)row_pass<T, 64>, RowPassSmem<T>::bytes(NP, k, s));
     set_smem((const void*)x2_pass<T>, x2_smem());
     set_smem((const void*)coef_kernel<T>, 2 * sizeof(T) * k * k);
+    set_smem((const void*)chol_small<T>, 2 * sizeof(double) * k * k);
     WLR_CUDA(cudaStreamSynchronize(stream_));
   }
 
@@ -581,7 +582,7 @@ class Solver final : public SolverBase {
     reduce(part_, (int64_t)k * k, ch_S1_.nch, (int64_t)k * k, S1_, nullptr);
     {
       Prof pf(this, "chol_small");
-      chol_small<T><<<1, 64, sizeof(T) * k * k, stream_>>>(S1_, k, R1_, R1inv_, err_);
+      chol_small<T><<<1, 64, 2 * sizeof(double) * k * k, stream_>>>(S1_, k, R1_, R1inv_, err_);
     }
     {
       Prof pf(this, "form_q");
