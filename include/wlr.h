@@ -177,6 +177,42 @@ wlr_status wlr_profile(wlr_handle h, int32_t reps, char* names, int32_t names_ca
                        double* ms_total, int32_t* launches, int32_t max_kernels,
                        int32_t* n_kernels);
 
+/* Allocation-free X1 update.  The paper has no counterpart: this is a packaging of
+ * the library's own row-update kernels for callers that cannot allocate device
+ * memory -- code that must keep within memory it has already reserved (a framework
+ * whose caching allocator owns the device), or latency-sensitive code for which a
+ * cudaMalloc/cudaFree, which can synchronise the device, is not acceptable.
+ *
+ * Given X1_p (m x k, column-major, leading dimension m), the data A (m x n, lda) and
+ * W1 (m x k, ldw), and the factors of the (C, D) step for X1_p -- C (k x (n-k),
+ * leading dimension k) and V_s ((n-k) x (r-k), leading dimension n-k), as returned by
+ * wlr_get_factors -- it writes X1_{p+1} (m x k, leading dimension m) with
+ * X1_{p+1}(i,:) = E(i,:) (diag(W1(i,:)^2) + C C^T)^{-1},
+ * E = A1 o W1 o W1 + (A2 - D) C^T, D = (P_perp A2) V_s V_s^T, i.e. the same values as
+ * the X1 step of wlr_step.  All pointers are FP32 device pointers except wterm
+ * (device double: ||(A1 - X1_p) o W1||_F^2, may be NULL) and status (device int: 0, or
+ * 4 = WLR_ERR_NOT_SPD if a row system broke down; may be NULL).  Work is queued on
+ * cuda_stream (a cudaStream_t, NULL = the legacy default stream); the call does not
+ * synchronise.
+ *
+ * Scratch: one fixed 1 MiB device array, held by every GPU that loads the library
+ * until the process exits.  A problem fits when
+ *   4 (n-k) ceil16(r) + 4 k^2 + 4 k (r-k) + 8 ceil(m / 64)  (each term rounded up to
+ *   256 bytes, plus 256) <= 1 MiB,
+ * e.g. m up to 5,000,000 with n - k <= 1000 and r <= 64; larger problems get
+ * WLR_ERR_UNSUPPORTED.  No cudaMalloc, cudaFree or allocating routine is called.
+ * The first call on a device (with that device current) looks up the array's device
+ * address and sets kernel attributes; make that first call before any stream capture.
+ * Every call on a device shares the one array and overwrites what the last call left
+ * there, so calls whose GPU work overlaps (on different streams, or from different
+ * threads) race: serialise them.
+ * Returns WLR_ERR_INVALID_ARG (NULL pointer, shapes as in wlr_create, lda or ldw < m),
+ * WLR_ERR_UNSUPPORTED (k > 64, r - k > 32, or the scratch rule above), WLR_ERR_CUDA. */
+wlr_status wlr_x1_update_noalloc(const float* A, int64_t lda, const float* W1, int64_t ldw,
+                                 const float* X1, int64_t m, int64_t n, int64_t k, int64_t r,
+                                 const float* C, const float* Vs, float* X1_next,
+                                 double* wterm, int* status, void* cuda_stream);
+
 /* Number of kernels this handle has launched (graph replays count each node). */
 int64_t wlr_kernel_launches(wlr_handle h);
 

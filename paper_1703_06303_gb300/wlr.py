@@ -79,6 +79,7 @@ def _load():
         "wlr_last_error": (ct.c_char_p, [H]),
         "wlr_kernel_launches": (i64, [H]),
         "wlr_profile": (i32, [H, i32, ct.c_char_p, i32, P, P, i32, ct.POINTER(i32)]),
+        "wlr_x1_update_noalloc": (i32, [P, i64, P, i64, P, i64, i64, i64, i64, P, P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -92,7 +93,7 @@ EXPORTED = (
     "wlr_default_options", "wlr_create", "wlr_set_data", "wlr_set_init", "wlr_step",
     "wlr_solve", "wlr_objective", "wlr_get_result", "wlr_get_factors", "wlr_get_history",
     "wlr_get_iteration", "wlr_destroy", "wlr_status_string", "wlr_last_error",
-    "wlr_kernel_launches", "wlr_profile",
+    "wlr_kernel_launches", "wlr_profile", "wlr_x1_update_noalloc",
 )
 
 
@@ -281,6 +282,31 @@ def wlr_profile(h, reps=20, max_kernels=64):
                             ct.byref(n)), h)
     names = buf.value.decode().split("\n")[:n.value]
     return {nm: (float(ms[q]), int(ln[q])) for q, nm in enumerate(names)}
+
+
+def wlr_x1_update_noalloc(A, W1, X1, k, r, C, Vs, X1_next, wterm=None, status=None, stream=None):
+    """X1 update into X1_next without any device allocation (see include/wlr.h).
+    A, W1, X1, C, Vs, X1_next: float32 CUDA tensors, column-major; X1 and X1_next with
+    leading dimension m; wterm: a 1-element float64 CUDA tensor or None; status: a
+    1-element int32 CUDA tensor or None.  Asynchronous on `stream`."""
+    pa, lda, dta, mema, _ = _matrix(A)
+    pw, ldw, dtw, memw, _ = _matrix(W1)
+    px, ldx, dtx, memx, _ = _matrix(X1)
+    pn, ldn, dtn, memn, _ = _matrix(X1_next)
+    m, n = A.shape
+    if {dta, dtw, dtx, dtn} != {WLR_F32} or {mema, memw, memx, memn} != {WLR_MEM_DEVICE}:
+        raise ValueError("float32 device tensors only")
+    if ldx != m or ldn != m:
+        raise ValueError("X1 and X1_next need leading dimension m")
+    pc = C.data_ptr() if C is not None and C.numel() else None
+    pv = Vs.data_ptr() if Vs is not None and Vs.numel() else None
+    st = _lib.wlr_x1_update_noalloc(pa, lda, pw, ldw, px, m, n, int(k), int(r), pc, pv, pn,
+                                    wterm.data_ptr() if wterm is not None else None,
+                                    status.data_ptr() if status is not None else None,
+                                    _stream_ptr(stream))
+    if st != WLR_OK:
+        raise WlrError(st, "wlr_x1_update_noalloc")
+    return st
 
 
 class Solver:
