@@ -5,17 +5,21 @@
 //
 // Step map (Section 3 / Algorithm 1):
 //   a1  X1 = Q R by CholeskyQR2:  S1 = X1^T X1 -> R1;  Q1 = X1 R1^{-1};
-//       S2 = Q1^T Q1 -> R2;  R = R2 R1                    gemm_tn_partial, chol_small, form_q
-//   a2  B = Q^T A2 = R2^{-T} Q1^T A2,  C = R^{-1} B        gemm_tn_partial, coef_kernel
+//       S2 = Q1^T Q1 -> R2;  R = R2 R1                    gram_tn, chol1_kernel, form_q,
+//                                                         chol2_kernel
+//   a2  B = Q^T A2 = R2^{-T} Q1^T A2,  C = R^{-1} B        gram_tn, coef_kernel2
 //   a3  D = H_{r-k}((I - Q Q^T) A2) through the Gram (P_perp A2)^T (P_perp A2) = K - B^T B,
 //       K = A2^T A2 formed once; top-(r-k) eigenpairs by subspace iteration with
 //       Rayleigh-Ritz (parallel Jacobi on the b x b projection)
-//                                                         form_g2, eig_mult, eig_small, eig_update
+//                                                         form_g2_df, eig_mult, eig_small,
+//                                                         eig_update
 //   a4  E = A1 o W1 o W1 + A2 C^T - U_s (V_s^T C^T), U_s = A2 V_s - X1 (C V_s)  = (A2 - D) C^T
-//   a5  X1(i,:) = E(i,:) (diag(W1(i,:)^2) + C C^T)^{-1}   prep_rowpass, row_pass
+//   a5  X1(i,:) = E(i,:) (diag(W1(i,:)^2) + C C^T)^{-1}   prep_gram, row_pass
 //   a6  F_p = ||(A1-X1) o W1||^2 + ||A2||^2 - ||B||^2 - sum_{j<=r-k} sigma_j^2
 //                                                         finalize_objective, x2_pass (exact)
 #pragma once
+
+#include <type_traits>
 
 #include "wlr_common.cuh"
 
@@ -24,15 +28,18 @@ namespace wlr {
 constexpr int EIG_BMAX = 32;   // largest subspace block (Jacobi size)
 
 // --------------------------------------------------------------------------------
-// part[off + c*stride + a + b*P] = sum_{i in rows of chunk c} X[i + a*ldx] * Y[i + b*ldy]
-// for a < P, b < Q.  One (PT x QT) output tile per block, rows in steps of 32.
-// Thread (tx, ty) owns rows ty + (PT/4) u and columns tx + (QT/4) v of the tile, so the
-// shared-memory reads are conflict-free.
+// Split-m Gram product with hierarchical accumulation:
+//   part[off + c*stride + a + b*P] = sum_{i in rows of chunk c} X[i, a] * Y[i, b]
+// for a < P, b < Q, where column b of Y is Y1[:, b] for b < q1 and Y2[:, b - q1] after
+// (a virtual concatenation [Y1 Y2]).  Each 32-row slab is summed in T, then added to a
+// double accumulator, so the cross-slab sum keeps FP64 accuracy while the inner
+// products run at the T rate.  One (PT x QT) output tile per block; thread (tx, ty)
+// owns rows ty + (PT/4) u and columns tx + (QT/4) v (conflict-free shared reads).
 template <typename T, int PT, int QT>
 __global__ void __launch_bounds__((PT / 4) * (QT / 4))
-gemm_tn_partial(const T* __restrict__ X, int64_t ldx, const T* __restrict__ Y, int64_t ldy,
-                int m, int P, int Q, int chunk_rows, T* __restrict__ part,
-                int64_t part_stride, int64_t part_offset) {
+gram_tn(const T* __restrict__ X, int64_t ldx, const T* __restrict__ Y1, int64_t ldy1, int q1,
+        const T* __restrict__ Y2, int64_t ldy2, int m, int P, int Q, int chunk_rows,
+        double* __restrict__ part, int64_t part_stride, int64_t part_offset) {
   constexpr int BK = 32;
   constexpr int NTX = QT / 4, NTY = PT / 4, NT = NTX * NTY;
   __shared__ T Xs[BK][PT + 1];
@@ -41,11 +48,11 @@ gemm_tn_partial(const T* __restrict__ X, int64_t ldx, const T* __restrict__ Y, i
   const int i_begin = c * chunk_rows;
   const int i_end = min(m, i_begin + chunk_rows);
   const int tx = threadIdx.x % NTX, ty = threadIdx.x / NTX;
-  T acc[4][4];
+  double acc[4][4];
 #pragma unroll
   for (int u = 0; u < 4; ++u)
 #pragma unroll
-    for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
+    for (int v = 0; v < 4; ++v) acc[u][v] = 0.0;
 
   for (int i0 = i_begin; i0 < i_end; i0 += BK) {
     for (int e = threadIdx.x; e < BK * PT; e += NT) {
@@ -56,9 +63,17 @@ gemm_tn_partial(const T* __restrict__ X, int64_t ldx, const T* __restrict__ Y, i
     for (int e = threadIdx.x; e < BK * QT; e += NT) {
       const int kk = e % BK, b = e / BK;
       const int i = i0 + kk, gb = b0 + b;
-      Ys[kk][b] = (i < i_end && gb < Q) ? Y[i + (int64_t)gb * ldy] : T(0);
+      T v = T(0);
+      if (i < i_end && gb < Q)
+        v = gb < q1 ? Y1[i + (int64_t)gb * ldy1] : Y2[i + (int64_t)(gb - q1) * ldy2];
+      Ys[kk][b] = v;
     }
     __syncthreads();
+    T sl[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) sl[u][v] = T(0);
 #pragma unroll 8
     for (int kk = 0; kk < BK; ++kk) {
       T xa[4], yb[4];
@@ -69,11 +84,15 @@ gemm_tn_partial(const T* __restrict__ X, int64_t ldx, const T* __restrict__ Y, i
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = fma(xa[u], yb[v], acc[u][v]);
+        for (int v = 0; v < 4; ++v) sl[u][v] = fma(xa[u], yb[v], sl[u][v]);
     }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[u][v] += (double)sl[u][v];
     __syncthreads();
   }
-  T* out = part + part_offset + (int64_t)c * part_stride;
+  double* out = part + part_offset + (int64_t)c * part_stride;
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
     const int a = a0 + ty + NTY * u;
@@ -152,55 +171,33 @@ __global__ void random_normal_fill(T* __restrict__ X, int64_t ldx, int m, int k,
 }
 
 // --------------------------------------------------------------------------------
-// In-place Cholesky S = L L^T of a k x k matrix held column-major in shared memory
-// (lower triangle used).  All threads of the block take part.  Returns false (in every
-// thread) when a pivot is not positive and finite.
+// First CholeskyQR factor (one block): S1 = sum of the nch partial Grams (double, in a
+// fixed order), S1 = R1^T R1 in double, and R1^{-1} (upper) written in T.  A pivot
+// below 1e-13 of its column's original diagonal means X1 is numerically of rank < k.
 template <typename T>
-__device__ bool block_cholesky(T* L, int k, int* flag_sh) {
-  const int tid = threadIdx.x, nt = blockDim.x;
-  if (tid == 0) *flag_sh = 0;
-  __syncthreads();
-  for (int t = 0; t < k; ++t) {
-    if (tid == 0) {
-      T d = L[t + t * k];
-      if (!(d > T(0)) || !wfinite(d)) { *flag_sh = 1; d = T(1); }
-      L[t + t * k] = wsqrt(d);
-    }
-    __syncthreads();
-    const T piv = L[t + t * k];
-    for (int i = t + 1 + tid; i < k; i += nt) L[i + t * k] /= piv;
-    __syncthreads();
-    const int w = k - t - 1;
-    for (int e = tid; e < w * w; e += nt) {
-      const int i = t + 1 + e % w, j = t + 1 + e / w;
-      if (i >= j) L[i + j * k] -= L[i + t * k] * L[j + t * k];
-    }
-    __syncthreads();
-  }
-  return *flag_sh == 0;
-}
-
-// One block: R (upper, S = R^T R) and R^{-1} from a reduced k x k Gram S, factored in
-// double whatever T is (the first CholeskyQR factor meets cond(X1)^2).  A pivot below
-// 1e-13 of its column's original diagonal means X1 is numerically of rank < k.
-template <typename T>
-__global__ void chol_small(const double* __restrict__ S, int k, T* __restrict__ R,
-                           T* __restrict__ Rinv, int* __restrict__ err) {
+__global__ void __launch_bounds__(256)
+chol1_kernel(const double* __restrict__ part, int nch, int k, T* __restrict__ R1inv,
+             int* __restrict__ err) {
   extern __shared__ unsigned char smem_raw[];
-  double* L = reinterpret_cast<double*>(smem_raw);
-  double* Ri = L + k * k;
+  double* L = reinterpret_cast<double*>(smem_raw);  // k*k
+  double* Ri = L + k * k;                            // k*k
+  double* dg = Ri + k * k;                           // k: original diagonal
   __shared__ int flag;
   const int tid = threadIdx.x, nt = blockDim.x;
-  for (int e = tid; e < k * k; e += nt) {
+  const int kk = k * k;
+  for (int e = tid; e < kk; e += nt) {
+    double v = 0.0;
+    for (int c = 0; c < nch; ++c) v += part[(int64_t)c * kk + e];
     const int i = e % k, j = e / k;
-    L[e] = i >= j ? S[i + j * k] : 0.0;
+    L[e] = i >= j ? v : 0.0;
+    if (i == j) dg[i] = v;
   }
   if (tid == 0) flag = 0;
   __syncthreads();
   for (int t = 0; t < k; ++t) {
     if (tid == 0) {
       double d = L[t + t * k];
-      if (!(d > 1e-13 * S[t + t * k]) || !isfinite(d)) { flag = 1; d = 1.0; }
+      if (!(d > 1e-13 * dg[t]) || !isfinite(d)) { flag = 1; d = 1.0; }
       L[t + t * k] = sqrt(d);
     }
     __syncthreads();
@@ -215,7 +212,7 @@ __global__ void chol_small(const double* __restrict__ S, int k, T* __restrict__ 
     __syncthreads();
   }
   if (flag && tid == 0) atomicOr(err, ERRBIT_RANK_DEFICIENT);
-  // R^{-1}: column c solves R x = e_c by back substitution (R(a,l) = L(l,a)).
+  // R1^{-1}: column c solves R1 x = e_c (R1(a,l) = L(l,a)), one thread per column.
   for (int c = tid; c < k; c += nt) {
     for (int a = k - 1; a >= 0; --a) {
       double v = a == c ? 1.0 : 0.0;
@@ -224,10 +221,73 @@ __global__ void chol_small(const double* __restrict__ S, int k, T* __restrict__ 
     }
   }
   __syncthreads();
+  for (int e = tid; e < kk; e += nt) R1inv[e] = (T)Ri[e];
+}
+
+// Second CholeskyQR factor (one block).  S2 = Q1^T Q1 is close to I, so it is factored
+// in "difference form": S2 = (I + F)(I + F)^T with F lower triangular, computed from
+// Delta = S2 - I so that the small F keeps full relative precision in T:
+//   F_tt = delta / (1 + sqrt(1 + delta)),  delta = Delta_tt - sum_{j<t} F_tj^2
+//   F_it = (Delta_it - sum_{j<t} F_ij F_tj) / (1 + F_tt)               (i > t)
+// Outputs (T): N = (I + F)^{-1} - I = R2^{-T} - I (lower), and
+// Rinv = R1^{-1} (I + N)^T = (R2 R1)^{-1}, the inverse of the full triangular factor.
+template <typename T>
+__global__ void __launch_bounds__(256)
+chol2_kernel(const double* __restrict__ S2, int k, const T* __restrict__ R1inv,
+             T* __restrict__ Nout, T* __restrict__ Rinv, int* __restrict__ err) {
+  extern __shared__ unsigned char smem_raw[];
+  T* F = reinterpret_cast<T*>(smem_raw);  // k*k lower (col-major)
+  T* Nm = F + k * k;                       // k*k lower
+  T* Ri1 = Nm + k * k;                     // k*k upper
+  __shared__ int flag;
+  const int tid = threadIdx.x, nt = blockDim.x;
   for (int e = tid; e < k * k; e += nt) {
-    const int a = e % k, b = e / k;  // R(a, b) = L(b, a)
-    R[e] = a <= b ? (T)L[b + a * k] : T(0);
-    Rinv[e] = (T)Ri[e];
+    const int i = e % k, j = e / k;
+    F[e] = i >= j ? (T)(S2[e] - (i == j ? 1.0 : 0.0)) : T(0);
+    Ri1[e] = R1inv[e];
+  }
+  if (tid == 0) flag = 0;
+  __syncthreads();
+  for (int t = 0; t < k; ++t) {
+    if (tid == 0) {
+      T d = F[t + t * k];
+      for (int j = 0; j < t; ++j) d -= F[t + j * k] * F[t + j * k];
+      if (!(T(1) + d > T(0)) || !wfinite(d)) { flag = 1; d = T(0); }
+      F[t + t * k] = d / (T(1) + wsqrt(T(1) + d));
+    }
+    __syncthreads();
+    const T den = T(1) + F[t + t * k];
+    for (int i = t + 1 + tid; i < k; i += nt) {
+      T v = F[i + t * k];
+      for (int j = 0; j < t; ++j) v -= F[i + j * k] * F[t + j * k];
+      F[i + t * k] = v / den;
+    }
+    __syncthreads();
+  }
+  if (flag && tid == 0) atomicOr(err, ERRBIT_RANK_DEFICIENT);
+  // (I + F) N = -F, column c by forward substitution (N lower)
+  for (int c = tid; c < k; c += nt) {
+    for (int a = 0; a < k; ++a) {
+      T v = T(0);
+      if (a >= c) {
+        v = -F[a + c * k];
+        for (int l = c; l < a; ++l) v -= F[a + l * k] * Nm[l + c * k];
+        v /= (T(1) + F[a + a * k]);
+      }
+      Nm[a + c * k] = v;
+    }
+  }
+  __syncthreads();
+  // Rinv(a, b) = R1inv(a, b) + sum_{l=a..b} R1inv(a, l) N(b, l)
+  for (int e = tid; e < k * k; e += nt) {
+    const int a = e % k, b = e / k;
+    T v = T(0);
+    if (a <= b) {
+      v = Ri1[a + b * k];
+      for (int l = a; l <= b; ++l) v += Ri1[a + l * k] * Nm[b + l * k];
+    }
+    Rinv[e] = v;
+    Nout[e] = Nm[e];
   }
 }
 
@@ -250,85 +310,117 @@ __global__ void form_q(const T* __restrict__ X1, int64_t ldx, const T* __restric
   }
 }
 
-// Coefficient step.  In every block: R2 = chol(S2) (upper), R = R2 R1.  Thread per
-// column j of A2: B(:,j) = R2^{-T} (Q1^T A2)(:,j), C(:,j) = R^{-1} B(:,j).
-// Writes C (k x n2), B (k x n2), the C^T part of Z2 (row j: Z2[j*NP + a] = C(a,j)),
-// and the block's partial ||B||_F^2.
+// Coefficient step, one thread per column j of A2:
+//   B(:,j) = R2^{-T} (Q1^T A2)(:,j) = t + N t  (t kept in double, the small N t in T)
+//   C(:,j) = R^{-1} B(:,j)
+// Writes C (k x n2, T), B in double, B split as float hi + lo (for the double-float
+// Gram), the C^T part of Z2 (row j: Z2[j*NP + a] = C(a,j)), and the block's ||B||^2.
 template <typename T>
-__global__ void __launch_bounds__(64)
-coef_kernel(const double* __restrict__ S2, const double* __restrict__ QtA2,
-            const T* __restrict__ R1, int k, int n2, int NP, T* __restrict__ Cout,
-            T* __restrict__ Bout, T* __restrict__ Z2, double* __restrict__ bnorm_part,
-            int* __restrict__ err) {
+__global__ void __launch_bounds__(128)
+coef_kernel2(const double* __restrict__ QtA2, const T* __restrict__ Nm, const T* __restrict__ Rinv,
+             int k, int n2, int NP, T* __restrict__ Cout, double* __restrict__ B64,
+             float* __restrict__ Bh, float* __restrict__ Bl, T* __restrict__ Z2,
+             double* __restrict__ bnorm_part) {
   extern __shared__ unsigned char smem_raw[];
-  T* L2 = reinterpret_cast<T*>(smem_raw);  // k*k, chol of S2 (lower)
-  T* R = L2 + k * k;                        // k*k, R = R2 R1 (upper)
-  __shared__ int flag;
+  T* Ns = reinterpret_cast<T*>(smem_raw);
+  T* Rs = Ns + k * k;
   __shared__ double sh[32];
   for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
-    const int i = e % k, j = e / k;
-    L2[e] = i >= j ? (T)S2[i + j * k] : T(0);
-  }
-  __syncthreads();
-  const bool ok = block_cholesky(L2, k, &flag);
-  if (!ok && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(err, ERRBIT_RANK_DEFICIENT);
-  // R(a,c) = sum_{b=a..c} R2(a,b) R1(b,c),  R2(a,b) = L2(b,a)
-  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
-    const int a = e % k, c = e / k;
-    T v = T(0);
-    for (int b = a; b <= c; ++b) v = fma(L2[b + a * k], R1[b + c * k], v);
-    R[e] = a <= c ? v : T(0);
+    Ns[e] = Nm[e];
+    Rs[e] = Rinv[e];
   }
   __syncthreads();
   double bn = 0.0;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j < n2) {
+    T tv[64];
     T bv[64];
-    T cv[64];
-    // forward: L2 b = t
+    for (int a = 0; a < k; ++a) tv[a] = (T)QtA2[a + (int64_t)j * k];
     for (int a = 0; a < k; ++a) {
-      T v = (T)QtA2[a + (int64_t)j * k];
-      for (int l = 0; l < a; ++l) v -= L2[a + l * k] * bv[l];
-      bv[a] = v / L2[a + a * k];
-      bn += (double)bv[a] * (double)bv[a];
-    }
-    // back: R c = b
-    for (int a = k - 1; a >= 0; --a) {
-      T v = bv[a];
-      for (int l = a + 1; l < k; ++l) v -= R[a + l * k] * cv[l];
-      cv[a] = v / R[a + a * k];
+      T corr = T(0);
+      for (int l = 0; l <= a; ++l) corr = fma(Ns[a + l * k], tv[l], corr);
+      const double b = QtA2[a + (int64_t)j * k] + (double)corr;
+      B64[a + (int64_t)j * k] = b;
+      const float hi = (float)b;
+      Bh[a + (int64_t)j * k] = hi;
+      Bl[a + (int64_t)j * k] = (float)(b - (double)hi);
+      bv[a] = (T)b;
+      bn += b * b;
     }
     for (int a = 0; a < k; ++a) {
-      Cout[a + (int64_t)j * k] = cv[a];
-      Bout[a + (int64_t)j * k] = bv[a];
-      Z2[(int64_t)j * NP + a] = cv[a];
+      T c = T(0);
+      for (int l = a; l < k; ++l) c = fma(Rs[a + l * k], bv[l], c);
+      Cout[a + (int64_t)j * k] = c;
+      Z2[(int64_t)j * NP + a] = c;
     }
   }
   bn = block_sum_double(bn, sh);
   if (threadIdx.x == 0) bnorm_part[blockIdx.x] = bn;
 }
 
-// G2 = K - B^T B (n2 x n2): 32x32 tile per block, 256 threads (each 4 entries).
+// Error-free transformations (Dekker 1971; Knuth TAOCP vol. 2, 4.2.2):
+// a + b = s + e exactly (TwoSum) and a * b = p + e exactly (TwoProduct via fma).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bp = s - a;
+  const float ap = s - bp;
+  e = (a - ap) + (b - bp);
+}
+
+// G2 = K - B^T B (n2 x n2), 32x32 tile per block, 256 threads (4 entries each).
+// FP32 path: sum_a B_ai B_aj in double-float arithmetic from B = hi + lo (the dropped
+// lo*lo term is below 2^-48 relative), then K (double) minus it in double, rounded
+// to T.  FP64 path: plain double.
 template <typename T>
 __global__ void __launch_bounds__(256)
-form_g2(const T* __restrict__ K, const T* __restrict__ B, int k, int n2, T* __restrict__ G2) {
-  __shared__ T Bi[64][33];
-  __shared__ T Bj[64][33];
+form_g2_df(const double* __restrict__ K64, const double* __restrict__ B64,
+           const float* __restrict__ Bh, const float* __restrict__ Bl, int k, int n2,
+           T* __restrict__ G2) {
+  constexpr bool kDouble = std::is_same<T, double>::value;
+  constexpr int FR = kDouble ? 1 : 64, DR = kDouble ? 64 : 1;
+  __shared__ float Hi[FR][33], Li[FR][33], Hj[FR][33], Lj[FR][33];
+  __shared__ double Di[DR][33], Dj[DR][33];
   const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
   for (int e = threadIdx.x; e < k * 32; e += blockDim.x) {
     const int a = e % k, c = e / k;
-    Bi[a][c] = (i0 + c < n2) ? B[a + (int64_t)(i0 + c) * k] : T(0);
-    Bj[a][c] = (j0 + c < n2) ? B[a + (int64_t)(j0 + c) * k] : T(0);
+    const bool vi = i0 + c < n2, vj = j0 + c < n2;
+    const int64_t oi = a + (int64_t)(i0 + c) * k, oj = a + (int64_t)(j0 + c) * k;
+    if (kDouble) {
+      Di[a][c] = vi ? B64[oi] : 0.0;
+      Dj[a][c] = vj ? B64[oj] : 0.0;
+    } else {
+      Hi[a][c] = vi ? Bh[oi] : 0.f;
+      Li[a][c] = vi ? Bl[oi] : 0.f;
+      Hj[a][c] = vj ? Bh[oj] : 0.f;
+      Lj[a][c] = vj ? Bl[oj] : 0.f;
+    }
   }
   __syncthreads();
   const int ti = threadIdx.x % 32, tj = threadIdx.x / 32;
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
     const int jj = tj + 8 * u;
-    T v = T(0);
-    for (int a = 0; a < k; ++a) v = fma(Bi[a][ti], Bj[a][jj], v);
+    double sum;
+    if (kDouble) {
+      double v = 0.0;
+      for (int a = 0; a < k; ++a) v = fma(Di[a][ti], Dj[a][jj], v);
+      sum = v;
+    } else {
+      float sh_ = 0.f, sl_ = 0.f;
+      for (int a = 0; a < k; ++a) {
+        const float hi = Hi[a][ti], hj = Hj[a][jj];
+        const float p = hi * hj;
+        const float pe = fmaf(hi, hj, -p);
+        const float x = fmaf(hi, Lj[a][jj], fmaf(Li[a][ti], hj, pe));
+        float s, e;
+        two_sum(sh_, p, s, e);
+        sh_ = s;
+        sl_ += e + x;
+      }
+      sum = (double)sh_ + (double)sl_;
+    }
     const int i = i0 + ti, j = j0 + jj;
-    if (i < n2 && j < n2) G2[i + (int64_t)j * n2] = K[i + (int64_t)j * n2] - v;
+    if (i < n2 && j < n2) G2[i + (int64_t)j * n2] = (T)(K64[i + (int64_t)j * n2] - sum);
   }
 }
 
@@ -336,15 +428,23 @@ form_g2(const T* __restrict__ K, const T* __restrict__ B, int k, int n2, T* __re
 // Subspace iteration, multiply: Z = G2 V (n2 x b), one warp per row of Z (G2 is
 // symmetric, so row j of Z uses the contiguous column j of G2).  Per block partials
 // H = V^T Z and P = Z^T Z over its rows: part[blk][0][b][b], part[blk][1][b][b].
-template <typename T>
+// VSMEM: V is staged in shared memory transposed (Vt[c][l]) once per block.
+template <typename T, bool VSMEM>
 __global__ void __launch_bounds__(256)
 eig_mult(const T* __restrict__ G2, const T* __restrict__ V, int n2, int b, T* __restrict__ Z,
          T* __restrict__ part) {
-  constexpr int RB = 32;
+  constexpr int RB = 16;
+  extern __shared__ unsigned char smem_raw[];
+  T* Vt = reinterpret_cast<T*>(smem_raw);  // [b][n2] when VSMEM
   __shared__ T Zs[RB][EIG_BMAX + 1];
   __shared__ T Vr[RB][EIG_BMAX + 1];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int j0 = blockIdx.x * RB;
+  if (VSMEM) {
+    for (int e = threadIdx.x; e < b * n2; e += blockDim.x) Vt[e] = V[e];
+    __syncthreads();
+  }
+  const T* Vsrc = VSMEM ? Vt : V;
   for (int rr = w; rr < RB; rr += 8) {
     const int j = j0 + rr;
     T acc[EIG_BMAX];
@@ -355,7 +455,7 @@ eig_mult(const T* __restrict__ G2, const T* __restrict__ V, int n2, int b, T* __
         const T g = G2[l + (int64_t)j * n2];
 #pragma unroll
         for (int c = 0; c < EIG_BMAX; ++c)
-          if (c < b) acc[c] = fma(g, V[l + (int64_t)c * n2], acc[c]);
+          if (c < b) acc[c] = fma(g, Vsrc[l + (int64_t)c * n2], acc[c]);
       }
     }
     T mine = T(0);
@@ -368,7 +468,7 @@ eig_mult(const T* __restrict__ G2, const T* __restrict__ V, int n2, int b, T* __
     }
     if (lane < b) {
       Zs[rr][lane] = j < n2 ? mine : T(0);
-      Vr[rr][lane] = j < n2 ? V[j + (int64_t)lane * n2] : T(0);
+      Vr[rr][lane] = j < n2 ? Vsrc[j + (int64_t)lane * n2] : T(0);
       if (j < n2) Z[j + (int64_t)lane * n2] = mine;
     }
   }
@@ -377,6 +477,7 @@ eig_mult(const T* __restrict__ G2, const T* __restrict__ V, int n2, int b, T* __
   for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
     const int c1 = e % b, c2 = e / b;
     T h = T(0), p = T(0);
+#pragma unroll
     for (int rr = 0; rr < RB; ++rr) {
       h = fma(Vr[rr][c1], Zs[rr][c2], h);
       p = fma(Zs[rr][c1], Zs[rr][c2], p);
@@ -439,7 +540,9 @@ eig_small(const T* __restrict__ part, int nblk, int b, int max_sweeps, T* __rest
   __syncthreads();
   // ---- parallel Jacobi
   const int N = (b + 1) & ~1;  // even number of players (index b is a dummy when b odd)
-  const T eps = sizeof(T) == 4 ? T(1e-7) : T(1e-15);
+  // stop once the off-diagonal mass is at the rounding level of a b x b rotation
+  // sequence: ||offdiag|| <= 4 b u ||H||
+  const T eps = T(4 * b) * (sizeof(T) == 4 ? T(5.96e-8) : T(1.11e-16));
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     // convergence: off-diagonal mass relative to the total
     double off = 0.0, tot = 0.0;
@@ -682,6 +785,50 @@ __global__ void prep_rowpass(const T* __restrict__ C, const T* __restrict__ Vs, 
   }
 }
 
+// G = C C^T (k x k) and CV = C V_s (k x s) from Z2 = [C^T | V_s] (row-major n2 x NP):
+// G(a,t) = sum_j Z2[j][a] Z2[j][t], CV(a,c) = sum_j Z2[j][a] Z2[j][k+c].  Each block
+// sums 64 rows into a double partial; the last block to finish (counted with an atomic
+// ticket after a memory fence, so it sees every partial) adds the partials in block
+// order and resets the ticket for the next launch.  No block ever waits on another.
+template <typename T>
+__global__ void __launch_bounds__(256)
+prep_gram(const T* __restrict__ Z2, int n2, int k, int s, int NP, double* __restrict__ part,
+          unsigned int* __restrict__ ticket, T* __restrict__ G, T* __restrict__ CV) {
+  constexpr int RB = 64;
+  extern __shared__ unsigned char smem_raw[];
+  T* Zr = reinterpret_cast<T*>(smem_raw);  // [RB][NP + 1]
+  __shared__ bool is_last;
+  const int tid = threadIdx.x;
+  const int j0 = blockIdx.x * RB;
+  const int ks = k + s, L = k * ks;
+  for (int e = tid; e < RB * NP; e += blockDim.x) {
+    const int r = e / NP, c = e % NP;
+    Zr[r * (NP + 1) + c] = j0 + r < n2 ? Z2[(int64_t)(j0 + r) * NP + c] : T(0);
+  }
+  __syncthreads();
+  for (int o = tid; o < L; o += blockDim.x) {
+    const int a = o % k, t = o / k;
+    T v = T(0);
+#pragma unroll 8
+    for (int r = 0; r < RB; ++r) v = fma(Zr[r * (NP + 1) + a], Zr[r * (NP + 1) + t], v);
+    part[(int64_t)blockIdx.x * L + o] = (double)v;
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) is_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  for (int o = tid; o < L; o += blockDim.x) {
+    double v = 0.0;
+    for (int c = 0; c < (int)gridDim.x; ++c) v += __ldcg(&part[(int64_t)c * L + o]);
+    const int a = o % k, t = o / k;
+    if (t < k) G[a + t * k] = (T)v;
+    else CV[a + (t - k) * k] = (T)v;
+  }
+  if (tid == 0) *ticket = 0u;
+}
+
 // --------------------------------------------------------------------------------
 // Fused row pass (steps a4 + a5), BM = 64 rows per block, 256 threads.
 //   Y = A2(rows,:) [C^T | V_s]                     (GEMM over n2, Z2 row-major n2 x NP)
@@ -694,12 +841,17 @@ __global__ void prep_rowpass(const T* __restrict__ C, const T* __restrict__ Vs, 
 constexpr int RP_BM = 64;
 constexpr int RP_BK = 32;
 
+// Shared memory of row_pass.  U (phase 2) reuses the phase-1 staging area; the rows of
+// X1old, A1 and W1 are staged in shared memory for float only (double reads them from
+// global memory to stay within the 227 KB limit at k = 64).
 template <typename T>
 struct RowPassSmem {
+  static constexpr bool kStage = sizeof(T) == 4;
   static size_t bytes(int NP, int k, int s) {
-    return sizeof(T) * ((size_t)RP_BK * RP_BM + (size_t)RP_BK * NP + (size_t)RP_BM * (NP + 1) +
-                        (size_t)k * k + (size_t)k * (s > 0 ? s : 1) +
-                        (size_t)RP_BM * (EIG_BMAX + 1));
+    const size_t stage = (size_t)RP_BK * RP_BM + (size_t)RP_BK * NP;
+    const size_t us = (size_t)RP_BM * (EIG_BMAX + 1);
+    return sizeof(T) * ((stage > us ? stage : us) + (size_t)RP_BM * (NP + 1) + (size_t)k * k +
+                        (size_t)k * (s > 0 ? s : 1) + (kStage ? 3 * (size_t)RP_BM * (k + 1) : 0));
   }
 };
 
@@ -710,48 +862,98 @@ row_pass(const T* __restrict__ A, int64_t lda, const T* __restrict__ W1, int64_t
          const T* __restrict__ CV, int m, int n2, int k, int s, int NP, T* __restrict__ X1new,
          double* __restrict__ wpart, int* __restrict__ err) {
   extern __shared__ unsigned char smem_raw[];
-  T* As = reinterpret_cast<T*>(smem_raw);   // [RP_BK][RP_BM]
-  T* Zs = As + RP_BK * RP_BM;               // [RP_BK][NP]
-  T* Ys = Zs + RP_BK * NP;                  // [RP_BM][NP+1]
+  constexpr bool kStage = RowPassSmem<T>::kStage;
+  const size_t stage_elems = (size_t)RP_BK * RP_BM + (size_t)RP_BK * NP;
+  const size_t us_elems = (size_t)RP_BM * (EIG_BMAX + 1);
+  T* As = reinterpret_cast<T*>(smem_raw);   // [RP_BK][RP_BM]           (phase 1)
+  T* Zs = As + RP_BK * RP_BM;               // [RP_BK][NP]              (phase 1)
+  T* Us = As;                               // [RP_BM][EIG_BMAX+1]      (phase 2, reuses As)
+  T* Ys = As + (stage_elems > us_elems ? stage_elems : us_elems);  // [RP_BM][NP+1]
   T* Gs = Ys + RP_BM * (NP + 1);            // [k][k]
   T* CVs = Gs + k * k;                      // [k][s]
-  T* Us = CVs + k * (s > 0 ? s : 1);        // [RP_BM][EIG_BMAX+1]
+  T* Xo = CVs + k * (s > 0 ? s : 1);        // [RP_BM][k+1]  X1old rows (float)
+  T* A1s = Xo + RP_BM * (k + 1);            // [RP_BM][k+1]  A1 rows    (float)
+  T* W1s = A1s + RP_BM * (k + 1);           // [RP_BM][k+1]  W1 rows    (float)
   __shared__ double sh[32];
 
   const int tid = threadIdx.x;
   const int i0 = blockIdx.x * RP_BM;
   const T* A2 = A + (int64_t)k * lda;
   const int NPU = NP / 16;
+  const int kp = k + 1;
+  // row r of the block, column a, of X1old / A1 / W1 (zero / one outside the matrix)
+  auto xo_at = [&](int r, int a) -> T {
+    if (kStage) return Xo[r * kp + a];
+    return i0 + r < m ? X1old[(i0 + r) + (int64_t)a * m] : T(0);
+  };
+  auto a1_at = [&](int r, int a) -> T {
+    if (kStage) return A1s[r * kp + a];
+    return i0 + r < m ? A[(i0 + r) + (int64_t)a * lda] : T(0);
+  };
+  auto w1_at = [&](int r, int a) -> T {
+    if (kStage) return W1s[r * kp + a];
+    return i0 + r < m ? W1[(i0 + r) + (int64_t)a * ldw] : T(1);
+  };
 
   for (int e = tid; e < k * k; e += 256) Gs[e] = Gm[e];
   for (int e = tid; e < k * s; e += 256) CVs[e] = CV[e];
+  if (kStage) {
+    // the block's rows of X1old, A1 and W1 (coalesced down each column)
+    for (int e = tid; e < RP_BM * k; e += 256) {
+      const int r = e % RP_BM, a = e / RP_BM;
+      const int i = i0 + r;
+      const bool ok = i < m;
+      Xo[r * kp + a] = ok ? X1old[i + (int64_t)a * m] : T(0);
+      A1s[r * kp + a] = ok ? A[i + (int64_t)a * lda] : T(0);
+      W1s[r * kp + a] = ok ? W1[i + (int64_t)a * ldw] : T(1);
+    }
+  }
 
-  // ---- phase 1: Y = A2 rows * Z2
+  // ---- phase 1: Y = A2 rows * Z2, slabs of 32 columns, next slab prefetched in registers
   {
-    const int rg = tid % 16, cg = tid / 16;
+    const int rg = tid % 16, cg = tid / 16;   // rows 4 rg .. 4 rg + 3, columns cg + 16 v
     T acc[4][6];
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
       for (int v = 0; v < 6; ++v) acc[u][v] = T(0);
-    for (int j0 = 0; j0 < n2; j0 += RP_BK) {
-      __syncthreads();
-      for (int e = tid; e < RP_BK * RP_BM; e += 256) {
+    constexpr int AQ = RP_BK * RP_BM / 256;   // 8 A2 elements per thread per slab
+    constexpr int ZQ = RP_BK * 96 / 256;      // up to 12 Z2 elements per thread per slab
+    T ra[AQ], rz[ZQ];
+    auto fetch = [&](int j0) {
+#pragma unroll
+      for (int q = 0; q < AQ; ++q) {
+        const int e = tid + 256 * q;
         const int r = e % RP_BM, kk = e / RP_BM;
         const int i = i0 + r, j = j0 + kk;
-        As[kk * RP_BM + r] = (i < m && j < n2) ? A2[i + (int64_t)j * lda] : T(0);
+        ra[q] = (i < m && j < n2) ? A2[i + (int64_t)j * lda] : T(0);
       }
-      for (int e = tid; e < RP_BK * NP; e += 256) {
-        const int kk = e / NP, c = e % NP;
-        const int j = j0 + kk;
-        Zs[kk * NP + c] = j < n2 ? Z2[(int64_t)j * NP + c] : T(0);
+#pragma unroll
+      for (int q = 0; q < ZQ; ++q) {
+        const int e = tid + 256 * q;
+        T v = T(0);
+        if (e < RP_BK * NP) {
+          const int j = j0 + e / NP;
+          v = j < n2 ? Z2[(int64_t)j0 * NP + e] : T(0);
+        }
+        rz[q] = v;
       }
+    };
+    if (n2 > 0) fetch(0);
+    for (int j0 = 0; j0 < n2; j0 += RP_BK) {
       __syncthreads();
+#pragma unroll
+      for (int q = 0; q < AQ; ++q) As[tid + 256 * q] = ra[q];
+#pragma unroll
+      for (int q = 0; q < ZQ; ++q)
+        if (tid + 256 * q < RP_BK * NP) Zs[tid + 256 * q] = rz[q];
+      __syncthreads();
+      if (j0 + RP_BK < n2) fetch(j0 + RP_BK);
 #pragma unroll 4
       for (int kk = 0; kk < RP_BK; ++kk) {
         T a[4], z[6];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) a[u] = As[kk * RP_BM + rg + 16 * u];
+        for (int u = 0; u < 4; ++u) a[u] = As[kk * RP_BM + 4 * rg + u];
 #pragma unroll
         for (int v = 0; v < 6; ++v) z[v] = v < NPU ? Zs[kk * NP + cg + 16 * v] : T(0);
 #pragma unroll
@@ -764,17 +966,15 @@ row_pass(const T* __restrict__ A, int64_t lda, const T* __restrict__ W1, int64_t
     for (int u = 0; u < 4; ++u)
 #pragma unroll
       for (int v = 0; v < 6; ++v)
-        if (v < NPU) Ys[(rg + 16 * u) * (NP + 1) + cg + 16 * v] = acc[u][v];
+        if (v < NPU) Ys[(4 * rg + u) * (NP + 1) + cg + 16 * v] = acc[u][v];
   }
   __syncthreads();
 
   // ---- phase 2a: U = Y_V - X1old C V_s
   for (int e = tid; e < RP_BM * s; e += 256) {
     const int r = e % RP_BM, c = e / RP_BM;
-    const int i = i0 + r;
     T v = Ys[r * (NP + 1) + k + c];
-    if (i < m)
-      for (int a = 0; a < k; ++a) v -= X1old[i + (int64_t)a * m] * CVs[a + c * k];
+    for (int a = 0; a < k; ++a) v -= xo_at(r, a) * CVs[a + c * k];
     Us[r * (EIG_BMAX + 1) + c] = v;
   }
   __syncthreads();
@@ -783,11 +983,10 @@ row_pass(const T* __restrict__ A, int64_t lda, const T* __restrict__ W1, int64_t
   double wsum = 0.0;
   for (int e = tid; e < RP_BM * k; e += 256) {
     const int r = e % RP_BM, a = e / RP_BM;
-    const int i = i0 + r;
-    if (i >= m) continue;
-    const T w = W1[i + (int64_t)a * ldw];
-    const T a1 = A[i + (int64_t)a * lda];
-    const T xo = X1old[i + (int64_t)a * m];
+    if (i0 + r >= m) continue;
+    const T w = w1_at(r, a);
+    const T a1 = a1_at(r, a);
+    const T xo = xo_at(r, a);
     T v = a1 * w * w + Ys[r * (NP + 1) + a];
     for (int c = 0; c < s; ++c) v -= Us[r * (EIG_BMAX + 1) + c] * CVs[a + c * k];
     Ys[r * (NP + 1) + a] = v;
@@ -812,8 +1011,8 @@ row_pass(const T* __restrict__ A, int64_t lda, const T* __restrict__ W1, int64_t
     const bool active = i < m;
     T c0[KMAX], c1[KMAX];
     T d0 = T(1), d1 = T(1);
-    if (active && j0c < k) { const T w = W1[i + (int64_t)j0c * ldw]; d0 = w * w; }
-    if (active && j1c < k) { const T w = W1[i + (int64_t)j1c * ldw]; d1 = w * w; }
+    if (j0c < k) { const T w = w1_at(r, j0c); d0 = w * w; }
+    if (j1c < k) { const T w = w1_at(r, j1c); d1 = w * w; }
 #pragma unroll
     for (int q = 0; q < KMAX; ++q) {
       c0[q] = (q < k && j0c < k) ? Gs[q + j0c * k] + (q == j0c ? d0 : T(0)) : (q == j0c ? T(1) : T(0));

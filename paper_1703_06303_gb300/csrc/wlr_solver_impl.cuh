@@ -30,26 +30,31 @@ class Solver final : public SolverBase {
     Q1_ = dalloc<T>((size_t)m * k);
     // chunking of the split-m Gram products
     ch_S1_ = chunking(m, 1);
-    ch_T_ = chunking(m, 1 * std::max(1, cdiv(n2, 64)));
+    ch_T_ = chunking(m, (size_t)cdiv(k + n2, 64));
     ch_K_ = chunking(m, (size_t)std::max(1, cdiv(n2, 64)) * std::max(1, cdiv(n2, 64)));
     const size_t L = (size_t)k * k + (size_t)k * n2;
     size_t part_elems = std::max((size_t)ch_S1_.nch * k * k, (size_t)ch_T_.nch * L);
     part_elems = std::max(part_elems, (size_t)ch_K_.nch * n2 * n2);
-    part_ = dalloc<T>(std::max<size_t>(part_elems, 1));
-    S1_ = dalloc<double>((size_t)k * k);
+    part64_ = dalloc<double>(std::max<size_t>(part_elems, 1));
     S2T_ = dalloc<double>(L);
-    R1_ = dalloc<T>((size_t)k * k);
     R1inv_ = dalloc<T>((size_t)k * k);
+    Nm_ = dalloc<T>((size_t)k * k);
+    Rinv_ = dalloc<T>((size_t)k * k);
     C_ = dalloc<T>(std::max<size_t>((size_t)k * n2, 1));
-    B_ = dalloc<T>(std::max<size_t>((size_t)k * n2, 1));
+    B64_ = dalloc<double>(std::max<size_t>((size_t)k * n2, 1));
+    Bh_ = dalloc<float>(std::max<size_t>((size_t)k * n2, 1));
+    Bl_ = dalloc<float>(std::max<size_t>((size_t)k * n2, 1));
     Z2_ = dalloc<T>(std::max<size_t>((size_t)n2 * NP, 1));
     Z2prev_ = dalloc<T>(std::max<size_t>((size_t)n2 * NP, 1));
-    nblk_coef_ = cdiv(n2, 64);
+    nblk_coef_ = cdiv(n2, 128);
     bpart_ = dalloc<double>(std::max(nblk_coef_, 1));
-    K_ = dalloc<T>(std::max<size_t>((size_t)n2 * n2, 1));
+    K64_ = dalloc<double>(std::max<size_t>((size_t)n2 * n2, 1));
     G2_ = dalloc<T>(std::max<size_t>((size_t)n2 * n2, 1));
+    nblk_prep_ = cdiv(n2, 64);
+    prep_part_ = dalloc<double>((size_t)std::max(nblk_prep_, 1) * k * (k + std::max(s, 0)));
+    prep_ticket_ = dalloc<unsigned int>(1);
     normA2_ = dalloc<double>(1);
-    nblk_eig_ = cdiv(n2, 32);
+    nblk_eig_ = cdiv(n2, 16);
     const int bb = std::max(b, 1);
     V_ = dalloc<T>((size_t)std::max(n2, 1) * bb);
     Zeig_ = dalloc<T>((size_t)std::max(n2, 1) * bb);
@@ -79,14 +84,20 @@ class Solver final : public SolverBase {
     WLR_CUDA(cudaMemsetAsync(CV_, 0, sizeof(T) * k * std::max(s, 1), stream_));
     WLR_CUDA(cudaMemsetAsync(CVprev_, 0, sizeof(T) * k * std::max(s, 1), stream_));
     WLR_CUDA(cudaMemsetAsync(bpart_, 0, sizeof(double) * std::max(nblk_coef_, 1), stream_));
+    WLR_CUDA(cudaMemsetAsync(prep_ticket_, 0, sizeof(unsigned int), stream_));
+    WLR_CUDA(cudaMemsetAsync(G_, 0, sizeof(T) * k * k, stream_));
     // dynamic shared memory limits
     set_smem((const void*)row_pass<T, 8>, RowPassSmem<T>::bytes(NP, k, s));
     set_smem((const void*)row_pass<T, 16>, RowPassSmem<T>::bytes(NP, k, s));
     set_smem((const void*)row_pass<T, 32>, RowPassSmem<T>::bytes(NP, k, s));
     set_smem((const void*)row_pass<T, 64>, RowPassSmem<T>::bytes(NP, k, s));
     set_smem((const void*)x2_pass<T>, x2_smem());
-    set_smem((const void*)coef_kernel<T>, 2 * sizeof(T) * k * k);
-    set_smem((const void*)chol_small<T>, 2 * sizeof(double) * k * k);
+    set_smem((const void*)coef_kernel2<T>, 2 * sizeof(T) * k * k);
+    set_smem((const void*)chol1_kernel<T>, sizeof(double) * (2 * k * k + k));
+    set_smem((const void*)chol2_kernel<T>, 3 * sizeof(T) * k * k);
+    set_smem((const void*)prep_gram<T>, sizeof(T) * 64 * (NP + 1));
+    eig_vsmem_ = (size_t)n2 * std::max(b, 1) * sizeof(T) <= 200 * 1024;
+    if (eig_vsmem_) set_smem((const void*)eig_mult<T, true>, (size_t)n2 * std::max(b, 1) * sizeof(T));
     WLR_CUDA(cudaStreamSynchronize(stream_));
   }
 
@@ -362,6 +373,7 @@ class Solver final : public SolverBase {
   static Chunk chunking(int m, size_t tiles) {
     const int target = 304;
     int nch = std::max<int>(1, (int)((target + tiles - 1) / std::max<size_t>(tiles, 1)));
+    nch = std::min(nch, 64);
     int rows = cdiv(m, nch);
     rows = std::max(32, ((rows + 31) / 32) * 32);
     nch = std::max(1, cdiv(m, rows));
@@ -529,27 +541,28 @@ class Solver final : public SolverBase {
   }
 
   // ------------------------------------------------------------------ kernels
-  void gemm_tn(const T* X, int64_t ldx, const T* Y, int64_t ldy, int P, int Q, T* part,
-               int64_t stride, int64_t offset, const Chunk& ch) {
+  // part64 <- chunked partials of X^T [Y1 Y2] (Y1: q1 columns, Y2: the rest)
+  void gram(const T* X, int64_t ldx, const T* Y1, int64_t ldy1, int q1, const T* Y2, int64_t ldy2,
+            int P, int Q, int64_t stride, const Chunk& ch) {
     if (P <= 0 || Q <= 0) return;
     const int m = d_.m;
-    Prof pf(this, "gemm_tn_partial");
+    Prof pf(this, "gram_tn");
     if (P <= 32 && Q <= 32) {
       dim3 g(cdiv(P, 32), cdiv(Q, 32), ch.nch);
-      gemm_tn_partial<T, 32, 32><<<g, 64, 0, stream_>>>(X, ldx, Y, ldy, m, P, Q, ch.rows, part, stride, offset);
+      gram_tn<T, 32, 32><<<g, 64, 0, stream_>>>(X, ldx, Y1, ldy1, q1, Y2, ldy2, m, P, Q, ch.rows, part64_, stride, 0);
     } else if (P <= 32) {
       dim3 g(cdiv(P, 32), cdiv(Q, 64), ch.nch);
-      gemm_tn_partial<T, 32, 64><<<g, 128, 0, stream_>>>(X, ldx, Y, ldy, m, P, Q, ch.rows, part, stride, offset);
+      gram_tn<T, 32, 64><<<g, 128, 0, stream_>>>(X, ldx, Y1, ldy1, q1, Y2, ldy2, m, P, Q, ch.rows, part64_, stride, 0);
     } else {
       dim3 g(cdiv(P, 64), cdiv(Q, 64), ch.nch);
-      gemm_tn_partial<T, 64, 64><<<g, 256, 0, stream_>>>(X, ldx, Y, ldy, m, P, Q, ch.rows, part, stride, offset);
+      gram_tn<T, 64, 64><<<g, 256, 0, stream_>>>(X, ldx, Y1, ldy1, q1, Y2, ldy2, m, P, Q, ch.rows, part64_, stride, 0);
     }
     count(1);
   }
-  void reduce(const T* part, int64_t stride, int nch, int64_t len, double* out64, T* outT) {
+  void reduce64(int64_t stride, int nch, int64_t len, double* out64) {
     if (len <= 0) return;
     Prof pf(this, "reduce_partials");
-    reduce_partials<T><<<grid1d(len), 256, 0, stream_>>>(part, stride, nch, len, out64, outT);
+    reduce_partials<double><<<grid1d(len), 256, 0, stream_>>>(part64_, stride, nch, len, out64, nullptr);
     count(1);
   }
 
@@ -565,8 +578,8 @@ class Solver final : public SolverBase {
     sumsq_partial<T><<<nb, 256, 0, stream_>>>(A2, lda_, m, n2, wpart_scratch(nb));
     reduce_partials<double><<<1, 32, 0, stream_>>>(wpart_scratch(nb), 1, nb, 1, normA2_, nullptr);
     count(2);
-    gemm_tn(A2, lda_, A2, lda_, n2, n2, part_, (int64_t)n2 * n2, 0, ch_K_);
-    reduce(part_, (int64_t)n2 * n2, ch_K_.nch, (int64_t)n2 * n2, nullptr, K_);
+    gram(A2, lda_, A2, lda_, n2, nullptr, 0, n2, n2, (int64_t)n2 * n2, ch_K_);
+    reduce64((int64_t)n2 * n2, ch_K_.nch, (int64_t)n2 * n2, K64_);
   }
   double* wpart_scratch(int n) {
     if (!sumsq_part_) sumsq_part_ = dalloc<double>(std::max(n, 304));
@@ -578,11 +591,10 @@ class Solver final : public SolverBase {
     const int m = d_.m, k = d_.k, n2 = d_.n2, NP = d_.NP;
     const T* X1 = X1buf_[xi];
     const T* A2 = A_ + (int64_t)k * lda_;
-    gemm_tn(X1, m, X1, m, k, k, part_, (int64_t)k * k, 0, ch_S1_);
-    reduce(part_, (int64_t)k * k, ch_S1_.nch, (int64_t)k * k, S1_, nullptr);
+    gram(X1, m, X1, m, k, nullptr, 0, k, k, (int64_t)k * k, ch_S1_);
     {
-      Prof pf(this, "chol_small");
-      chol_small<T><<<1, 64, 2 * sizeof(double) * k * k, stream_>>>(S1_, k, R1_, R1inv_, err_);
+      Prof pf(this, "chol1");
+      chol1_kernel<T><<<1, 256, sizeof(double) * (2 * k * k + k), stream_>>>(part64_, ch_S1_.nch, k, R1inv_, err_);
     }
     {
       Prof pf(this, "form_q");
@@ -590,13 +602,17 @@ class Solver final : public SolverBase {
     }
     count(2);
     const int64_t L = (int64_t)k * k + (int64_t)k * n2;
-    gemm_tn(Q1_, m, Q1_, m, k, k, part_, L, 0, ch_T_);
-    gemm_tn(Q1_, m, A2, lda_, k, n2, part_, L, (int64_t)k * k, ch_T_);
-    reduce(part_, L, ch_T_.nch, L, S2T_, nullptr);
+    gram(Q1_, m, Q1_, m, k, A2, lda_, k, k + n2, L, ch_T_);
+    reduce64(L, ch_T_.nch, L, S2T_);
+    {
+      Prof pf(this, "chol2");
+      chol2_kernel<T><<<1, 256, 3 * sizeof(T) * k * k, stream_>>>(S2T_, k, R1inv_, Nm_, Rinv_, err_);
+    }
+    count(1);
     if (n2 > 0) {
-      Prof pf(this, "coef_kernel");
-      coef_kernel<T><<<nblk_coef_, 64, 2 * sizeof(T) * k * k, stream_>>>(
-          S2T_, S2T_ + (int64_t)k * k, R1_, k, n2, NP, C_, B_, Z2_, bpart_, err_);
+      Prof pf(this, "coef");
+      coef_kernel2<T><<<nblk_coef_, 128, 2 * sizeof(T) * k * k, stream_>>>(
+          S2T_ + (int64_t)k * k, Nm_, Rinv_, k, n2, NP, C_, B64_, Bh_, Bl_, Z2_, bpart_);
       count(1);
     }
   }
@@ -604,18 +620,21 @@ class Solver final : public SolverBase {
     const int n2 = d_.n2;
     dim3 g(cdiv(n2, 32), cdiv(n2, 32));
     Prof pf(this, "form_g2");
-    form_g2<T><<<g, 256, 0, stream_>>>(K_, B_, d_.k, n2, G2_);
+    form_g2_df<T><<<g, 256, 0, stream_>>>(K64_, B64_, Bh_, Bl_, d_.k, n2, G2_);
     count(1);
   }
   void eig_iteration() {
     const int n2 = d_.n2, b = d_.b, s = d_.s;
     {
       Prof pf(this, "eig_mult");
-      eig_mult<T><<<nblk_eig_, 256, 0, stream_>>>(G2_, V_, n2, b, Zeig_, eigpart_);
+      if (eig_vsmem_)
+        eig_mult<T, true><<<nblk_eig_, 256, (size_t)n2 * b * sizeof(T), stream_>>>(G2_, V_, n2, b, Zeig_, eigpart_);
+      else
+        eig_mult<T, false><<<nblk_eig_, 256, 0, stream_>>>(G2_, V_, n2, b, Zeig_, eigpart_);
     }
     {
       Prof pf(this, "eig_small");
-      eig_small<T><<<1, 512, 0, stream_>>>(eigpart_, nblk_eig_, b, sizeof(T) == 4 ? 12 : 24, Y_, Mv_, Mz_,
+      eig_small<T><<<1, 512, 0, stream_>>>(eigpart_, nblk_eig_, b, sizeof(T) == 4 ? 8 : 20, Y_, Mv_, Mz_,
                                           theta_, resid_, err_);
     }
     Prof pf(this, "eig_update");
@@ -628,8 +647,11 @@ class Solver final : public SolverBase {
     count(1);
   }
   void prep() {
-    Prof pf(this, "prep_rowpass");
-    prep_rowpass<T><<<d_.k, 128, 0, stream_>>>(C_, Vs_, d_.k, d_.n2, d_.s, G_, CV_);
+    const int k = d_.k, n2 = d_.n2, s = d_.s, NP = d_.NP;
+    if (n2 == 0) return;  // G = 0 (cleared at construction), CV unused
+    Prof pf(this, "prep_gram");
+    prep_gram<T><<<nblk_prep_, 256, sizeof(T) * 64 * (NP + 1), stream_>>>(Z2_, n2, k, s, NP, prep_part_,
+                                                                        prep_ticket_, G_, CV_);
     count(1);
   }
   // steps a1..a3 (+ the small products for a4/a5) for X1 = X1buf_[xi]
@@ -768,11 +790,15 @@ class Solver final : public SolverBase {
   std::vector<double> rel_err_hist_;
 
   T* X1buf_[3] = {nullptr, nullptr, nullptr};
-  T *Q1_ = nullptr, *part_ = nullptr, *R1_ = nullptr, *R1inv_ = nullptr;
-  double *S1_ = nullptr, *S2T_ = nullptr;
-  T *C_ = nullptr, *B_ = nullptr, *Z2_ = nullptr, *Z2prev_ = nullptr;
-  double* bpart_ = nullptr;
-  T *K_ = nullptr, *G2_ = nullptr;
+  T *Q1_ = nullptr, *R1inv_ = nullptr, *Nm_ = nullptr, *Rinv_ = nullptr;
+  double *part64_ = nullptr, *S2T_ = nullptr;
+  T *C_ = nullptr, *Z2_ = nullptr, *Z2prev_ = nullptr;
+  double *B64_ = nullptr, *bpart_ = nullptr, *K64_ = nullptr, *prep_part_ = nullptr;
+  float *Bh_ = nullptr, *Bl_ = nullptr;
+  unsigned int* prep_ticket_ = nullptr;
+  int nblk_prep_ = 0;
+  bool eig_vsmem_ = false;
+  T* G2_ = nullptr;
   double* normA2_ = nullptr;
   T *V_ = nullptr, *Zeig_ = nullptr, *eigpart_ = nullptr, *Y_ = nullptr, *Mv_ = nullptr, *Mz_ = nullptr;
   T *theta_ = nullptr, *resid_ = nullptr, *Vs_ = nullptr;
