@@ -84,7 +84,7 @@ typedef struct {
   int32_t stop;           /* wlr_stop (default WLR_STOP_RELATIVE)                        */
   int32_t eig_block;      /* subspace block size b >= r-k for the rank-(r-k) SVD step;  */
                           /* 0 = min(n-k, 32, max(r-k+8, 2(r-k)))                      */
-  int32_t eig_iters;      /* subspace iterations per sWLR iteration (warm start); 0 = 2 */
+  int32_t eig_iters;      /* subspace iterations per sWLR iteration (warm start); 0 = 1 */
   int32_t eig_iters_cold; /* subspace iterations from a cold start; 0 = 40              */
   int32_t use_graph;      /* capture one iteration in a CUDA graph and replay it (1)    */
   uint64_t seed;          /* seed of the random subspace start (and WLR_INIT_RANDOM)     */

@@ -70,7 +70,7 @@ wlr_status wlr_create(wlr_handle* out, int64_t m, int64_t n, int64_t k, int64_t 
     return fail(nullptr, WLR_ERR_INVALID_ARG, "unknown precision");
   if (o.stop < WLR_STOP_PAPER || o.stop > WLR_STOP_OBJECTIVE)
     return fail(nullptr, WLR_ERR_INVALID_ARG, "unknown stop rule");
-  if (o.eig_iters <= 0) o.eig_iters = 2;
+  if (o.eig_iters <= 0) o.eig_iters = 1;
   if (o.eig_iters_cold <= 0) o.eig_iters_cold = 40;
   wlr::Dims d;
   d.m = (int)m;

@@ -28,47 +28,157 @@ namespace wlr {
 constexpr int EIG_BMAX = 32;   // largest subspace block (Jacobi size)
 
 // --------------------------------------------------------------------------------
+// Asynchronous global -> shared copies of one element (zero-filled when !ok).
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* dst_smem, const T* src, bool ok) {
+  const unsigned dst = (unsigned)__cvta_generic_to_shared(dst_smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(dst), "l"(src),
+               "n"(sizeof(T)), "r"(ok ? (int)sizeof(T) : 0));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// Four consecutive shared-memory elements (one 16-byte load for float).
+__device__ __forceinline__ void load4(float (&a)[4], const float* p) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  a[0] = v.x; a[1] = v.y; a[2] = v.z; a[3] = v.w;
+}
+__device__ __forceinline__ void load4(double (&a)[4], const double* p) {
+  a[0] = p[0]; a[1] = p[1]; a[2] = p[2]; a[3] = p[3];
+}
+
+// 1/sqrt(x): hardware estimate plus one Newton step (float); IEEE for double.
+__device__ __forceinline__ float wrsqrt(float x) {
+  float r = rsqrtf(x);
+  return r * (1.5f - 0.5f * x * r * r);
+}
+__device__ __forceinline__ double wrsqrt(double x) { return 1.0 / sqrt(x); }
+
+// Error-free transformations (Dekker 1971; Knuth TAOCP vol. 2, 4.2.2):
+// a + b = s + e exactly (TwoSum).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bp = s - a;
+  const float ap = s - bp;
+  e = (a - ap) + (b - bp);
+}
+
+// Running sum that keeps about twice the working precision: float hi + lo pairs
+// (TwoSum) for T = float, a plain double for T = double.
+template <typename T>
+struct WideAcc;
+template <>
+struct WideAcc<float> {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    float s, e;
+    two_sum(hi, x, s, e);
+    hi = s;
+    lo += e;
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+template <>
+struct WideAcc<double> {
+  double v = 0.0;
+  __device__ __forceinline__ void add(double x) { v += x; }
+  __device__ __forceinline__ double value() const { return v; }
+};
+
 // Split-m Gram product with hierarchical accumulation:
 //   part[off + c*stride + a + b*P] = sum_{i in rows of chunk c} X[i, a] * Y[i, b]
 // for a < P, b < Q, where column b of Y is Y1[:, b] for b < q1 and Y2[:, b - q1] after
-// (a virtual concatenation [Y1 Y2]).  Each 32-row slab is summed in T, then added to a
-// double accumulator, so the cross-slab sum keeps FP64 accuracy while the inner
-// products run at the T rate.  One (PT x QT) output tile per block; thread (tx, ty)
-// owns rows ty + (PT/4) u and columns tx + (QT/4) v (conflict-free shared reads).
-template <typename T, int PT, int QT>
+// (a virtual concatenation [Y1 Y2]).  With Rq != nullptr the X operand and Y1 are
+// Q1 = X R^{-1} formed on the fly per 32-row slab (Rq: upper P x P, so q1 = P).
+// Each 32-row slab is summed in T, then added to a WideAcc, so the cross-slab sum keeps
+// about FP64 accuracy while the inner products run at the T rate.  The next slab is
+// prefetched into registers.  One (PT x QT) output tile per block; thread (tx, ty) owns
+// rows ty + (PT/4) u and columns tx + (QT/4) v (conflict-free shared reads).
+template <typename T, int PT, int QT, bool FUSE>
 __global__ void __launch_bounds__((PT / 4) * (QT / 4))
 gram_tn(const T* __restrict__ X, int64_t ldx, const T* __restrict__ Y1, int64_t ldy1, int q1,
-        const T* __restrict__ Y2, int64_t ldy2, int m, int P, int Q, int chunk_rows,
-        double* __restrict__ part, int64_t part_stride, int64_t part_offset) {
+        const T* __restrict__ Y2, int64_t ldy2, const T* __restrict__ Rq, int m, int P, int Q,
+        int chunk_rows, double* __restrict__ part, int64_t part_stride, int64_t part_offset) {
   constexpr int BK = 32;
   constexpr int NTX = QT / 4, NTY = PT / 4, NT = NTX * NTY;
+  constexpr int XQ = BK * PT / NT, YQ = BK * QT / NT;
   __shared__ T Xs[BK][PT + 1];
   __shared__ T Ys[BK][QT + 1];
+  __shared__ T Xraw[FUSE ? BK : 1][FUSE ? PT + 1 : 1];   // raw X1 slab (FUSE)
+  __shared__ T Rs[FUSE ? PT : 1][FUSE ? PT + 1 : 1];     // R^{-1} (FUSE)
+  constexpr bool fuse_q = FUSE;
   const int a0 = blockIdx.x * PT, b0 = blockIdx.y * QT, c = blockIdx.z;
   const int i_begin = c * chunk_rows;
   const int i_end = min(m, i_begin + chunk_rows);
   const int tx = threadIdx.x % NTX, ty = threadIdx.x / NTX;
-  double acc[4][4];
+  // in the fused form every block needs the whole Q1 slab (a0 must be 0: P <= PT)
+  if (fuse_q)
+    for (int e = threadIdx.x; e < PT * PT; e += NT) {
+      const int r = e % PT, q = e / PT;
+      Rs[FUSE ? r : 0][FUSE ? q : 0] = (r < P && q < P) ? Rq[r + q * P] : T(0);
+    }
+  WideAcc<T> acc[4][4];
+  T rx[XQ], ry[YQ];
+  auto fetch = [&](int i0) {
 #pragma unroll
-  for (int u = 0; u < 4; ++u)
-#pragma unroll
-    for (int v = 0; v < 4; ++v) acc[u][v] = 0.0;
-
-  for (int i0 = i_begin; i0 < i_end; i0 += BK) {
-    for (int e = threadIdx.x; e < BK * PT; e += NT) {
+    for (int q = 0; q < XQ; ++q) {
+      const int e = threadIdx.x + NT * q;
       const int kk = e % BK, a = e / BK;
       const int i = i0 + kk, ga = a0 + a;
-      Xs[kk][a] = (i < i_end && ga < P) ? X[i + (int64_t)ga * ldx] : T(0);
+      rx[q] = (i < i_end && ga < P) ? X[i + (int64_t)ga * ldx] : T(0);
     }
-    for (int e = threadIdx.x; e < BK * QT; e += NT) {
+#pragma unroll
+    for (int q = 0; q < YQ; ++q) {
+      const int e = threadIdx.x + NT * q;
       const int kk = e % BK, b = e / BK;
       const int i = i0 + kk, gb = b0 + b;
       T v = T(0);
-      if (i < i_end && gb < Q)
+      if (i < i_end && gb < Q && !(fuse_q && gb < q1))
         v = gb < q1 ? Y1[i + (int64_t)gb * ldy1] : Y2[i + (int64_t)(gb - q1) * ldy2];
-      Ys[kk][b] = v;
+      ry[q] = v;
+    }
+  };
+  if (i_begin < i_end) fetch(i_begin);
+  for (int i0 = i_begin; i0 < i_end; i0 += BK) {
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < XQ; ++q) {
+      const int e = threadIdx.x + NT * q;
+      if (fuse_q) Xraw[FUSE ? e % BK : 0][FUSE ? e / BK : 0] = rx[q];
+      else Xs[e % BK][e / BK] = rx[q];
+    }
+#pragma unroll
+    for (int q = 0; q < YQ; ++q) {
+      const int e = threadIdx.x + NT * q;
+      Ys[e % BK][e / BK] = ry[q];
     }
     __syncthreads();
+    if (i0 + BK < i_end) fetch(i0 + BK);
+    if (fuse_q) {
+      // Q1 slab = X1 slab * R^{-1} (upper), written to Xs and to the Q1 columns of Ys;
+      // each thread carries XQ independent dot products through the l loop
+      T qv[XQ];
+#pragma unroll
+      for (int q = 0; q < XQ; ++q) qv[q] = T(0);
+      for (int l = 0; l < P; ++l) {
+#pragma unroll
+        for (int q = 0; q < XQ; ++q) {
+          const int e = threadIdx.x + NT * q;
+          const int kk = e % BK, a = e / BK;
+          if (l <= a) qv[q] = fma(Xraw[FUSE ? kk : 0][FUSE ? l : 0], Rs[FUSE ? l : 0][FUSE ? a : 0], qv[q]);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < XQ; ++q) {
+        const int e = threadIdx.x + NT * q;
+        const int kk = e % BK, a = e / BK;
+        Xs[kk][a] = qv[q];
+        const int gb = a - b0;
+        if (gb >= 0 && gb < QT && a < q1) Ys[kk][gb] = qv[q];
+      }
+      __syncthreads();
+    }
     T sl[4][4];
 #pragma unroll
     for (int u = 0; u < 4; ++u)
@@ -89,8 +199,7 @@ gram_tn(const T* __restrict__ X, int64_t ldx, const T* __restrict__ Y1, int64_t 
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
-      for (int v = 0; v < 4; ++v) acc[u][v] += (double)sl[u][v];
-    __syncthreads();
+      for (int v = 0; v < 4; ++v) acc[u][v].add(sl[u][v]);
   }
   double* out = part + part_offset + (int64_t)c * part_stride;
 #pragma unroll
@@ -99,7 +208,7 @@ gram_tn(const T* __restrict__ X, int64_t ldx, const T* __restrict__ Y1, int64_t 
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
       const int b = b0 + tx + NTX * v;
-      if (a < P && b < Q) out[a + (int64_t)b * P] = acc[u][v];
+      if (a < P && b < Q) out[a + (int64_t)b * P] = acc[u][v].value();
     }
   }
 }
@@ -194,15 +303,21 @@ chol1_kernel(const double* __restrict__ part, int nch, int k, T* __restrict__ R1
   }
   if (tid == 0) flag = 0;
   __syncthreads();
+  __shared__ double rpiv;
   for (int t = 0; t < k; ++t) {
     if (tid == 0) {
       double d = L[t + t * k];
       if (!(d > 1e-13 * dg[t]) || !isfinite(d)) { flag = 1; d = 1.0; }
-      L[t + t * k] = sqrt(d);
+      // 1/sqrt(d): float estimate, two Newton steps in double (error ~1e-16)
+      double r = (double)rsqrtf((float)d);
+      r = r * (1.5 - 0.5 * d * r * r);
+      r = r * (1.5 - 0.5 * d * r * r);
+      L[t + t * k] = d * r;
+      rpiv = r;
     }
     __syncthreads();
-    const double piv = L[t + t * k];
-    for (int i = t + 1 + tid; i < k; i += nt) L[i + t * k] /= piv;
+    const double rp = rpiv;
+    for (int i = t + 1 + tid; i < k; i += nt) L[i + t * k] *= rp;
     __syncthreads();
     const int w = k - t - 1;
     for (int e = tid; e < w * w; e += nt) {
@@ -212,12 +327,21 @@ chol1_kernel(const double* __restrict__ part, int nch, int k, T* __restrict__ R1
     __syncthreads();
   }
   if (flag && tid == 0) atomicOr(err, ERRBIT_RANK_DEFICIENT);
+  // reciprocals of the diagonal: float estimate + two Newton steps in double
+  for (int a = tid; a < k; a += nt) {
+    const double d = L[a + a * k];
+    double r = (double)(1.0f / (float)d);
+    r = r * (2.0 - d * r);
+    r = r * (2.0 - d * r);
+    dg[a] = r;
+  }
+  __syncthreads();
   // R1^{-1}: column c solves R1 x = e_c (R1(a,l) = L(l,a)), one thread per column.
   for (int c = tid; c < k; c += nt) {
     for (int a = k - 1; a >= 0; --a) {
       double v = a == c ? 1.0 : 0.0;
       for (int l = a + 1; l <= c; ++l) v -= L[l + a * k] * Ri[l + c * k];
-      Ri[a + c * k] = a <= c ? v / L[a + a * k] : 0.0;
+      Ri[a + c * k] = a <= c ? v * dg[a] : 0.0;
     }
   }
   __syncthreads();
@@ -233,17 +357,22 @@ chol1_kernel(const double* __restrict__ part, int nch, int k, T* __restrict__ R1
 // Rinv = R1^{-1} (I + N)^T = (R2 R1)^{-1}, the inverse of the full triangular factor.
 template <typename T>
 __global__ void __launch_bounds__(256)
-chol2_kernel(const double* __restrict__ S2, int k, const T* __restrict__ R1inv,
-             T* __restrict__ Nout, T* __restrict__ Rinv, int* __restrict__ err) {
+chol2_kernel(const double* __restrict__ part, int nch, int64_t pstride, int k,
+             const T* __restrict__ R1inv, T* __restrict__ Nout, T* __restrict__ Rinv,
+             int* __restrict__ err) {
   extern __shared__ unsigned char smem_raw[];
   T* F = reinterpret_cast<T*>(smem_raw);  // k*k lower (col-major)
   T* Nm = F + k * k;                       // k*k lower
   T* Ri1 = Nm + k * k;                     // k*k upper
   __shared__ int flag;
   const int tid = threadIdx.x, nt = blockDim.x;
+  // S2 = Q1^T Q1: the leading k x k block of the nch chunk partials (fixed order)
   for (int e = tid; e < k * k; e += nt) {
     const int i = e % k, j = e / k;
-    F[e] = i >= j ? (T)(S2[e] - (i == j ? 1.0 : 0.0)) : T(0);
+    double v = 0.0;
+    if (i >= j)
+      for (int c = 0; c < nch; ++c) v += part[(int64_t)c * pstride + e];
+    F[e] = i >= j ? (T)(v - (i == j ? 1.0 : 0.0)) : T(0);
     Ri1[e] = R1inv[e];
   }
   if (tid == 0) flag = 0;
@@ -265,6 +394,9 @@ chol2_kernel(const double* __restrict__ S2, int k, const T* __restrict__ R1inv,
     __syncthreads();
   }
   if (flag && tid == 0) atomicOr(err, ERRBIT_RANK_DEFICIENT);
+  __shared__ T rdiag[64];
+  for (int a = tid; a < k; a += nt) rdiag[a] = T(1) / (T(1) + F[a + a * k]);
+  __syncthreads();
   // (I + F) N = -F, column c by forward substitution (N lower)
   for (int c = tid; c < k; c += nt) {
     for (int a = 0; a < k; ++a) {
@@ -272,7 +404,7 @@ chol2_kernel(const double* __restrict__ S2, int k, const T* __restrict__ R1inv,
       if (a >= c) {
         v = -F[a + c * k];
         for (int l = c; l < a; ++l) v -= F[a + l * k] * Nm[l + c * k];
-        v /= (T(1) + F[a + a * k]);
+        v *= rdiag[a];
       }
       Nm[a + c * k] = v;
     }
@@ -358,15 +490,80 @@ coef_kernel2(const double* __restrict__ QtA2, const T* __restrict__ Nm, const T*
   if (threadIdx.x == 0) bnorm_part[blockIdx.x] = bn;
 }
 
-// Error-free transformations (Dekker 1971; Knuth TAOCP vol. 2, 4.2.2):
-// a + b = s + e exactly (TwoSum) and a * b = p + e exactly (TwoProduct via fma).
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = a + b;
-  const float bp = s - a;
-  const float ap = s - bp;
-  e = (a - ap) + (b - bp);
+// Coefficient step, one warp per column j of A2 (lanes over the k coefficients):
+//   t = (Q1^T A2)(:,j) summed from the chunk partials in double,
+//   B(:,j) = R2^{-T} t = t + N t  (t kept in double, the small N t in T)
+//   C(:,j) = R^{-1} B(:,j)
+// Writes C (k x n2, T), B in double and as float hi + lo (for the double-float Gram),
+// the C^T part of Z2 (row j: Z2[j*NP + a] = C(a,j)) and the block's ||B||_F^2.
+template <typename T>
+__global__ void __launch_bounds__(256)
+coef_kernel3(const double* __restrict__ part, int nch, int64_t pstride,
+             const T* __restrict__ Nm, const T* __restrict__ Rinv,
+             int k, int n2, int NP, T* __restrict__ Cout, double* __restrict__ B64,
+             float* __restrict__ Bh, float* __restrict__ Bl, T* __restrict__ Z2,
+             double* __restrict__ bnorm_part) {
+  extern __shared__ unsigned char smem_raw[];
+  T* Ns = reinterpret_cast<T*>(smem_raw);   // k*k
+  T* Rs = Ns + k * k;                       // k*k
+  T* tw = Rs + k * k;                       // [8][64] per-warp t
+  T* bw = tw + 8 * 64;                      // [8][64] per-warp B
+  __shared__ double sh[32];
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+    Ns[e] = Nm[e];
+    Rs[e] = Rinv[e];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int j = blockIdx.x * 8 + w;
+  double bn = 0.0;
+  if (j < n2) {
+    double t64[2] = {0.0, 0.0};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int a = lane + 32 * h;
+      if (a < k) {
+        // (Q1^T A2)(a, j): column k + j of the k x (k + n2) chunk partials
+        const int64_t o = a + (int64_t)(k + j) * k;
+        double v = 0.0;
+        for (int c = 0; c < nch; ++c) v += part[(int64_t)c * pstride + o];
+        t64[h] = v;
+        tw[w * 64 + a] = (T)v;
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int a = lane + 32 * h;
+      if (a < k) {
+        T corr = T(0);
+        for (int l = 0; l <= a; ++l) corr = fma(Ns[a + l * k], tw[w * 64 + l], corr);
+        const double b = t64[h] + (double)corr;
+        B64[a + (int64_t)j * k] = b;
+        const float hi = (float)b;
+        Bh[a + (int64_t)j * k] = hi;
+        Bl[a + (int64_t)j * k] = (float)(b - (double)hi);
+        bw[w * 64 + a] = (T)b;
+        bn += b * b;
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int a = lane + 32 * h;
+      if (a < k) {
+        T cv = T(0);
+        for (int l = a; l < k; ++l) cv = fma(Rs[a + l * k], bw[w * 64 + l], cv);
+        Cout[a + (int64_t)j * k] = cv;
+        Z2[(int64_t)j * NP + a] = cv;
+      }
+    }
+  }
+  bn = block_sum_double(bn, sh);
+  if (threadIdx.x == 0) bnorm_part[blockIdx.x] = bn;
 }
 
+// a * b = p + e exactly (TwoProduct via fma, Dekker 1971).
 // G2 = K - B^T B (n2 x n2), 32x32 tile per block, 256 threads (4 entries each).
 // FP32 path: sum_a B_ai B_aj in double-float arithmetic from B = hi + lo (the dropped
 // lo*lo term is below 2^-48 relative), then K (double) minus it in double, rounded
@@ -432,8 +629,8 @@ form_g2_df(const double* __restrict__ K64, const double* __restrict__ B64,
 template <typename T, bool VSMEM>
 __global__ void __launch_bounds__(256)
 eig_mult(const T* __restrict__ G2, const T* __restrict__ V, int n2, int b, T* __restrict__ Z,
-         T* __restrict__ part) {
-  constexpr int RB = 16;
+         T* __restrict__ part, unsigned int* __restrict__ ticket, double* __restrict__ HP) {
+  constexpr int RB = 8;   // one row of Z per warp
   extern __shared__ unsigned char smem_raw[];
   T* Vt = reinterpret_cast<T*>(smem_raw);  // [b][n2] when VSMEM
   __shared__ T Zs[RB][EIG_BMAX + 1];
@@ -451,6 +648,7 @@ eig_mult(const T* __restrict__ G2, const T* __restrict__ V, int n2, int b, T* __
 #pragma unroll
     for (int c = 0; c < EIG_BMAX; ++c) acc[c] = T(0);
     if (j < n2) {
+#pragma unroll 4
       for (int l = lane; l < n2; l += 32) {
         const T g = G2[l + (int64_t)j * n2];
 #pragma unroll
@@ -485,10 +683,24 @@ eig_mult(const T* __restrict__ G2, const T* __restrict__ V, int n2, int b, T* __
     out[e] = h;
     out[b * b + e] = p;
   }
+  // the last block to finish adds the partials in block order (no block waits)
+  __shared__ bool is_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  for (int e = threadIdx.x; e < 2 * b * b; e += blockDim.x) {
+    double v = 0.0;
+    for (int c = 0; c < (int)gridDim.x; ++c) v += (double)__ldcg(&part[(int64_t)c * 2 * b * b + e]);
+    HP[e] = v;
+  }
+  if (threadIdx.x == 0) *ticket = 0u;
 }
 
-// Subspace iteration, small step (one block of 512 threads, b <= 32):
-//  1. H = V^T G2 V, P = Z^T Z from the partials (double sums).
+// Subspace iteration, small step (one block of 128 threads, b <= 32):
+//  1. H = V^T G2 V and P = Z^T Z (b x b, summed by the last eig_mult block).
 //  2. Rayleigh-Ritz: H = Y Theta Y^T by the parallel cyclic Jacobi method (round-robin
 //     ordering, b/2 disjoint rotations per round), sorted descending.
 //  3. Next basis W = [V Y F_v + Z Y F_z], F_z = diag(1/||Z y_c||) for the columns with a
@@ -499,8 +711,8 @@ eig_mult(const T* __restrict__ G2, const T* __restrict__ V, int n2, int b, T* __
 // Outputs (T, b x b col-major): Y, Mv, Mz; theta (b, descending); resid (b): estimate of
 // ||G2 v_c - theta_c v_c||^2 = (Y^T P Y)_cc - theta_c^2.
 template <typename T>
-__global__ void __launch_bounds__(512)
-eig_small(const T* __restrict__ part, int nblk, int b, int max_sweeps, T* __restrict__ Yout,
+__global__ void __launch_bounds__(128)
+eig_small(const double* __restrict__ HP, int b, int max_sweeps, T* __restrict__ Yout,
           T* __restrict__ Mv, T* __restrict__ Mz, T* __restrict__ theta,
           T* __restrict__ resid, int* __restrict__ err) {
   constexpr int BM = EIG_BMAX;
@@ -512,24 +724,19 @@ eig_small(const T* __restrict__ part, int nblk, int b, int max_sweeps, T* __rest
   __shared__ int pairs[BM / 2][2];
   __shared__ int perm[BM];
   __shared__ T th[BM];
-  __shared__ int flag;
-  __shared__ double sh[32];
-  const int tid = threadIdx.x, nt = blockDim.x;
+  __shared__ T fz[BM];
+  __shared__ int usev[BM];
+  const int lane = threadIdx.x, NT = blockDim.x;
+  __shared__ T red[2][4];
   const int bb = b * b;
-  for (int e = tid; e < bb; e += nt) {
-    double h = 0.0, p = 0.0;
-    for (int c = 0; c < nblk; ++c) {
-      h += (double)part[(int64_t)c * 2 * bb + e];
-      p += (double)part[(int64_t)c * 2 * bb + bb + e];
-    }
+  for (int e = lane; e < bb; e += NT) {
     const int r = e % b, q = e / b;
-    H[r][q] = (T)h;
-    P[r][q] = (T)p;
+    H[r][q] = (T)HP[e];
+    P[r][q] = (T)HP[bb + e];
     Y[r][q] = r == q ? T(1) : T(0);
   }
   __syncthreads();
-  // symmetrise H
-  for (int e = tid; e < bb; e += nt) {
+  for (int e = lane; e < bb; e += NT) {
     const int r = e % b, q = e / b;
     if (r < q) {
       const T v = T(0.5) * (H[r][q] + H[q][r]);
@@ -538,125 +745,121 @@ eig_small(const T* __restrict__ part, int nblk, int b, int max_sweeps, T* __rest
     }
   }
   __syncthreads();
-  // ---- parallel Jacobi
-  const int N = (b + 1) & ~1;  // even number of players (index b is a dummy when b odd)
-  // stop once the off-diagonal mass is at the rounding level of a b x b rotation
-  // sequence: ||offdiag|| <= 4 b u ||H||
+  // ---- parallel Jacobi; stop once ||offdiag|| <= 4 b u ||H||
+  const int N = (b + 1) & ~1;
   const T eps = T(4 * b) * (sizeof(T) == 4 ? T(5.96e-8) : T(1.11e-16));
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-    // convergence: off-diagonal mass relative to the total
-    double off = 0.0, tot = 0.0;
-    for (int e = tid; e < bb; e += nt) {
+    T off = T(0), tot = T(0);
+    for (int e = lane; e < bb; e += NT) {
       const int r = e % b, q = e / b;
-      const double v = (double)H[r][q];
+      const T v = H[r][q];
       tot += v * v;
       if (r != q) off += v * v;
     }
-    const double offs = block_sum_double(off, sh);
+    off = warp_sum(off);
+    tot = warp_sum(tot);
+    if ((lane & 31) == 0) {
+      red[0][lane >> 5] = off;
+      red[1][lane >> 5] = tot;
+    }
     __syncthreads();
-    const double tots = block_sum_double(tot, sh);
-    if (tid == 0) flag = (offs <= (double)eps * (double)eps * tots) ? 1 : 0;
+    off = T(0);
+    tot = T(0);
+    for (int q = 0; q < (NT >> 5); ++q) {
+      off += red[0][q];
+      tot += red[1][q];
+    }
     __syncthreads();
-    if (flag) break;
+    if (off <= eps * eps * tot) break;
     for (int round = 0; round < N - 1; ++round) {
-      if (tid < N / 2) {
-        // circle method: player N-1 fixed, the others rotate by `round`
-        const int i = tid;
+      if (lane < N / 2) {
+        const int i = lane;
         int p = (i == 0) ? N - 1 : (round + i) % (N - 1);
         int q = (round + N - 1 - i) % (N - 1);
         if (p > q) { const int t = p; p = q; q = t; }
         pairs[i][0] = p;
         pairs[i][1] = q;
-        T c = T(1), s = T(0);
+        T c = T(1), sn = T(0);
         if (q < b) {
           const T apq = H[p][q];
           if (apq != T(0)) {
             const T tau = (H[q][q] - H[p][p]) / (T(2) * apq);
             const T t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + wsqrt(T(1) + tau * tau));
             c = T(1) / wsqrt(T(1) + t * t);
-            s = t * c;
+            sn = t * c;
           }
         }
         cs[i][0] = c;
-        cs[i][1] = s;
+        cs[i][1] = sn;
       }
       __syncthreads();
-      // rows: H <- J^T H
-      for (int e = tid; e < (N / 2) * b; e += nt) {
+      for (int e = lane; e < (N / 2) * b; e += NT) {   // rows: H <- J^T H
         const int i = e % (N / 2), l = e / (N / 2);
         const int p = pairs[i][0], q = pairs[i][1];
         if (q < b) {
-          const T c = cs[i][0], s = cs[i][1];
+          const T c = cs[i][0], sn = cs[i][1];
           const T hp = H[p][l], hq = H[q][l];
-          H[p][l] = c * hp - s * hq;
-          H[q][l] = s * hp + c * hq;
+          H[p][l] = c * hp - sn * hq;
+          H[q][l] = sn * hp + c * hq;
         }
       }
       __syncthreads();
-      // columns: H <- H J, Y <- Y J
-      for (int e = tid; e < (N / 2) * b; e += nt) {
+      for (int e = lane; e < (N / 2) * b; e += NT) {   // columns: H <- H J, Y <- Y J
         const int i = e % (N / 2), l = e / (N / 2);
         const int p = pairs[i][0], q = pairs[i][1];
         if (q < b) {
-          const T c = cs[i][0], s = cs[i][1];
+          const T c = cs[i][0], sn = cs[i][1];
           const T hp = H[l][p], hq = H[l][q];
-          H[l][p] = c * hp - s * hq;
-          H[l][q] = s * hp + c * hq;
+          H[l][p] = c * hp - sn * hq;
+          H[l][q] = sn * hp + c * hq;
           const T yp = Y[l][p], yq = Y[l][q];
-          Y[l][p] = c * yp - s * yq;
-          Y[l][q] = s * yp + c * yq;
+          Y[l][p] = c * yp - sn * yq;
+          Y[l][q] = sn * yp + c * yq;
         }
       }
       __syncthreads();
     }
   }
-  // ---- sort descending
-  if (tid == 0) {
-    for (int c = 0; c < b; ++c) perm[c] = c;
-    for (int c = 0; c < b; ++c) {
-      int best = c;
-      for (int d = c + 1; d < b; ++d)
-        if (H[perm[d]][perm[d]] > H[perm[best]][perm[best]]) best = d;
-      const int t = perm[c]; perm[c] = perm[best]; perm[best] = t;
+  // ---- sort descending: lane c's rank = #{d : theta_d > theta_c, or equal with d < c}
+  if (lane < b) {
+    const T tc = H[lane][lane];
+    int rank = 0;
+    for (int d = 0; d < b; ++d) {
+      const T td = H[d][d];
+      rank += (td > tc) || (td == tc && d < lane);
     }
-    for (int c = 0; c < b; ++c) th[c] = H[perm[c]][perm[c]];
-    flag = 0;
-    for (int c = 0; c < b; ++c)
-      if (!wfinite(th[c])) flag = 1;
-    if (flag) atomicOr(err, ERRBIT_EIG);
+    perm[rank] = lane;
+    if (!wfinite(tc)) atomicOr(err, ERRBIT_EIG);
   }
   __syncthreads();
-  // Wg <- Y permuted (columns sorted)
-  for (int e = tid; e < bb; e += nt) {
+  if (lane < b) th[lane] = H[perm[lane]][perm[lane]];
+  for (int e = lane; e < bb; e += NT) {
     const int r = e % b, c = e / b;
     Wg[r][c] = Y[r][perm[c]];
   }
   __syncthreads();
-  for (int e = tid; e < bb; e += nt) {
+  for (int e = lane; e < bb; e += NT) {
     const int r = e % b, c = e / b;
     Y[r][c] = Wg[r][c];
   }
   __syncthreads();
-  // H <- P Y   (b x b), then Wg <- Y^T P Y
-  for (int e = tid; e < bb; e += nt) {
+  // H <- P Y, then Wg <- Y^T P Y
+  for (int e = lane; e < bb; e += NT) {
     const int r = e % b, c = e / b;
     T v = T(0);
     for (int l = 0; l < b; ++l) v = fma(P[r][l], Y[l][c], v);
     H[r][c] = v;
   }
   __syncthreads();
-  for (int e = tid; e < bb; e += nt) {
+  for (int e = lane; e < bb; e += NT) {
     const int r = e % b, c = e / b;
     T v = T(0);
     for (int l = 0; l < b; ++l) v = fma(Y[l][r], H[l][c], v);
     Wg[r][c] = v;
   }
   __syncthreads();
-  // scaling: z-columns for non-negligible Ritz values, v-columns otherwise
-  __shared__ T fz[BM];
-  __shared__ int usev[BM];
-  if (tid < b) {
-    const int c = tid;
+  if (lane < b) {
+    const int c = lane;
     const T tmax = fabs(th[0]);
     const T small = sizeof(T) == 4 ? T(1e-6) : T(1e-13);
     const T nz2 = Wg[c][c];
@@ -667,40 +870,34 @@ eig_small(const T* __restrict__ part, int nblk, int b, int max_sweeps, T* __rest
     theta[c] = th[c];
   }
   __syncthreads();
-  // Gram of W into P (overwrite): W_c = v-column (Vy_c) or z-column (Zy_c * fz_c)
-  //   <Vy_a, Vy_b> = delta_ab, <Zy_a, Zy_b> = Wg_ab, <Vy_a, Zy_b> = theta_b delta_ab
-  for (int e = tid; e < bb; e += nt) {
+  // Gram of W into P: <Vy_a, Vy_b> = delta_ab, <Zy_a, Zy_b> = Wg_ab, mixed pairs 0
+  for (int e = lane; e < bb; e += NT) {
     const int r = e % b, c = e / b;
     T g;
     if (usev[r] && usev[c]) g = r == c ? T(1) : T(0);
     else if (!usev[r] && !usev[c]) g = fz[r] * fz[c] * Wg[r][c];
-    else if (usev[r]) g = r == c ? th[c] * fz[c] : T(0);
-    else g = r == c ? th[r] * fz[r] : T(0);
+    else g = T(0);
     P[r][c] = g;
   }
   __syncthreads();
-  // Cholesky of the Gram (lower, in place, b x b) -- small: one thread column loop
-  if (tid == 0) flag = 0;
-  __syncthreads();
+  // Cholesky of the Gram (lower, in place)
+  bool bad = false;
   for (int t = 0; t < b; ++t) {
-    if (tid == 0) {
-      T d = P[t][t];
-      if (!(d > T(0)) || !wfinite(d)) { flag = 1; d = T(1); }
-      P[t][t] = wsqrt(d);
-    }
+    T d = P[t][t];
+    if (!(d > T(0)) || !wfinite(d)) { bad = true; d = T(1); }
+    const T lt = wsqrt(d);
     __syncthreads();
-    for (int i = t + 1 + tid; i < b; i += nt) P[i][t] /= P[t][t];
+    if (lane == 0) P[t][t] = lt;
+    for (int i = t + 1 + lane; i < b; i += NT) P[i][t] /= lt;
     __syncthreads();
-    const int w = b - t - 1;
-    for (int e = tid; e < w * w; e += nt) {
-      const int i = t + 1 + e % w, j = t + 1 + e / w;
-      if (i >= j) P[i][j] -= P[i][t] * P[j][t];
-    }
+    for (int i = t + 1 + lane; i < b; i += NT)
+      for (int j = t + 1; j <= i; ++j) P[i][j] -= P[i][t] * P[j][t];
     __syncthreads();
   }
-  if (tid == 0 && flag) atomicOr(err, ERRBIT_EIG);
-  // Linv^T: H <- L^{-T} (upper).  Column c of L^{-T} solves L^T x = e_c.
-  for (int c = tid; c < b; c += nt) {
+  if (lane == 0 && bad) atomicOr(err, ERRBIT_EIG);
+  // L^{-T} into H (upper): column c solves L^T x = e_c (one lane per column)
+  if (lane < b) {
+    const int c = lane;
     for (int a = b - 1; a >= 0; --a) {
       T v = a == c ? T(1) : T(0);
       for (int l = a + 1; l <= c; ++l) v -= P[l][a] * H[l][c];
@@ -708,8 +905,7 @@ eig_small(const T* __restrict__ part, int nblk, int b, int max_sweeps, T* __rest
     }
   }
   __syncthreads();
-  // outputs: Y, Mv = Y Fv L^{-T}, Mz = Y Fz L^{-T}
-  for (int e = tid; e < bb; e += nt) {
+  for (int e = lane; e < bb; e += NT) {
     const int r = e % b, c = e / b;
     T mv = T(0), mz = T(0);
     for (int l = 0; l <= c; ++l) {
@@ -841,17 +1037,56 @@ prep_gram(const T* __restrict__ Z2, int n2, int k, int s, int NP, double* __rest
 constexpr int RP_BM = 64;
 constexpr int RP_BK = 32;
 
-// Shared memory of row_pass.  U (phase 2) reuses the phase-1 staging area; the rows of
-// X1old, A1 and W1 are staged in shared memory for float only (double reads them from
-// global memory to stay within the 227 KB limit at k = 64).
+// Row-solve layout (phase 3 of row_pass).  LG lanes factor one row's k x k system,
+// held in shared memory as a square column-major block with an even leading dimension
+// ld (so the diagonal walk j*ld + j + i of the trailing update has odd stride ld + 1
+// across lanes) and a per-row pitch P = LG*(ld + 1) (mod 32), which puts the 32 lanes
+// of a warp on 32 distinct banks.  R rows are solved per pass, R limited by a 96 KB
+// budget and rounded to whole warps.
+template <typename T, int KMAX>
+struct RowSolveLayout {
+  static constexpr int LG = KMAX <= 8 ? 4 : (KMAX <= 32 ? 8 : 32);
+  __host__ __device__ static int ld(int k) { return k + (k & 1); }
+  __host__ __device__ static int pitch(int k) {
+    const int l = ld(k), want = (LG * (l + 1)) & 31;
+    int p = k * l;
+    while ((p & 31) != want) ++p;
+    return p;
+  }
+  __host__ __device__ static int rows(int k) {
+    const int per_warp = 32 / LG;
+    int r = (int)((96 * 1024) / ((size_t)pitch(k) * sizeof(T)));
+    r = r < 256 / LG ? r : 256 / LG;
+    r = (r / per_warp) * per_warp;
+    return r < per_warp ? per_warp : r;
+  }
+};
+
+// Shared memory of row_pass.  Region 0 holds the phase-1 staging (A2 and Z2 slabs), then
+// U (phase 2), then the row systems (phase 3); the rows of X1old, A1 and W1 are staged
+// for float only (double reads them from global memory to keep within 227 KB).
 template <typename T>
 struct RowPassSmem {
   static constexpr bool kStage = sizeof(T) == 4;
-  static size_t bytes(int NP, int k, int s) {
-    const size_t stage = (size_t)RP_BK * RP_BM + (size_t)RP_BK * NP;
+  static constexpr int kStages = sizeof(T) == 4 ? 4 : 2;   // phase-1 pipeline depth
+  template <int KMAX>
+  __host__ __device__ static size_t region0(int NP, int k) {
+    const size_t stage = (size_t)kStages * ((size_t)RP_BK * RP_BM + (size_t)RP_BK * NP);
     const size_t us = (size_t)RP_BM * (EIG_BMAX + 1);
-    return sizeof(T) * ((stage > us ? stage : us) + (size_t)RP_BM * (NP + 1) + (size_t)k * k +
+    const size_t rs = (size_t)RowSolveLayout<T, KMAX>::rows(k) * RowSolveLayout<T, KMAX>::pitch(k);
+    size_t r0 = stage > us ? stage : us;
+    return r0 > rs ? r0 : rs;
+  }
+  template <int KMAX>
+  static size_t bytes_k(int NP, int k, int s) {
+    return sizeof(T) * (region0<KMAX>(NP, k) + (size_t)RP_BM * (NP + 1) + (size_t)k * k +
                         (size_t)k * (s > 0 ? s : 1) + (kStage ? 3 * (size_t)RP_BM * (k + 1) : 0));
+  }
+  static size_t bytes(int NP, int k, int s) {
+    if (k <= 8) return bytes_k<8>(NP, k, s);
+    if (k <= 16) return bytes_k<16>(NP, k, s);
+    if (k <= 32) return bytes_k<32>(NP, k, s);
+    return bytes_k<64>(NP, k, s);
   }
 };
 
@@ -863,12 +1098,11 @@ row_pass(const T* __restrict__ A, int64_t lda, const T* __restrict__ W1, int64_t
          double* __restrict__ wpart, int* __restrict__ err) {
   extern __shared__ unsigned char smem_raw[];
   constexpr bool kStage = RowPassSmem<T>::kStage;
-  const size_t stage_elems = (size_t)RP_BK * RP_BM + (size_t)RP_BK * NP;
-  const size_t us_elems = (size_t)RP_BM * (EIG_BMAX + 1);
   T* As = reinterpret_cast<T*>(smem_raw);   // [RP_BK][RP_BM]           (phase 1)
   T* Zs = As + RP_BK * RP_BM;               // [RP_BK][NP]              (phase 1)
-  T* Us = As;                               // [RP_BM][EIG_BMAX+1]      (phase 2, reuses As)
-  T* Ys = As + (stage_elems > us_elems ? stage_elems : us_elems);  // [RP_BM][NP+1]
+  T* Us = As;                               // [RP_BM][EIG_BMAX+1]      (phase 2)
+  T* Ms = As;                               // row systems              (phase 3)
+  T* Ys = As + RowPassSmem<T>::template region0<KMAX>(NP, k);  // [RP_BM][NP+1]
   T* Gs = Ys + RP_BM * (NP + 1);            // [k][k]
   T* CVs = Gs + k * k;                      // [k][s]
   T* Xo = CVs + k * (s > 0 ? s : 1);        // [RP_BM][k+1]  X1old rows (float)
@@ -909,64 +1143,68 @@ row_pass(const T* __restrict__ A, int64_t lda, const T* __restrict__ W1, int64_t
     }
   }
 
-  // ---- phase 1: Y = A2 rows * Z2, slabs of 32 columns, next slab prefetched in registers
+  // ---- phase 1: Y = A2 rows * Z2 in slabs of 32 columns, an S-stage cp.async pipeline
+  // (S - 1 slabs in flight while one is consumed; S = 4 for float, 2 for double).  Warp w covers rows 32 (w % 2) .. +31
+  // and the column quarter w / 2; lane (rg, cq) = (lane % 8, lane / 8) owns 4 rows x NPU
+  // columns, so a warp reads one 128-byte row segment of A2 and 4 words of Z2 per step.
   {
-    const int rg = tid % 16, cg = tid / 16;   // rows 4 rg .. 4 rg + 3, columns cg + 16 v
+    constexpr int S = RowPassSmem<T>::kStages;
+    const int slab = RP_BK * RP_BM + RP_BK * NP;   // elements per stage
+    const int lane = tid & 31, w = tid >> 5;
+    const int rg = lane & 7, cq = lane >> 3;
+    const int row0 = 32 * (w & 1) + 4 * rg;
+    const int col0 = (w >> 1) * 4 * NPU + cq;     // columns col0 + 4 v, v < NPU
     T acc[4][6];
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
       for (int v = 0; v < 6; ++v) acc[u][v] = T(0);
-    constexpr int AQ = RP_BK * RP_BM / 256;   // 8 A2 elements per thread per slab
-    constexpr int ZQ = RP_BK * 96 / 256;      // up to 12 Z2 elements per thread per slab
-    T ra[AQ], rz[ZQ];
-    auto fetch = [&](int j0) {
-#pragma unroll
-      for (int q = 0; q < AQ; ++q) {
-        const int e = tid + 256 * q;
-        const int r = e % RP_BM, kk = e / RP_BM;
-        const int i = i0 + r, j = j0 + kk;
-        ra[q] = (i < m && j < n2) ? A2[i + (int64_t)j * lda] : T(0);
-      }
-#pragma unroll
-      for (int q = 0; q < ZQ; ++q) {
-        const int e = tid + 256 * q;
-        T v = T(0);
-        if (e < RP_BK * NP) {
-          const int j = j0 + e / NP;
-          v = j < n2 ? Z2[(int64_t)j0 * NP + e] : T(0);
+    const int nsl = (n2 + RP_BK - 1) / RP_BK;
+    auto issue = [&](int sl) {
+      if (sl < nsl) {
+        T* As_ = As + (size_t)(sl % S) * slab;
+        T* Zs_ = As_ + RP_BK * RP_BM;
+        const int j0 = sl * RP_BK;
+        for (int e = tid; e < RP_BK * RP_BM; e += 256) {
+          const int r = e % RP_BM, kk = e / RP_BM;
+          const int i = i0 + r, j = j0 + kk;
+          const bool ok = i < m && j < n2;
+          cp_async_elem(As_ + kk * RP_BM + r, ok ? A2 + i + (int64_t)j * lda : A2, ok);
         }
-        rz[q] = v;
+        for (int e = tid; e < RP_BK * NP; e += 256) {
+          const bool ok = j0 + e / NP < n2;
+          cp_async_elem(Zs_ + e, ok ? Z2 + (int64_t)j0 * NP + e : Z2, ok);
+        }
       }
+      cp_async_commit();
     };
-    if (n2 > 0) fetch(0);
-    for (int j0 = 0; j0 < n2; j0 += RP_BK) {
+    for (int sl = 0; sl < S - 1; ++sl) issue(sl);
+    for (int sl = 0; sl < nsl; ++sl) {
+      cp_async_wait<S - 2>();
       __syncthreads();
-#pragma unroll
-      for (int q = 0; q < AQ; ++q) As[tid + 256 * q] = ra[q];
-#pragma unroll
-      for (int q = 0; q < ZQ; ++q)
-        if (tid + 256 * q < RP_BK * NP) Zs[tid + 256 * q] = rz[q];
-      __syncthreads();
-      if (j0 + RP_BK < n2) fetch(j0 + RP_BK);
+      issue(sl + S - 1);
+      const T* As_ = As + (size_t)(sl % S) * slab;
+      const T* Zs_ = As_ + RP_BK * RP_BM;
 #pragma unroll 4
       for (int kk = 0; kk < RP_BK; ++kk) {
-        T a[4], z[6];
+        T a[4];
+        load4(a, As_ + kk * RP_BM + row0);
 #pragma unroll
-        for (int u = 0; u < 4; ++u) a[u] = As[kk * RP_BM + 4 * rg + u];
+        for (int v = 0; v < 6; ++v) {
+          if (v < NPU) {  // uniform: only the live column groups cost FMAs
+            const T z = Zs_[kk * NP + col0 + 4 * v];
 #pragma unroll
-        for (int v = 0; v < 6; ++v) z[v] = v < NPU ? Zs[kk * NP + cg + 16 * v] : T(0);
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-          for (int v = 0; v < 6; ++v) acc[u][v] = fma(a[u], z[v], acc[u][v]);
+            for (int u = 0; u < 4; ++u) acc[u][v] = fma(a[u], z, acc[u][v]);
+          }
+        }
       }
     }
+    cp_async_wait<0>();
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
       for (int v = 0; v < 6; ++v)
-        if (v < NPU) Ys[(4 * rg + u) * (NP + 1) + cg + 16 * v] = acc[u][v];
+        if (v < NPU) Ys[(row0 + u) * (NP + 1) + col0 + 4 * v] = acc[u][v];
   }
   __syncthreads();
 
@@ -997,85 +1235,86 @@ row_pass(const T* __restrict__ A, int64_t lda, const T* __restrict__ W1, int64_t
   if (tid == 0) wpart[blockIdx.x] = wsum;
   __syncthreads();
 
-  // ---- phase 3: row solves
-  constexpr int GS = KMAX / 2;        // lanes per row
-  constexpr int RPW = 32 / GS;        // rows per warp pass
-  const int lane = tid & 31, warp = tid >> 5;
-  const int lg = lane % GS, grp = lane / GS;
-  const unsigned gmask = 0xffffffffu;  // every lane runs the same shuffles (uniform loops)
-  const int j0c = lg, j1c = lg + GS;
-  bool bad = false;
-  for (int rbase = warp * RPW; rbase < RP_BM; rbase += 8 * RPW) {
-    const int r = rbase + grp;
-    const int i = i0 + r;
-    const bool active = i < m;
-    T c0[KMAX], c1[KMAX];
-    T d0 = T(1), d1 = T(1);
-    if (j0c < k) { const T w = w1_at(r, j0c); d0 = w * w; }
-    if (j1c < k) { const T w = w1_at(r, j1c); d1 = w * w; }
-#pragma unroll
-    for (int q = 0; q < KMAX; ++q) {
-      c0[q] = (q < k && j0c < k) ? Gs[q + j0c * k] + (q == j0c ? d0 : T(0)) : (q == j0c ? T(1) : T(0));
-      c1[q] = (q < k && j1c < k) ? Gs[q + j1c * k] + (q == j1c ? d1 : T(0)) : (q == j1c ? T(1) : T(0));
-    }
-    T e0 = (active && j0c < k) ? Ys[r * (NP + 1) + j0c] : T(0);
-    T e1 = (active && j1c < k) ? Ys[r * (NP + 1) + j1c] : T(0);
-    // Cholesky: after step t, c_j[t] holds L(j,t) (row part, t < j), c_t[t] = L(t,t),
-    // c_t[q] = L(q,t) for q > t (column part).
-#pragma unroll
-    for (int t = 0; t < KMAX; ++t) {
-      if (t < k) {
-        const int own = t % GS;
-        const T pv = (t / GS == 0) ? c0[t] : c1[t];
-        T piv = __shfl_sync(gmask, pv, own, GS);
-        if (!(piv > T(0)) || !wfinite(piv)) { bad = bad || active; piv = T(1); }
-        const T ltt = wsqrt(piv);
-        const T rl = T(1) / ltt;
-        T l0 = c0[t] * rl, l1 = c1[t] * rl;
-        if (j0c > t) c0[t] = l0;
-        if (j1c > t) c1[t] = l1;
-        if (j0c == t) c0[t] = ltt;
-        if (j1c == t) c1[t] = ltt;
-#pragma unroll
-        for (int q = t + 1; q < KMAX; ++q) {
-          if (q < k) {
-            const T lq = __shfl_sync(gmask, (q / GS == 0) ? l0 : l1, q % GS, GS);
-            if (j0c > t) c0[q] -= lq * l0;
-            if (j1c > t) c1[q] -= lq * l1;
-            if (j0c == t) c0[q] = lq;
-            if (j1c == t) c1[q] = lq;
-          }
+  // ---- phase 3: row solves.  A group of LG lanes factors one row's system
+  // M = diag(W1(i,:)^2) + G (lower triangle, right-looking Cholesky: at step t the lanes
+  // scale column t, then each lane updates its own columns j > t down from the
+  // diagonal), then runs the two triangular solves on E(i,:) in place.
+  {
+    using Lay = RowSolveLayout<T, KMAX>;
+    constexpr int LG = Lay::LG;
+    const int ld = Lay::ld(k), P = Lay::pitch(k), R = Lay::rows(k);
+    const int grp = tid / LG, g = tid % LG;
+    T* M = Ms + (size_t)grp * P;
+    bool bad = false;
+    for (int base = 0; base < RP_BM; base += R) {
+      const int r = base + grp;
+      const bool in = grp < R && r < RP_BM;
+      const bool active = in && i0 + r < m;
+      if (in) {
+        for (int j = g; j < k; j += LG) {
+          const T w = w1_at(r, j);
+          for (int q = j; q < k; ++q) M[j * ld + q] = Gs[q + j * k] + (q == j ? w * w : T(0));
         }
       }
-    }
-    // forward: L y = e  (row j of L is c_j[0..j-1], diagonal c_j[j])
-#pragma unroll
-    for (int t = 0; t < KMAX; ++t) {
-      if (t < k) {
-        const T yv = (t / GS == 0) ? e0 / c0[t] : e1 / c1[t];
-        const T yt = __shfl_sync(gmask, yv, t % GS, GS);
-        if (j0c == t) e0 = yt;
-        if (j1c == t) e1 = yt;
-        if (j0c > t) e0 -= c0[t] * yt;
-        if (j1c > t) e1 -= c1[t] * yt;
+      __syncwarp();
+      T* e = Ys + (size_t)(in ? r : 0) * (NP + 1);
+      // Cholesky with the forward solve L y = e folded in: at step t column t of L is
+      // final, so y_t = e_t / L_tt and e_q -= L_qt y_t (q > t) join the trailing update.
+      // The diagonal is left holding 1 / L_tt for the backward solve.
+      for (int t = 0; t < k; ++t) {
+        T piv = in ? M[t * ld + t] : T(1);
+        if (!(piv > T(0)) || !wfinite(piv)) {
+          bad = bad || active;
+          piv = T(1);
+        }
+        const T rl = wrsqrt(piv);
+        const T yt = in ? e[t] * rl : T(0);
+        __syncwarp();
+        if (in) {
+          for (int q = t + 1 + g; q < k; q += LG) M[t * ld + q] *= rl;
+          if (g == 0) {
+            M[t * ld + t] = rl;
+            e[t] = yt;
+          }
+        }
+        __syncwarp();
+        if (in) {
+          const T* __restrict__ Mt = M + t * ld;
+          for (int q = t + 1 + g; q < k; q += LG) e[q] = fma(-Mt[q], yt, e[q]);
+          for (int j = t + 1 + g; j < k; j += LG) {
+            const T ljt = Mt[j];
+            T* __restrict__ Mj = M + j * ld;
+            int q = j;
+            for (; q + 4 <= k; q += 4) {
+              const T a0 = Mt[q], a1 = Mt[q + 1], a2 = Mt[q + 2], a3 = Mt[q + 3];
+              const T b0 = Mj[q], b1 = Mj[q + 1], b2 = Mj[q + 2], b3 = Mj[q + 3];
+              Mj[q] = fma(-a0, ljt, b0);
+              Mj[q + 1] = fma(-a1, ljt, b1);
+              Mj[q + 2] = fma(-a2, ljt, b2);
+              Mj[q + 3] = fma(-a3, ljt, b3);
+            }
+            for (; q < k; ++q) Mj[q] = fma(-Mt[q], ljt, Mj[q]);
+          }
+        }
+        __syncwarp();
       }
-    }
-    // backward: L^T x = y  (column j of L below the diagonal is c_j[j+1..k-1])
-#pragma unroll
-    for (int t = KMAX - 1; t >= 0; --t) {
-      if (t < k) {
-        const T xv = (t / GS == 0) ? e0 / c0[t] : e1 / c1[t];
-        const T xt = __shfl_sync(gmask, xv, t % GS, GS);
-        if (j0c == t) e0 = xt;
-        if (j1c == t) e1 = xt;
-        if (j0c < t) e0 -= c0[t] * xt;
-        if (j1c < t) e1 -= c1[t] * xt;
+      // backward: L^T x = y (column-oriented; L(t,q) for t > q is M[q*ld + t];
+      // the diagonal holds 1 / L_tt)
+      for (int t = k - 1; t >= 0; --t) {
+        if (in && g == 0) e[t] = e[t] * M[t * ld + t];
+        __syncwarp();
+        if (in) {
+          const T xt = e[t];
+          for (int q = g; q < t; q += LG) e[q] = fma(-M[q * ld + t], xt, e[q]);
+        }
+        __syncwarp();
       }
+      if (active)
+        for (int a = g; a < k; a += LG) X1new[(i0 + r) + (int64_t)a * m] = e[a];
+      __syncwarp();
     }
-    if (active && j0c < k) X1new[i + (int64_t)j0c * m] = e0;
-    if (active && j1c < k) X1new[i + (int64_t)j1c * m] = e1;
+    if (bad) atomicOr(err, ERRBIT_NOT_SPD);
   }
-  if (bad) atomicOr(err, ERRBIT_NOT_SPD);
 }
 
 // F_p = w-term + ||A2||^2 - ||B||^2 - sum_{c<s} theta_c, stored in Fhist[*iter], then

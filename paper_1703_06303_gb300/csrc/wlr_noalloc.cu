@@ -51,7 +51,7 @@ void* setup_device(int dev, const char** why) {
     *why = "cudaGetSymbolAddress failed for the scratch array";
     return nullptr;
   }
-  const int limit = 160 * 1024;
+  const int limit = 200 * 1024;  // above the largest row-pass need (k = 64, r - k = 32)
   if (cudaFuncSetAttribute((const void*)wlr::row_pass<float, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit) != cudaSuccess ||
       cudaFuncSetAttribute((const void*)wlr::row_pass<float, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit) != cudaSuccess ||
       cudaFuncSetAttribute((const void*)wlr::row_pass<float, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit) != cudaSuccess ||

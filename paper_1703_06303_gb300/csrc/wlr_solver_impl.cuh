@@ -29,9 +29,9 @@ class Solver final : public SolverBase {
     for (int q = 0; q < 3; ++q) X1buf_[q] = dalloc<T>((size_t)m * k);
     Q1_ = dalloc<T>((size_t)m * k);
     // chunking of the split-m Gram products
-    ch_S1_ = chunking(m, 1);
-    ch_T_ = chunking(m, (size_t)cdiv(k + n2, 64));
-    ch_K_ = chunking(m, (size_t)std::max(1, cdiv(n2, 64)) * std::max(1, cdiv(n2, 64)));
+    ch_S1_ = chunking(m, 1, 64);
+    ch_T_ = chunking(m, (size_t)cdiv(k + n2, 64), 608);
+    ch_K_ = chunking(m, (size_t)std::max(1, cdiv(n2, 64)) * std::max(1, cdiv(n2, 64)), 608);
     const size_t L = (size_t)k * k + (size_t)k * n2;
     size_t part_elems = std::max((size_t)ch_S1_.nch * k * k, (size_t)ch_T_.nch * L);
     part_elems = std::max(part_elems, (size_t)ch_K_.nch * n2 * n2);
@@ -46,7 +46,7 @@ class Solver final : public SolverBase {
     Bl_ = dalloc<float>(std::max<size_t>((size_t)k * n2, 1));
     Z2_ = dalloc<T>(std::max<size_t>((size_t)n2 * NP, 1));
     Z2prev_ = dalloc<T>(std::max<size_t>((size_t)n2 * NP, 1));
-    nblk_coef_ = cdiv(n2, 128);
+    nblk_coef_ = cdiv(n2, 8);
     bpart_ = dalloc<double>(std::max(nblk_coef_, 1));
     K64_ = dalloc<double>(std::max<size_t>((size_t)n2 * n2, 1));
     G2_ = dalloc<T>(std::max<size_t>((size_t)n2 * n2, 1));
@@ -54,7 +54,7 @@ class Solver final : public SolverBase {
     prep_part_ = dalloc<double>((size_t)std::max(nblk_prep_, 1) * k * (k + std::max(s, 0)));
     prep_ticket_ = dalloc<unsigned int>(1);
     normA2_ = dalloc<double>(1);
-    nblk_eig_ = cdiv(n2, 16);
+    nblk_eig_ = cdiv(n2, 8);
     const int bb = std::max(b, 1);
     V_ = dalloc<T>((size_t)std::max(n2, 1) * bb);
     Zeig_ = dalloc<T>((size_t)std::max(n2, 1) * bb);
@@ -63,6 +63,8 @@ class Solver final : public SolverBase {
     Mv_ = dalloc<T>((size_t)bb * bb);
     Mz_ = dalloc<T>((size_t)bb * bb);
     theta_ = dalloc<T>(bb);
+    HP_ = dalloc<double>(2 * (size_t)bb * bb);
+    eig_ticket_ = dalloc<unsigned int>(1);
     resid_ = dalloc<T>(bb);
     Vs_ = dalloc<T>((size_t)std::max(n2, 1) * std::max(s, 1));
     G_ = dalloc<T>((size_t)k * k);
@@ -85,6 +87,7 @@ class Solver final : public SolverBase {
     WLR_CUDA(cudaMemsetAsync(CVprev_, 0, sizeof(T) * k * std::max(s, 1), stream_));
     WLR_CUDA(cudaMemsetAsync(bpart_, 0, sizeof(double) * std::max(nblk_coef_, 1), stream_));
     WLR_CUDA(cudaMemsetAsync(prep_ticket_, 0, sizeof(unsigned int), stream_));
+    WLR_CUDA(cudaMemsetAsync(eig_ticket_, 0, sizeof(unsigned int), stream_));
     WLR_CUDA(cudaMemsetAsync(G_, 0, sizeof(T) * k * k, stream_));
     // dynamic shared memory limits
     set_smem((const void*)row_pass<T, 8>, RowPassSmem<T>::bytes(NP, k, s));
@@ -92,7 +95,7 @@ class Solver final : public SolverBase {
     set_smem((const void*)row_pass<T, 32>, RowPassSmem<T>::bytes(NP, k, s));
     set_smem((const void*)row_pass<T, 64>, RowPassSmem<T>::bytes(NP, k, s));
     set_smem((const void*)x2_pass<T>, x2_smem());
-    set_smem((const void*)coef_kernel2<T>, 2 * sizeof(T) * k * k);
+    set_smem((const void*)coef_kernel3<T>, sizeof(T) * (2 * k * k + 16 * 64));
     set_smem((const void*)chol1_kernel<T>, sizeof(double) * (2 * k * k + k));
     set_smem((const void*)chol2_kernel<T>, 3 * sizeof(T) * k * k);
     set_smem((const void*)prep_gram<T>, sizeof(T) * 64 * (NP + 1));
@@ -370,10 +373,11 @@ class Solver final : public SolverBase {
     if (bytes > 48 * 1024)
       WLR_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
   }
-  static Chunk chunking(int m, size_t tiles) {
-    const int target = 304;
+  // row chunks for a split-m Gram with `tiles` output tiles: about `target` blocks in
+  // all, at most 64 chunks (each chunk is a partial the consumer sums).
+  static Chunk chunking(int m, size_t tiles, int target = 160) {
     int nch = std::max<int>(1, (int)((target + tiles - 1) / std::max<size_t>(tiles, 1)));
-    nch = std::min(nch, 64);
+    nch = std::min(nch, 128);
     int rows = cdiv(m, nch);
     rows = std::max(32, ((rows + 31) / 32) * 32);
     nch = std::max(1, cdiv(m, rows));
@@ -541,22 +545,28 @@ class Solver final : public SolverBase {
   }
 
   // ------------------------------------------------------------------ kernels
-  // part64 <- chunked partials of X^T [Y1 Y2] (Y1: q1 columns, Y2: the rest)
+  // part64 <- chunked partials of X^T [Y1 Y2] (Y1: q1 columns, Y2: the rest).  With Rq,
+  // X and Y1 are Q1 = X Rq (formed inside the kernel; float path only).
   void gram(const T* X, int64_t ldx, const T* Y1, int64_t ldy1, int q1, const T* Y2, int64_t ldy2,
-            int P, int Q, int64_t stride, const Chunk& ch) {
+            int P, int Q, int64_t stride, const Chunk& ch, const T* Rq = nullptr) {
     if (P <= 0 || Q <= 0) return;
     const int m = d_.m;
     Prof pf(this, "gram_tn");
-    if (P <= 32 && Q <= 32) {
-      dim3 g(cdiv(P, 32), cdiv(Q, 32), ch.nch);
-      gram_tn<T, 32, 32><<<g, 64, 0, stream_>>>(X, ldx, Y1, ldy1, q1, Y2, ldy2, m, P, Q, ch.rows, part64_, stride, 0);
-    } else if (P <= 32) {
-      dim3 g(cdiv(P, 32), cdiv(Q, 64), ch.nch);
-      gram_tn<T, 32, 64><<<g, 128, 0, stream_>>>(X, ldx, Y1, ldy1, q1, Y2, ldy2, m, P, Q, ch.rows, part64_, stride, 0);
-    } else {
-      dim3 g(cdiv(P, 64), cdiv(Q, 64), ch.nch);
-      gram_tn<T, 64, 64><<<g, 256, 0, stream_>>>(X, ldx, Y1, ldy1, q1, Y2, ldy2, m, P, Q, ch.rows, part64_, stride, 0);
-    }
+    const bool fuse = Rq != nullptr;
+#define WLR_GRAM(PT, QT, NTH)                                                                    \
+  do {                                                                                          \
+    dim3 g(cdiv(P, PT), cdiv(Q, QT), ch.nch);                                                   \
+    if (fuse)                                                                                   \
+      gram_tn<T, PT, QT, true><<<g, NTH, 0, stream_>>>(X, ldx, Y1, ldy1, q1, Y2, ldy2, Rq, m, P, Q, \
+                                                       ch.rows, part64_, stride, 0);            \
+    else                                                                                        \
+      gram_tn<T, PT, QT, false><<<g, NTH, 0, stream_>>>(X, ldx, Y1, ldy1, q1, Y2, ldy2, nullptr, m, \
+                                                        P, Q, ch.rows, part64_, stride, 0);     \
+  } while (0)
+    if (P <= 32 && Q <= 32) WLR_GRAM(32, 32, 64);
+    else if (P <= 32) WLR_GRAM(32, 64, 128);
+    else WLR_GRAM(64, 64, 256);
+#undef WLR_GRAM
     count(1);
   }
   void reduce64(int64_t stride, int nch, int64_t len, double* out64) {
@@ -586,33 +596,47 @@ class Solver final : public SolverBase {
     return sumsq_part_;
   }
 
-  // steps a1 + a2 for X1 = X1buf_[xi]
-  void qr_coef(int xi) {
+  // steps a1 + a2 for X1 = X1buf_[xi].  precond: the first CholeskyQR factor is the
+  // previous iteration's R (X1 moves little per iteration, so X1 R_prev^{-1} is already
+  // nearly orthonormal and the second factor recovers the exact R = R2 R_prev); else a
+  // full CholeskyQR2 from S1 = X1^T X1.
+  void qr_coef(int xi, bool precond = false) {
     const int m = d_.m, k = d_.k, n2 = d_.n2, NP = d_.NP;
     const T* X1 = X1buf_[xi];
     const T* A2 = A_ + (int64_t)k * lda_;
-    gram(X1, m, X1, m, k, nullptr, 0, k, k, (int64_t)k * k, ch_S1_);
-    {
-      Prof pf(this, "chol1");
-      chol1_kernel<T><<<1, 256, sizeof(double) * (2 * k * k + k), stream_>>>(part64_, ch_S1_.nch, k, R1inv_, err_);
+    const T* Rpre = Rinv_;
+    if (!precond) {
+      gram(X1, m, X1, m, k, nullptr, 0, k, k, (int64_t)k * k, ch_S1_);
+      {
+        Prof pf(this, "chol1");
+        chol1_kernel<T><<<1, 256, sizeof(double) * (2 * k * k + k), stream_>>>(part64_, ch_S1_.nch, k, R1inv_, err_);
+      }
+      count(1);
+      Rpre = R1inv_;
     }
-    {
-      Prof pf(this, "form_q");
-      form_q<T><<<grid1d((int64_t)m * k), 256, sizeof(T) * k * k, stream_>>>(X1, m, R1inv_, m, k, Q1_);
-    }
-    count(2);
     const int64_t L = (int64_t)k * k + (int64_t)k * n2;
-    gram(Q1_, m, Q1_, m, k, A2, lda_, k, k + n2, L, ch_T_);
+    if (std::is_same<T, float>::value) {
+      // Q1 = X1 Rpre formed slab by slab inside the Gram kernel
+      gram(X1, m, nullptr, 0, k, A2, lda_, k, k + n2, L, ch_T_, Rpre);
+    } else {
+      {
+        Prof pf(this, "form_q");
+        form_q<T><<<grid1d((int64_t)m * k), 256, sizeof(T) * k * k, stream_>>>(X1, m, Rpre, m, k, Q1_);
+      }
+      count(1);
+      gram(Q1_, m, Q1_, m, k, A2, lda_, k, k + n2, L, ch_T_);
+    }
+    // Q1^T [Q1 A2] summed over the chunks by all SMs; chol2 and coef read the sum
     reduce64(L, ch_T_.nch, L, S2T_);
     {
       Prof pf(this, "chol2");
-      chol2_kernel<T><<<1, 256, 3 * sizeof(T) * k * k, stream_>>>(S2T_, k, R1inv_, Nm_, Rinv_, err_);
+      chol2_kernel<T><<<1, 256, 3 * sizeof(T) * k * k, stream_>>>(S2T_, 1, L, k, Rpre, Nm_, Rinv_, err_);
     }
     count(1);
     if (n2 > 0) {
       Prof pf(this, "coef");
-      coef_kernel2<T><<<nblk_coef_, 128, 2 * sizeof(T) * k * k, stream_>>>(
-          S2T_ + (int64_t)k * k, Nm_, Rinv_, k, n2, NP, C_, B64_, Bh_, Bl_, Z2_, bpart_);
+      coef_kernel3<T><<<nblk_coef_, 256, sizeof(T) * (2 * k * k + 16 * 64), stream_>>>(
+          S2T_, 1, L, Nm_, Rinv_, k, n2, NP, C_, B64_, Bh_, Bl_, Z2_, bpart_);
       count(1);
     }
   }
@@ -623,18 +647,19 @@ class Solver final : public SolverBase {
     form_g2_df<T><<<g, 256, 0, stream_>>>(K64_, B64_, Bh_, Bl_, d_.k, n2, G2_);
     count(1);
   }
-  void eig_iteration() {
+  void eig_iteration(bool cold = false) {
     const int n2 = d_.n2, b = d_.b, s = d_.s;
     {
       Prof pf(this, "eig_mult");
       if (eig_vsmem_)
-        eig_mult<T, true><<<nblk_eig_, 256, (size_t)n2 * b * sizeof(T), stream_>>>(G2_, V_, n2, b, Zeig_, eigpart_);
+        eig_mult<T, true><<<nblk_eig_, 256, (size_t)n2 * b * sizeof(T), stream_>>>(G2_, V_, n2, b, Zeig_, eigpart_,
+                                                                                   eig_ticket_, HP_);
       else
-        eig_mult<T, false><<<nblk_eig_, 256, 0, stream_>>>(G2_, V_, n2, b, Zeig_, eigpart_);
+        eig_mult<T, false><<<nblk_eig_, 256, 0, stream_>>>(G2_, V_, n2, b, Zeig_, eigpart_, eig_ticket_, HP_);
     }
     {
       Prof pf(this, "eig_small");
-      eig_small<T><<<1, 512, 0, stream_>>>(eigpart_, nblk_eig_, b, sizeof(T) == 4 ? 8 : 20, Y_, Mv_, Mz_,
+      eig_small<T><<<1, 128, 0, stream_>>>(HP_, b, cold ? (sizeof(T) == 4 ? 12 : 24) : (sizeof(T) == 4 ? 2 : 6), Y_, Mv_, Mz_,
                                           theta_, resid_, err_);
     }
     Prof pf(this, "eig_update");
@@ -655,17 +680,19 @@ class Solver final : public SolverBase {
     count(1);
   }
   // steps a1..a3 (+ the small products for a4/a5) for X1 = X1buf_[xi]
-  void compute_cd(int xi, bool warm) {
-    qr_coef(xi);
+  void compute_cd(int xi, bool warm, bool precond = false) {
+    qr_coef(xi, precond);
     if (d_.s > 0) {
       form_g2_launch();
       int q = warm ? o_.eig_iters : o_.eig_iters_cold;
+      bool cold = false;
       if (eig_cold_) {
         eig_start();
         q = o_.eig_iters_cold;
         eig_cold_ = false;
+        cold = true;
       }
-      for (int t = 0; t < q; ++t) eig_iteration();
+      for (int t = 0; t < q; ++t) eig_iteration(cold);
     }
     prep();
     cd_valid_ = true;
@@ -679,7 +706,7 @@ class Solver final : public SolverBase {
     const int s = d_.s;
     std::vector<T> prev(s, (T)0), now(s);
     for (int round = 0; round < 400; ++round) {
-      for (int t = 0; t < 10; ++t) eig_iteration();
+      for (int t = 0; t < 10; ++t) eig_iteration(true);
       WLR_CUDA(cudaMemcpyAsync(hbuf_ + 128, theta_, sizeof(T) * s, cudaMemcpyDeviceToHost, stream_));
       WLR_CUDA(cudaStreamSynchronize(stream_));
       std::memcpy(now.data(), hbuf_ + 128, sizeof(T) * s);
@@ -691,7 +718,7 @@ class Solver final : public SolverBase {
   }
 
   // step a4 + a5 + objective, then a1..a3 for the new X1 (one loop body of Algorithm 1)
-  void iteration_body(int xi, int xo) {
+  void iteration_body(int xi, int xo, bool steady) {
     const int m = d_.m, k = d_.k, n2 = d_.n2, s = d_.s, NP = d_.NP;
     const size_t smem = RowPassSmem<T>::bytes(NP, k, s);
     const int g = nblk_row_;
@@ -717,19 +744,24 @@ class Solver final : public SolverBase {
       WLR_CUDA(cudaMemcpyAsync(Z2prev_, Z2_, sizeof(T) * (size_t)n2 * NP, cudaMemcpyDeviceToDevice, stream_));
     if (s > 0)
       WLR_CUDA(cudaMemcpyAsync(CVprev_, CV_, sizeof(T) * (size_t)k * s, cudaMemcpyDeviceToDevice, stream_));
-    compute_cd(xo, true);
+    compute_cd(xo, true, steady);
   }
+
+  // iterations after set_init that use the full CholeskyQR2 before switching to the
+  // previous-R preconditioned form (and to graph replay)
+  static constexpr int kFullQrIters = 3;
 
   void iterate_once() {
     const int xi = cur_, xo = (cur_ + 1) % 3;
-    if (o_.use_graph && !eig_cold_) {
+    const bool steady = iters_host_ >= kFullQrIters;
+    if (o_.use_graph && !eig_cold_ && steady) {
       auto it = graphs_.find(xi);
       if (it == graphs_.end()) {
         cudaGraph_t graph;
         const int64_t before = launches_;
         WLR_CUDA(cudaStreamBeginCapture(stream_, cudaStreamCaptureModeThreadLocal));
         try {
-          iteration_body(xi, xo);
+          iteration_body(xi, xo, true);
         } catch (...) {
           cudaStreamEndCapture(stream_, &graph);
           throw;
@@ -745,7 +777,7 @@ class Solver final : public SolverBase {
       WLR_CUDA(cudaGraphLaunch(it->second, stream_));
       launches_ += graph_launch_count_;
     } else {
-      iteration_body(xi, xo);
+      iteration_body(xi, xo, steady);
     }
     prev_ = xi;
     cur_ = xo;
@@ -795,7 +827,8 @@ class Solver final : public SolverBase {
   T *C_ = nullptr, *Z2_ = nullptr, *Z2prev_ = nullptr;
   double *B64_ = nullptr, *bpart_ = nullptr, *K64_ = nullptr, *prep_part_ = nullptr;
   float *Bh_ = nullptr, *Bl_ = nullptr;
-  unsigned int* prep_ticket_ = nullptr;
+  unsigned int *prep_ticket_ = nullptr, *eig_ticket_ = nullptr;
+  double* HP_ = nullptr;
   int nblk_prep_ = 0;
   bool eig_vsmem_ = false;
   T* G2_ = nullptr;
