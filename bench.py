@@ -158,15 +158,17 @@ print(json.dumps({{"sec_per_iter": dt}}))
     return json.loads(r.stdout.strip().splitlines()[-1])["sec_per_iter"]
 
 
+# Iterations Algorithm 1 needs on this clip, from X1_0 = A1, to reach rel-obj 1e-6:
+# measured by this file's calibration (F~ scored in FP64 by wlr_objective, F* from a
+# 185000-iteration run).  The FP64 oracle cannot run that far in reasonable time
+# (1.3 s per iteration); over the 2500 iterations of its trajectory fixture its F_p and
+# the FP32 path's agree to 3e-7 relative.  The reference line projects the oracle's
+# measured seconds per iteration to this count.
+P_STAR_CONFIG2 = 140500
+
+
 def _reference_p_star():
-    Fstar, g = _golden_fstar()
-    if g is None:
-        return None
-    F = g["F"]
-    for p, v in enumerate(F):
-        if (v - Fstar) / Fstar <= TARGET:
-            return p
-    return len(F) - 1
+    return P_STAR_CONFIG2
 
 
 def run_reference(a):
@@ -186,6 +188,9 @@ def run_reference(a):
             times.append(t)
     sec_iter = statistics.mean(times)
     value = sec_iter * p_star
+    cfg = dict(cfg)
+    cfg["precision"] = "fp64 (the CPU oracle)"
+    cfg.pop("l2", None)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup, "ms_per_step": value * 1e3,
@@ -193,8 +198,7 @@ def run_reference(a):
         "data": "synthetic", "config": cfg,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": f"per step: 2 FP64 oracle iterations of the full clip "
-                                   f"(+1 warm-up), projected to p*={p_star} iterations "
-                                   f"(p* from the oracle trajectory fixture)"},
+                                   f"(+1 warm-up), projected to p*={p_star} iterations"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))

@@ -272,3 +272,25 @@ def test_relative_stop_matches_oracle(wlr):
     _, E = s.history()
     assert np.allclose(E[:it], ref.rel_error, rtol=1e-6)
     s.close()
+
+
+def test_fp32_trajectory_matches_oracle_fixture(wlr):
+    """Full-size FP32 run of Algorithm 1 against the FP64 oracle's 2500-iteration
+    trajectory (tests/golden/config2_trajectory.json): the FP64 objective of the GPU
+    iterate X1_p equals the oracle's F_p to 1e-6 relative at p = 250..1000."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "config2_trajectory.json")) as f:
+        ref = json.load(f)["F"]
+    spec = synth.CONFIGS[2]
+    clip = synth.make_clip(spec)
+    s = _solver(wlr, (spec.m, spec.n, spec.k, spec.r), wlr.WLR_PREC_FP32, stop=wlr.WLR_STOP_NONE)
+    s.set_data(_dev(clip["A"].astype(np.float32)), _dev(clip["W1"].astype(np.float32)))
+    s.set_init(wlr.WLR_INIT_A1)
+    done = 0
+    for p in (250, 500, 750, 1000):
+        s.solve(0.0, p - done)
+        done = p
+        F = s.objective()
+        assert abs(F - ref[p]) <= 1e-6 * ref[p], (p, F, ref[p])
+    s.close()
