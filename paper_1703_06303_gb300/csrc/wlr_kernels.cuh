@@ -1090,12 +1090,27 @@ struct RowPassSmem {
   }
 };
 
+// Objective finalisation done by the last row_pass block (ticket != nullptr):
+// F_p = sum(wpart) + ||A2||^2 - sum(bpart) - sum_{c<s} theta_c into Fhist[*iter], *iter += 1.
+template <typename T>
+struct FinalizeArgs {
+  const double* bpart;
+  int nb;
+  const double* normA2;
+  const T* theta;
+  double* Fhist;
+  int hist_cap;
+  int* iter;
+  double* Fcur;
+  unsigned int* ticket;
+};
+
 template <typename T, int KMAX>
 __global__ void __launch_bounds__(256)
 row_pass(const T* __restrict__ A, int64_t lda, const T* __restrict__ W1, int64_t ldw,
          const T* __restrict__ X1old, const T* __restrict__ Z2, const T* __restrict__ Gm,
          const T* __restrict__ CV, int m, int n2, int k, int s, int NP, T* __restrict__ X1new,
-         double* __restrict__ wpart, int* __restrict__ err) {
+         double* __restrict__ wpart, int* __restrict__ err, FinalizeArgs<T> fin) {
   extern __shared__ unsigned char smem_raw[];
   constexpr bool kStage = RowPassSmem<T>::kStage;
   T* As = reinterpret_cast<T*>(smem_raw);   // [RP_BK][RP_BM]           (phase 1)
@@ -1314,6 +1329,33 @@ row_pass(const T* __restrict__ A, int64_t lda, const T* __restrict__ W1, int64_t
       __syncwarp();
     }
     if (bad) atomicOr(err, ERRBIT_NOT_SPD);
+  }
+  if (fin.ticket != nullptr) {
+    // the last block to finish adds the block partials (in block order) into F_p
+    __shared__ bool is_last;
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) is_last = atomicAdd(fin.ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (is_last) {
+      __threadfence();
+      double w = 0.0, bn = 0.0;
+      for (int e = tid; e < (int)gridDim.x; e += 256) w += __ldcg(&wpart[e]);
+      for (int e = tid; e < fin.nb; e += 256) bn += __ldcg(&fin.bpart[e]);
+      w = block_sum_double(w, sh);
+      __syncthreads();
+      bn = block_sum_double(bn, sh);
+      if (tid == 0) {
+        double t = 0.0;
+        for (int c = 0; c < s; ++c) t += (double)fin.theta[c];
+        const double F = w + (*fin.normA2 - bn - t);
+        const int p = *fin.iter;
+        if (p < fin.hist_cap) fin.Fhist[p] = F;
+        *fin.Fcur = F;
+        *fin.iter = p + 1;
+        *fin.ticket = 0u;
+      }
+    }
   }
 }
 

@@ -126,14 +126,15 @@ extern "C" wlr_status wlr_x1_update_noalloc(const float* A, int64_t lda, const f
   }
   wlr::prep_rowpass<float><<<ki, 128, 0, st>>>(C, Vs, ki, n2, s, G, CV);
   const size_t smem = wlr::RowPassSmem<float>::bytes(NP, ki, s);
+  const wlr::FinalizeArgs<float> nofin{nullptr, 0, nullptr, nullptr, nullptr, 0, nullptr, nullptr, nullptr};
   if (ki <= 8)
-    wlr::row_pass<float, 8><<<nblk, 256, smem, st>>>(A, lda, W1, ldw, X1, Z2, G, CV, mi, n2, ki, s, NP, X1_next, wpart, err);
+    wlr::row_pass<float, 8><<<nblk, 256, smem, st>>>(A, lda, W1, ldw, X1, Z2, G, CV, mi, n2, ki, s, NP, X1_next, wpart, err, nofin);
   else if (ki <= 16)
-    wlr::row_pass<float, 16><<<nblk, 256, smem, st>>>(A, lda, W1, ldw, X1, Z2, G, CV, mi, n2, ki, s, NP, X1_next, wpart, err);
+    wlr::row_pass<float, 16><<<nblk, 256, smem, st>>>(A, lda, W1, ldw, X1, Z2, G, CV, mi, n2, ki, s, NP, X1_next, wpart, err, nofin);
   else if (ki <= 32)
-    wlr::row_pass<float, 32><<<nblk, 256, smem, st>>>(A, lda, W1, ldw, X1, Z2, G, CV, mi, n2, ki, s, NP, X1_next, wpart, err);
+    wlr::row_pass<float, 32><<<nblk, 256, smem, st>>>(A, lda, W1, ldw, X1, Z2, G, CV, mi, n2, ki, s, NP, X1_next, wpart, err, nofin);
   else
-    wlr::row_pass<float, 64><<<nblk, 256, smem, st>>>(A, lda, W1, ldw, X1, Z2, G, CV, mi, n2, ki, s, NP, X1_next, wpart, err);
+    wlr::row_pass<float, 64><<<nblk, 256, smem, st>>>(A, lda, W1, ldw, X1, Z2, G, CV, mi, n2, ki, s, NP, X1_next, wpart, err, nofin);
   if (wterm) wlr::reduce_partials<double><<<1, 32, 0, st>>>(wpart, 1, nblk, 1, wterm, nullptr);
   if (status) store_err<<<1, 1, 0, st>>>(err, status);
   if (cudaGetLastError() != cudaSuccess) return fail(WLR_ERR_CUDA, "kernel launch failed");

@@ -65,6 +65,7 @@ class Solver final : public SolverBase {
     theta_ = dalloc<T>(bb);
     HP_ = dalloc<double>(2 * (size_t)bb * bb);
     eig_ticket_ = dalloc<unsigned int>(1);
+    fin_ticket_ = dalloc<unsigned int>(1);
     resid_ = dalloc<T>(bb);
     Vs_ = dalloc<T>((size_t)std::max(n2, 1) * std::max(s, 1));
     G_ = dalloc<T>((size_t)k * k);
@@ -88,6 +89,7 @@ class Solver final : public SolverBase {
     WLR_CUDA(cudaMemsetAsync(bpart_, 0, sizeof(double) * std::max(nblk_coef_, 1), stream_));
     WLR_CUDA(cudaMemsetAsync(prep_ticket_, 0, sizeof(unsigned int), stream_));
     WLR_CUDA(cudaMemsetAsync(eig_ticket_, 0, sizeof(unsigned int), stream_));
+    WLR_CUDA(cudaMemsetAsync(fin_ticket_, 0, sizeof(unsigned int), stream_));
     WLR_CUDA(cudaMemsetAsync(G_, 0, sizeof(T) * k * k, stream_));
     // dynamic shared memory limits
     set_smem((const void*)row_pass<T, 8>, RowPassSmem<T>::bytes(NP, k, s));
@@ -723,22 +725,19 @@ class Solver final : public SolverBase {
     const size_t smem = RowPassSmem<T>::bytes(NP, k, s);
     const int g = nblk_row_;
     {
-    Prof pf(this, "row_pass");
-    if (k <= 8)
-      row_pass<T, 8><<<g, 256, smem, stream_>>>(A_, lda_, W1_, ldw_, X1buf_[xi], Z2_, G_, CV_, m, n2, k, s, NP, X1buf_[xo], wpart_, err_);
-    else if (k <= 16)
-      row_pass<T, 16><<<g, 256, smem, stream_>>>(A_, lda_, W1_, ldw_, X1buf_[xi], Z2_, G_, CV_, m, n2, k, s, NP, X1buf_[xo], wpart_, err_);
-    else if (k <= 32)
-      row_pass<T, 32><<<g, 256, smem, stream_>>>(A_, lda_, W1_, ldw_, X1buf_[xi], Z2_, G_, CV_, m, n2, k, s, NP, X1buf_[xo], wpart_, err_);
-    else
-      row_pass<T, 64><<<g, 256, smem, stream_>>>(A_, lda_, W1_, ldw_, X1buf_[xi], Z2_, G_, CV_, m, n2, k, s, NP, X1buf_[xo], wpart_, err_);
+      Prof pf(this, "row_pass");
+      FinalizeArgs<T> fin{bpart_, n2 > 0 ? nblk_coef_ : 0, normA2_, theta_, Fhist_, hist_cap_, iter_, Fcur_,
+                          fin_ticket_};
+      if (k <= 8)
+        row_pass<T, 8><<<g, 256, smem, stream_>>>(A_, lda_, W1_, ldw_, X1buf_[xi], Z2_, G_, CV_, m, n2, k, s, NP, X1buf_[xo], wpart_, err_, fin);
+      else if (k <= 16)
+        row_pass<T, 16><<<g, 256, smem, stream_>>>(A_, lda_, W1_, ldw_, X1buf_[xi], Z2_, G_, CV_, m, n2, k, s, NP, X1buf_[xo], wpart_, err_, fin);
+      else if (k <= 32)
+        row_pass<T, 32><<<g, 256, smem, stream_>>>(A_, lda_, W1_, ldw_, X1buf_[xi], Z2_, G_, CV_, m, n2, k, s, NP, X1buf_[xo], wpart_, err_, fin);
+      else
+        row_pass<T, 64><<<g, 256, smem, stream_>>>(A_, lda_, W1_, ldw_, X1buf_[xi], Z2_, G_, CV_, m, n2, k, s, NP, X1buf_[xo], wpart_, err_, fin);
     }
-    {
-    Prof pf(this, "finalize_objective");
-    finalize_objective<T><<<1, 256, 0, stream_>>>(wpart_, g, bpart_, n2 > 0 ? nblk_coef_ : 0, normA2_, theta_,
-                                                  s, Fhist_, hist_cap_, iter_, Fcur_);
-    }
-    count(2);
+    count(1);
     // keep the factors of X1_p for Error_p
     if (n2 > 0)
       WLR_CUDA(cudaMemcpyAsync(Z2prev_, Z2_, sizeof(T) * (size_t)n2 * NP, cudaMemcpyDeviceToDevice, stream_));
@@ -827,7 +826,7 @@ class Solver final : public SolverBase {
   T *C_ = nullptr, *Z2_ = nullptr, *Z2prev_ = nullptr;
   double *B64_ = nullptr, *bpart_ = nullptr, *K64_ = nullptr, *prep_part_ = nullptr;
   float *Bh_ = nullptr, *Bl_ = nullptr;
-  unsigned int *prep_ticket_ = nullptr, *eig_ticket_ = nullptr;
+  unsigned int *prep_ticket_ = nullptr, *eig_ticket_ = nullptr, *fin_ticket_ = nullptr;
   double* HP_ = nullptr;
   int nblk_prep_ = 0;
   bool eig_vsmem_ = false;
