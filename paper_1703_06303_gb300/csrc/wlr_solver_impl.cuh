@@ -5,8 +5,11 @@
 #include <algorithm>
 #include <type_traits>
 
+#include <cudaTypedefs.h>
+
 #include "wlr_kernels.cuh"
 #include "wlr_solver.cuh"
+#include "wlr_tc.cuh"
 
 namespace wlr {
 
@@ -36,6 +39,7 @@ class Solver final : public SolverBase {
     size_t part_elems = std::max((size_t)ch_S1_.nch * k * k, (size_t)ch_T_.nch * L);
     part_elems = std::max(part_elems, (size_t)ch_K_.nch * n2 * n2);
     part64_ = dalloc<double>(std::max<size_t>(part_elems, 1));
+    part_elems_ = std::max<size_t>(part_elems, 1);
     S2T_ = dalloc<double>(L);
     R1inv_ = dalloc<T>((size_t)k * k);
     Nm_ = dalloc<T>((size_t)k * k);
@@ -80,6 +84,7 @@ class Solver final : public SolverBase {
     Fcur_ = dalloc<double>(1);
     iter_ = dalloc<int>(1);
     err_ = dalloc<int>(1);
+    if (std::is_same<T, float>::value && n2 > 0) setup_tc();
     WLR_CUDA(cudaMemsetAsync(Z2_, 0, sizeof(T) * std::max<size_t>((size_t)n2 * NP, 1), stream_));
     WLR_CUDA(cudaMemsetAsync(Z2prev_, 0, sizeof(T) * std::max<size_t>((size_t)n2 * NP, 1), stream_));
     WLR_CUDA(cudaMemsetAsync(err_, 0, sizeof(int), stream_));
@@ -546,6 +551,71 @@ class Solver final : public SolverBase {
     for (size_t q = 0; q < n; ++q) dst[q] = (double)tmp[q];
   }
 
+  // ------------------------------------------------------------------ tensor-core Gram
+  // Q1^T [Q1 A2] on tcgen05 (FP32 path): TF32-split copies of A2 (made in setup) and of Q1
+  // (each iteration), TMA tensor maps built once for these library-owned buffers.
+  void setup_tc() {
+    const int m = d_.m, k = d_.k, n2 = d_.n2;
+    if (k > tc::TN) return;  // the transposed kernel takes up to 32 columns of X
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &fn, cudaEnableDefault, &q) != cudaSuccess || !fn) {
+      cudaGetLastError();
+      return;
+    }
+    auto enc = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    ld4_ = ((m + 3) / 4) * 4;
+    A2h_ = dalloc<float>((size_t)ld4_ * n2);
+    A2l_ = dalloc<float>((size_t)ld4_ * n2);
+    Q1h_ = dalloc<float>((size_t)ld4_ * k);
+    Q1l_ = dalloc<float>((size_t)ld4_ * k);
+    auto mk = [&](CUtensorMap* map, const float* p, int cols, int boxc) {
+      cuuint64_t dims[2] = {(cuuint64_t)m, (cuuint64_t)cols};
+      cuuint64_t strides[1] = {(cuuint64_t)ld4_ * 4};
+      cuuint32_t box[2] = {32, (cuuint32_t)boxc};
+      cuuint32_t es[2] = {1, 1};
+      return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)p, dims, strides, box, es,
+                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
+    bool ok = mk(&mA2h_, A2h_, n2, 128) && mk(&mA2l_, A2l_, n2, 128) && mk(&mQh128_, Q1h_, k, 128) &&
+              mk(&mQl128_, Q1l_, k, 128) && mk(&mQh32_, Q1h_, k, tc::TN) && mk(&mQl32_, Q1l_, k, tc::TN);
+    if (!ok) return;
+    ch_tc_ = chunking(m, (size_t)(1 + cdiv(n2, 128)), 152);
+    const size_t need = (size_t)ch_tc_.nch * ((size_t)k * k + (size_t)k * n2);
+    if (need > part_elems_) {
+      part64_ = dalloc<double>(need);
+      part_elems_ = need;
+    }
+    WLR_CUDA(cudaFuncSetAttribute((const void*)tc::gram_tf32x3_t, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  tc::T_SMEM_BYTES));
+    use_tc_ = true;
+  }
+  void tc_split_a2() {
+    if (!use_tc_) return;
+    const int m = d_.m, k = d_.k, n2 = d_.n2;
+    tc::split_tf32<<<grid1d((int64_t)m * n2), 256, 0, stream_>>>((const float*)(A_ + (int64_t)k * lda_), lda_, m, n2,
+                                                                  A2h_, A2l_, ld4_);
+    count(1);
+  }
+  // part64 <- chunk partials of Q1^T [Q1 A2] with Q1 = X1 Rpre (k x (k + n2) per chunk)
+  void tc_gram(const T* X1, const T* Rpre) {
+    const int m = d_.m, k = d_.k, n2 = d_.n2;
+    {
+      Prof pf(this, "form_q_split");
+      tc::form_q_split<<<grid1d((int64_t)m * k), 256, sizeof(float) * k * k, stream_>>>(
+          (const float*)X1, m, (const float*)Rpre, m, k, Q1h_, Q1l_, ld4_);
+    }
+    {
+      Prof pf(this, "gram_tf32x3_t");
+      dim3 g(1 + cdiv(n2, 128), ch_tc_.nch);
+      tc::gram_tf32x3_t<<<g, 192, tc::T_SMEM_BYTES, stream_>>>(mQh128_, mQl128_, mA2h_, mA2l_, mQh32_, mQl32_, m, k,
+                                                               k, n2, ch_tc_.rows, part64_,
+                                                               (int64_t)k * k + (int64_t)k * n2, err_);
+    }
+    count(2);
+  }
+
   // ------------------------------------------------------------------ kernels
   // part64 <- chunked partials of X^T [Y1 Y2] (Y1: q1 columns, Y2: the rest).  With Rq,
   // X and Y1 are Q1 = X Rq (formed inside the kernel; float path only).
@@ -592,6 +662,7 @@ class Solver final : public SolverBase {
     count(2);
     gram(A2, lda_, A2, lda_, n2, nullptr, 0, n2, n2, (int64_t)n2 * n2, ch_K_);
     reduce64((int64_t)n2 * n2, ch_K_.nch, (int64_t)n2 * n2, K64_);
+    tc_split_a2();
   }
   double* wpart_scratch(int n) {
     if (!sumsq_part_) sumsq_part_ = dalloc<double>(std::max(n, 304));
@@ -617,7 +688,12 @@ class Solver final : public SolverBase {
       Rpre = R1inv_;
     }
     const int64_t L = (int64_t)k * k + (int64_t)k * n2;
-    if (std::is_same<T, float>::value) {
+    int nchT = ch_T_.nch;
+    if (use_tc_) {
+      // tensor cores (tcgen05 + TMA), Q1 = X1 Rpre split into TF32 hi + lo
+      tc_gram(X1, Rpre);
+      nchT = ch_tc_.nch;
+    } else if (std::is_same<T, float>::value) {
       // Q1 = X1 Rpre formed slab by slab inside the Gram kernel
       gram(X1, m, nullptr, 0, k, A2, lda_, k, k + n2, L, ch_T_, Rpre);
     } else {
@@ -629,7 +705,7 @@ class Solver final : public SolverBase {
       gram(Q1_, m, Q1_, m, k, A2, lda_, k, k + n2, L, ch_T_);
     }
     // Q1^T [Q1 A2] summed over the chunks by all SMs; chol2 and coef read the sum
-    reduce64(L, ch_T_.nch, L, S2T_);
+    reduce64(L, nchT, L, S2T_);
     {
       Prof pf(this, "chol2");
       chol2_kernel<T><<<1, 256, 3 * sizeof(T) * k * k, stream_>>>(S2T_, 1, L, k, Rpre, Nm_, Rinv_, err_);
@@ -828,6 +904,13 @@ class Solver final : public SolverBase {
   float *Bh_ = nullptr, *Bl_ = nullptr;
   unsigned int *prep_ticket_ = nullptr, *eig_ticket_ = nullptr, *fin_ticket_ = nullptr;
   double* HP_ = nullptr;
+  // tensor-core Gram (FP32 path)
+  bool use_tc_ = false;
+  int64_t ld4_ = 0;
+  size_t part_elems_ = 0;
+  float *A2h_ = nullptr, *A2l_ = nullptr, *Q1h_ = nullptr, *Q1l_ = nullptr;
+  CUtensorMap mA2h_, mA2l_, mQh128_, mQl128_, mQh32_, mQl32_;
+  Chunk ch_tc_{1, 32};
   int nblk_prep_ = 0;
   bool eig_vsmem_ = false;
   T* G2_ = nullptr;
