@@ -691,10 +691,19 @@ eig_mult(const T* __restrict__ G2, const T* __restrict__ V, int n2, int b, T* __
   __syncthreads();
   if (!is_last) return;
   __threadfence();
+  // summed in T: the Ritz problem is solved in T anyway (and FP64 adds are slow here)
   for (int e = threadIdx.x; e < 2 * b * b; e += blockDim.x) {
-    double v = 0.0;
-    for (int c = 0; c < (int)gridDim.x; ++c) v += (double)__ldcg(&part[(int64_t)c * 2 * b * b + e]);
-    HP[e] = v;
+    T v0 = T(0), v1 = T(0), v2 = T(0), v3 = T(0);
+    const int nb = (int)gridDim.x;
+    int c = 0;
+    for (; c + 4 <= nb; c += 4) {
+      v0 += __ldcg(&part[(int64_t)c * 2 * b * b + e]);
+      v1 += __ldcg(&part[(int64_t)(c + 1) * 2 * b * b + e]);
+      v2 += __ldcg(&part[(int64_t)(c + 2) * 2 * b * b + e]);
+      v3 += __ldcg(&part[(int64_t)(c + 3) * 2 * b * b + e]);
+    }
+    for (; c < nb; ++c) v0 += __ldcg(&part[(int64_t)c * 2 * b * b + e]);
+    HP[e] = (double)((v0 + v1) + (v2 + v3));
   }
   if (threadIdx.x == 0) *ticket = 0u;
 }
@@ -885,10 +894,11 @@ eig_small(const double* __restrict__ HP, int b, int max_sweeps, T* __restrict__ 
   for (int t = 0; t < b; ++t) {
     T d = P[t][t];
     if (!(d > T(0)) || !wfinite(d)) { bad = true; d = T(1); }
-    const T lt = wsqrt(d);
+    const T rl = wrsqrt(d);
+    const T lt = d * rl;
     __syncthreads();
     if (lane == 0) P[t][t] = lt;
-    for (int i = t + 1 + lane; i < b; i += NT) P[i][t] /= lt;
+    for (int i = t + 1 + lane; i < b; i += NT) P[i][t] *= rl;
     __syncthreads();
     for (int i = t + 1 + lane; i < b; i += NT)
       for (int j = t + 1; j <= i; ++j) P[i][j] -= P[i][t] * P[j][t];
@@ -901,7 +911,7 @@ eig_small(const double* __restrict__ HP, int b, int max_sweeps, T* __restrict__ 
     for (int a = b - 1; a >= 0; --a) {
       T v = a == c ? T(1) : T(0);
       for (int l = a + 1; l <= c; ++l) v -= P[l][a] * H[l][c];
-      H[a][c] = a <= c ? v / P[a][a] : T(0);
+      H[a][c] = a <= c ? v * (T(1) / P[a][a]) : T(0);
     }
   }
   __syncthreads();

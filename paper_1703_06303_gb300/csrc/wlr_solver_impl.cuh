@@ -737,7 +737,7 @@ class Solver final : public SolverBase {
     }
     {
       Prof pf(this, "eig_small");
-      eig_small<T><<<1, 128, 0, stream_>>>(HP_, b, cold ? (sizeof(T) == 4 ? 12 : 24) : (sizeof(T) == 4 ? 2 : 6), Y_, Mv_, Mz_,
+      eig_small<T><<<1, 128, 0, stream_>>>(HP_, b, cold ? (sizeof(T) == 4 ? 12 : 24) : (sizeof(T) == 4 ? 1 : 6), Y_, Mv_, Mz_,
                                           theta_, resid_, err_);
     }
     Prof pf(this, "eig_update");
