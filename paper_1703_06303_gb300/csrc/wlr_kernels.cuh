@@ -16,7 +16,7 @@
 //   a4  E = A1 o W1 o W1 + A2 C^T - U_s (V_s^T C^T), U_s = A2 V_s - X1 (C V_s)  = (A2 - D) C^T
 //   a5  X1(i,:) = E(i,:) (diag(W1(i,:)^2) + C C^T)^{-1}   prep_gram, row_pass
 //   a6  F_p = ||(A1-X1) o W1||^2 + ||A2||^2 - ||B||^2 - sum_{j<=r-k} sigma_j^2
-//                                                         finalize_objective, x2_pass (exact)
+//                                                         row_pass (last block), x2_pass (exact)
 #pragma once
 
 #include <type_traits>
@@ -1040,19 +1040,34 @@ prep_gram(const T* __restrict__ Z2, int n2, int k, int s, int NP, double* __rest
 //   Y = A2(rows,:) [C^T | V_s]                     (GEMM over n2, Z2 row-major n2 x NP)
 //   U = Y_V - X1old(rows,:) (C V_s)                (= rows of U_s Sigma_s = P_perp A2 V_s)
 //   E = A1 o W1^2 + Y_C - U (C V_s)^T              (= A1 o W1 o W1 + (A2 - D) C^T)
-//   X1new(i,:) solves (diag(W1(i,:)^2) + C C^T) x = E(i,:)^T, one group of KMAX/2 lanes
-//   per row, the k x k matrix held column-wise in registers (each lane owns two
-//   columns), right-looking Cholesky with shuffles, then two triangular solves.
+//   X1new(i,:) solves (diag(W1(i,:)^2) + C C^T) x = E(i,:)^T
 // Also the block's partial of ||(A1 - X1old) o W1||_F^2.
 constexpr int RP_BM = 64;
 constexpr int RP_BK = 32;
 
-// Row-solve layout (phase 3 of row_pass).  LG lanes factor one row's k x k system,
-// held in shared memory as a square column-major block with an even leading dimension
-// ld (so the diagonal walk j*ld + j + i of the trailing update has odd stride ld + 1
-// across lanes) and a per-row pitch P = LG*(ld + 1) (mod 32), which puts the 32 lanes
-// of a warp on 32 distinct banks.  R rows are solved per pass, R limited by a 96 KB
-// budget and rounded to whole warps.
+// Compile-time size KP of the row systems: the smallest of 8, 16, 20, 24, 32, 64 that
+// holds k (k <= 64).
+inline int row_kp(int k) {
+  return k <= 8 ? 8 : k <= 16 ? 16 : k <= 20 ? 20 : k <= 24 ? 24 : k <= 32 ? 32 : 64;
+}
+
+// Register row solve (phase 3 of row_pass) for a system padded to KP x KP: LG lanes
+// share one row system, lane g holding the NS = KP / LG matrix rows q = g + LG*s in
+// registers.  Off for double beyond KP = 16 and for KP = 64 (register budget), where the
+// shared-memory solve below runs instead.
+template <typename T, int KP>
+struct RegSolve {
+  static constexpr bool on = sizeof(T) == 4 ? KP <= 32 : KP <= 16;
+  static constexpr int LG = (KP <= 8 || (sizeof(T) == 4 && KP <= 20)) ? 4 : 8;
+  static constexpr int NS = KP / LG;
+};
+
+// Shared-memory row-solve layout (phase 3 of row_pass when the register solve is off).
+// LG lanes factor one row's k x k system, held in shared memory as a square
+// column-major block with an even leading dimension ld (so the diagonal walk
+// j*ld + j + i of the trailing update has odd stride ld + 1 across lanes) and a per-row
+// pitch P = LG*(ld + 1) (mod 32), which puts the 32 lanes of a warp on 32 distinct banks.
+// R rows are solved per pass, R limited by a 96 KB budget and rounded to whole warps.
 template <typename T, int KMAX>
 struct RowSolveLayout {
   static constexpr int LG = KMAX <= 8 ? 4 : (KMAX <= 32 ? 8 : 32);
@@ -1073,30 +1088,36 @@ struct RowSolveLayout {
 };
 
 // Shared memory of row_pass.  Region 0 holds the phase-1 staging (A2 and Z2 slabs), then
-// U (phase 2), then the row systems (phase 3); the rows of X1old, A1 and W1 are staged
-// for float only (double reads them from global memory to keep within 227 KB).
+// U (phase 2), then, for the shared-memory solve, the row systems (phase 3); the rows of
+// X1old, A1 and W1 are staged for float only (double reads them from global memory to
+// keep within 227 KB).
 template <typename T>
 struct RowPassSmem {
   static constexpr bool kStage = sizeof(T) == 4;
   static constexpr int kStages = sizeof(T) == 4 ? 4 : 2;   // phase-1 pipeline depth
-  template <int KMAX>
+  template <int KP>
   __host__ __device__ static size_t region0(int NP, int k) {
     const size_t stage = (size_t)kStages * ((size_t)RP_BK * RP_BM + (size_t)RP_BK * NP);
     const size_t us = (size_t)RP_BM * (EIG_BMAX + 1);
-    const size_t rs = (size_t)RowSolveLayout<T, KMAX>::rows(k) * RowSolveLayout<T, KMAX>::pitch(k);
+    const size_t rs = RegSolve<T, KP>::on ? 0
+                      : (size_t)RowSolveLayout<T, KP>::rows(k) * RowSolveLayout<T, KP>::pitch(k);
     size_t r0 = stage > us ? stage : us;
     return r0 > rs ? r0 : rs;
   }
-  template <int KMAX>
+  template <int KP>
   static size_t bytes_k(int NP, int k, int s) {
-    return sizeof(T) * (region0<KMAX>(NP, k) + (size_t)RP_BM * (NP + 1) + (size_t)k * k +
+    return sizeof(T) * (region0<KP>(NP, k) + (size_t)RP_BM * (NP + 1) + (size_t)k * k +
                         (size_t)k * (s > 0 ? s : 1) + (kStage ? 3 * (size_t)RP_BM * (k + 1) : 0));
   }
   static size_t bytes(int NP, int k, int s) {
-    if (k <= 8) return bytes_k<8>(NP, k, s);
-    if (k <= 16) return bytes_k<16>(NP, k, s);
-    if (k <= 32) return bytes_k<32>(NP, k, s);
-    return bytes_k<64>(NP, k, s);
+    switch (row_kp(k)) {
+      case 8: return bytes_k<8>(NP, k, s);
+      case 16: return bytes_k<16>(NP, k, s);
+      case 20: return bytes_k<20>(NP, k, s);
+      case 24: return bytes_k<24>(NP, k, s);
+      case 32: return bytes_k<32>(NP, k, s);
+      default: return bytes_k<64>(NP, k, s);
+    }
   }
 };
 
@@ -1115,7 +1136,137 @@ struct FinalizeArgs {
   unsigned int* ticket;
 };
 
-template <typename T, int KMAX>
+// 16-byte asynchronous copy global -> shared (zero-filled beyond src_bytes).
+__device__ __forceinline__ void cp_async16(void* dst_smem, const void* src, int src_bytes) {
+  const unsigned dst = (unsigned)__cvta_generic_to_shared(dst_smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src),
+               "r"(src_bytes));
+}
+
+// N consecutive shared-memory elements, in the widest aligned vector loads.
+template <int N>
+__device__ __forceinline__ void load_n(float (&z)[N], const float* p) {
+  if constexpr (N % 4 == 0) {
+#pragma unroll
+    for (int v = 0; v < N; v += 4) {
+      const float4 t = *reinterpret_cast<const float4*>(p + v);
+      z[v] = t.x; z[v + 1] = t.y; z[v + 2] = t.z; z[v + 3] = t.w;
+    }
+  } else if constexpr (N % 2 == 0) {
+#pragma unroll
+    for (int v = 0; v < N; v += 2) {
+      const float2 t = *reinterpret_cast<const float2*>(p + v);
+      z[v] = t.x; z[v + 1] = t.y;
+    }
+  } else {
+#pragma unroll
+    for (int v = 0; v < N; ++v) z[v] = p[v];
+  }
+}
+template <int N>
+__device__ __forceinline__ void load_n(double (&z)[N], const double* p) {
+  if constexpr (N % 2 == 0) {
+#pragma unroll
+    for (int v = 0; v < N; v += 2) {
+      const double2 t = *reinterpret_cast<const double2*>(p + v);
+      z[v] = t.x; z[v + 1] = t.y;
+    }
+  } else {
+#pragma unroll
+    for (int v = 0; v < N; ++v) z[v] = p[v];
+  }
+}
+
+__device__ __forceinline__ float wrcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double wrcp(double x) { return 1.0 / x; }
+
+// Phase 1 of row_pass: Ys[r][c] = sum_j A2(i0 + r, j) Z2(j, c) for the block's 64 rows and
+// the NP = 16 * NPU columns, with A2 and Z2 streamed through shared memory in slabs of 32
+// columns by an S-stage cp.async pipeline (S - 1 slabs in flight while one is consumed).
+// Thread (rg, cg) = (tid / 16, tid % 16) owns rows 4 rg .. 4 rg + 3 and columns
+// cg NPU .. cg NPU + NPU - 1: one 4-row vector of A2 and one NPU-vector of Z2 per step.
+// vec: A2 and lda allow 16-byte copies (rows of a slab column move 16 bytes at a time).
+template <typename T, int NPU>
+__device__ __forceinline__ void rp_phase1(const T* __restrict__ A2, int64_t lda,
+                                          const T* __restrict__ Z2, int m, int n2, int i0,
+                                          bool vec, T* __restrict__ As, T* __restrict__ Ys) {
+  constexpr int NP = 16 * NPU;
+  constexpr int S = RowPassSmem<T>::kStages;
+  constexpr int CH = 16 / sizeof(T);                 // elements per 16-byte chunk
+  constexpr int slab = RP_BK * RP_BM + RP_BK * NP;   // elements per stage
+  const int tid = threadIdx.x;
+  const int cg = tid & 15, rg = tid >> 4;
+  T acc[4][NPU];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < NPU; ++v) acc[u][v] = T(0);
+  const int nsl = (n2 + RP_BK - 1) / RP_BK;
+  auto issue = [&](int sl) {
+    if (sl < nsl) {
+      T* As_ = As + (size_t)(sl % S) * slab;
+      T* Zs_ = As_ + RP_BK * RP_BM;
+      const int j0 = sl * RP_BK;
+      if (vec) {
+        for (int e = tid; e < RP_BK * RP_BM / CH; e += 256) {
+          const int rc = e % (RP_BM / CH), kk = e / (RP_BM / CH);
+          const int i = i0 + CH * rc, j = j0 + kk;
+          T* dst = As_ + kk * RP_BM + CH * rc;
+          if (j >= n2 || i >= m) {
+            cp_async16(dst, A2, 0);
+          } else if (i + CH <= m) {
+            cp_async16(dst, A2 + i + (int64_t)j * lda, 16);
+          } else {
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+              const bool ok = i + c < m;
+              cp_async_elem(dst + c, ok ? A2 + i + c + (int64_t)j * lda : A2, ok);
+            }
+          }
+        }
+      } else {
+        for (int e = tid; e < RP_BK * RP_BM; e += 256) {
+          const int r = e % RP_BM, kk = e / RP_BM;
+          const int i = i0 + r, j = j0 + kk;
+          const bool ok = i < m && j < n2;
+          cp_async_elem(As_ + kk * RP_BM + r, ok ? A2 + i + (int64_t)j * lda : A2, ok);
+        }
+      }
+      for (int e = tid; e < RP_BK * NP / CH; e += 256) {
+        const bool ok = j0 + (CH * e) / NP < n2;
+        cp_async16(Zs_ + CH * e, ok ? Z2 + (int64_t)j0 * NP + CH * e : Z2, ok ? 16 : 0);
+      }
+    }
+    cp_async_commit();
+  };
+#pragma unroll 1
+  for (int sl = 0; sl < S - 1; ++sl) issue(sl);
+#pragma unroll 1
+  for (int sl = 0; sl < nsl; ++sl) {
+    cp_async_wait<S - 2>();
+    __syncthreads();
+    issue(sl + S - 1);
+    const T* As_ = As + (size_t)(sl % S) * slab + 4 * rg;
+    const T* Zs_ = As + (size_t)(sl % S) * slab + RP_BK * RP_BM + cg * NPU;
+#pragma unroll 8
+    for (int kk = 0; kk < RP_BK; ++kk) {
+      T a[4], z[NPU];
+      load4(a, As_ + kk * RP_BM);
+      load_n<NPU>(z, Zs_ + kk * NP);
+#pragma unroll
+      for (int v = 0; v < NPU; ++v)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[u][v] = fma(a[u], z[v], acc[u][v]);
+    }
+  }
+  cp_async_wait<0>();
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < NPU; ++v) Ys[(4 * rg + u) * (NP + 1) + cg * NPU + v] = acc[u][v];
+}
+
+template <typename T, int KP>
 __global__ void __launch_bounds__(256)
 row_pass(const T* __restrict__ A, int64_t lda, const T* __restrict__ W1, int64_t ldw,
          const T* __restrict__ X1old, const T* __restrict__ Z2, const T* __restrict__ Gm,
@@ -1123,11 +1274,10 @@ row_pass(const T* __restrict__ A, int64_t lda, const T* __restrict__ W1, int64_t
          double* __restrict__ wpart, int* __restrict__ err, FinalizeArgs<T> fin) {
   extern __shared__ unsigned char smem_raw[];
   constexpr bool kStage = RowPassSmem<T>::kStage;
-  T* As = reinterpret_cast<T*>(smem_raw);   // [RP_BK][RP_BM]           (phase 1)
-  T* Zs = As + RP_BK * RP_BM;               // [RP_BK][NP]              (phase 1)
-  T* Us = As;                               // [RP_BM][EIG_BMAX+1]      (phase 2)
-  T* Ms = As;                               // row systems              (phase 3)
-  T* Ys = As + RowPassSmem<T>::template region0<KMAX>(NP, k);  // [RP_BM][NP+1]
+  T* As = reinterpret_cast<T*>(smem_raw);   // phase-1 stages               (phase 1)
+  T* Us = As;                               // [RP_BM][EIG_BMAX+1]          (phase 2)
+  T* Ms = As;                               // shared-memory row systems    (phase 3)
+  T* Ys = As + RowPassSmem<T>::template region0<KP>(NP, k);  // [RP_BM][NP+1]
   T* Gs = Ys + RP_BM * (NP + 1);            // [k][k]
   T* CVs = Gs + k * k;                      // [k][s]
   T* Xo = CVs + k * (s > 0 ? s : 1);        // [RP_BM][k+1]  X1old rows (float)
@@ -1138,7 +1288,6 @@ row_pass(const T* __restrict__ A, int64_t lda, const T* __restrict__ W1, int64_t
   const int tid = threadIdx.x;
   const int i0 = blockIdx.x * RP_BM;
   const T* A2 = A + (int64_t)k * lda;
-  const int NPU = NP / 16;
   const int kp = k + 1;
   // row r of the block, column a, of X1old / A1 / W1 (zero / one outside the matrix)
   auto xo_at = [&](int r, int a) -> T {
@@ -1168,68 +1317,18 @@ row_pass(const T* __restrict__ A, int64_t lda, const T* __restrict__ W1, int64_t
     }
   }
 
-  // ---- phase 1: Y = A2 rows * Z2 in slabs of 32 columns, an S-stage cp.async pipeline
-  // (S - 1 slabs in flight while one is consumed; S = 4 for float, 2 for double).  Warp w covers rows 32 (w % 2) .. +31
-  // and the column quarter w / 2; lane (rg, cq) = (lane % 8, lane / 8) owns 4 rows x NPU
-  // columns, so a warp reads one 128-byte row segment of A2 and 4 words of Z2 per step.
+  // ---- phase 1: Y = A2 rows * Z2
   {
-    constexpr int S = RowPassSmem<T>::kStages;
-    const int slab = RP_BK * RP_BM + RP_BK * NP;   // elements per stage
-    const int lane = tid & 31, w = tid >> 5;
-    const int rg = lane & 7, cq = lane >> 3;
-    const int row0 = 32 * (w & 1) + 4 * rg;
-    const int col0 = (w >> 1) * 4 * NPU + cq;     // columns col0 + 4 v, v < NPU
-    T acc[4][6];
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-      for (int v = 0; v < 6; ++v) acc[u][v] = T(0);
-    const int nsl = (n2 + RP_BK - 1) / RP_BK;
-    auto issue = [&](int sl) {
-      if (sl < nsl) {
-        T* As_ = As + (size_t)(sl % S) * slab;
-        T* Zs_ = As_ + RP_BK * RP_BM;
-        const int j0 = sl * RP_BK;
-        for (int e = tid; e < RP_BK * RP_BM; e += 256) {
-          const int r = e % RP_BM, kk = e / RP_BM;
-          const int i = i0 + r, j = j0 + kk;
-          const bool ok = i < m && j < n2;
-          cp_async_elem(As_ + kk * RP_BM + r, ok ? A2 + i + (int64_t)j * lda : A2, ok);
-        }
-        for (int e = tid; e < RP_BK * NP; e += 256) {
-          const bool ok = j0 + e / NP < n2;
-          cp_async_elem(Zs_ + e, ok ? Z2 + (int64_t)j0 * NP + e : Z2, ok);
-        }
-      }
-      cp_async_commit();
-    };
-    for (int sl = 0; sl < S - 1; ++sl) issue(sl);
-    for (int sl = 0; sl < nsl; ++sl) {
-      cp_async_wait<S - 2>();
-      __syncthreads();
-      issue(sl + S - 1);
-      const T* As_ = As + (size_t)(sl % S) * slab;
-      const T* Zs_ = As_ + RP_BK * RP_BM;
-#pragma unroll 4
-      for (int kk = 0; kk < RP_BK; ++kk) {
-        T a[4];
-        load4(a, As_ + kk * RP_BM + row0);
-#pragma unroll
-        for (int v = 0; v < 6; ++v) {
-          if (v < NPU) {  // uniform: only the live column groups cost FMAs
-            const T z = Zs_[kk * NP + col0 + 4 * v];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) acc[u][v] = fma(a[u], z, acc[u][v]);
-          }
-        }
-      }
+    const bool vec = ((reinterpret_cast<uintptr_t>(A2) & 15) == 0) &&
+                     (((uint64_t)lda * sizeof(T)) % 16 == 0);
+    switch (NP / 16) {
+      case 1: rp_phase1<T, 1>(A2, lda, Z2, m, n2, i0, vec, As, Ys); break;
+      case 2: rp_phase1<T, 2>(A2, lda, Z2, m, n2, i0, vec, As, Ys); break;
+      case 3: rp_phase1<T, 3>(A2, lda, Z2, m, n2, i0, vec, As, Ys); break;
+      case 4: rp_phase1<T, 4>(A2, lda, Z2, m, n2, i0, vec, As, Ys); break;
+      case 5: rp_phase1<T, 5>(A2, lda, Z2, m, n2, i0, vec, As, Ys); break;
+      default: rp_phase1<T, 6>(A2, lda, Z2, m, n2, i0, vec, As, Ys); break;
     }
-    cp_async_wait<0>();
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-      for (int v = 0; v < 6; ++v)
-        if (v < NPU) Ys[(row0 + u) * (NP + 1) + col0 + 4 * v] = acc[u][v];
   }
   __syncthreads();
 
@@ -1260,17 +1359,100 @@ row_pass(const T* __restrict__ A, int64_t lda, const T* __restrict__ W1, int64_t
   if (tid == 0) wpart[blockIdx.x] = wsum;
   __syncthreads();
 
-  // ---- phase 3: row solves.  A group of LG lanes factors one row's system
-  // M = diag(W1(i,:)^2) + G (lower triangle, right-looking Cholesky: at step t the lanes
-  // scale column t, then each lane updates its own columns j > t down from the
-  // diagonal), then runs the two triangular solves on E(i,:) in place.
-  {
-    using Lay = RowSolveLayout<T, KMAX>;
+  // ---- phase 3: row solves M x = e, M = diag(W1(i,:)^2) + C C^T (symmetric positive
+  // definite), e = E(i,:)^T.
+  bool bad = false;
+  if constexpr (RegSolve<T, KP>::on) {
+    // Symmetric Gaussian elimination (LDL^T, no square roots) on the system padded to
+    // KP x KP with an identity block.  Step t: the pivot d_t = M(t,t) and the entries
+    // M(j,t) of column t (j > t) are broadcast from the lanes holding rows t and j; every
+    // row q > t takes M(q,j) -= M(q,t) M(j,t) / d_t for all j > t and
+    // e_q -= M(q,t) e_t / d_t.  Row t is left as it stands after step t - 1, which is row t
+    // of the upper factor U = D L^T, so the back substitution
+    // x_t = (e_t - sum_{j>t} U(t,j) x_j) / d_t reads it from the same registers.
+    constexpr int LG = RegSolve<T, KP>::LG, NS = RegSolve<T, KP>::NS;
+    constexpr int GPB = 256 / LG;                  // row systems per pass
+    constexpr unsigned FULL = 0xffffffffu;
+    const int g = tid % LG, grp = tid / LG;
+#pragma unroll 1
+    for (int base = 0; base < RP_BM; base += GPB) {
+      const int r = base + grp;                    // GPB divides RP_BM: r < RP_BM
+      const bool active = i0 + r < m;
+      T M[NS][KP], e[NS], rd[NS], acc[NS], x[NS];
+#pragma unroll
+      for (int sl = 0; sl < NS; ++sl) {
+        const int q = g + LG * sl;
+        const bool qk = q < k;
+        const T w = (active && qk) ? w1_at(r, q) : T(1);
+        const T dq = qk ? w * w : T(1);
+#pragma unroll
+        for (int j = 0; j < KP; ++j) {
+          const T gv = (qk && j < k) ? Gs[q + j * k] : T(0);
+          M[sl][j] = q == j ? gv + dq : gv;
+        }
+        e[sl] = (active && qk) ? Ys[r * (NP + 1) + q] : T(0);
+        rd[sl] = T(1);
+        acc[sl] = T(0);
+        x[sl] = T(0);
+      }
+#pragma unroll
+      for (int t = 0; t < KP; ++t) {
+        if (t < k) {
+          const int st = t / LG, ot = t % LG;
+          T d = __shfl_sync(FULL, M[st][t], ot, LG);
+          if (!(d > T(0)) || !wfinite(d)) {
+            bad = bad || active;
+            d = T(1);
+          }
+          const T rdt = wrcp(d);
+          if (g == ot) rd[st] = rdt;
+          const T et = __shfl_sync(FULL, e[st], ot, LG);
+          T f[NS];
+#pragma unroll
+          for (int sl = 0; sl < NS; ++sl) {
+            f[sl] = (g + LG * sl > t) ? M[sl][t] * rdt : T(0);
+            e[sl] = fma(-f[sl], et, e[sl]);
+          }
+#pragma unroll
+          for (int j = 1; j < KP; ++j) {
+            if (j > t) {
+              const T mj = __shfl_sync(FULL, M[j / LG][t], j % LG, LG);
+#pragma unroll
+              for (int sl = 0; sl < NS; ++sl) M[sl][j] = fma(-f[sl], mj, M[sl][j]);
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int tt = 0; tt < KP; ++tt) {
+        const int t = KP - 1 - tt;
+        if (t < k) {
+          const int st = t / LG, ot = t % LG;
+          const T xt = __shfl_sync(FULL, (e[st] - acc[st]) * rd[st], ot, LG);
+          if (g == ot) x[st] = xt;
+#pragma unroll
+          for (int sl = 0; sl < NS; ++sl)
+            acc[sl] = fma((g + LG * sl < t) ? M[sl][t] : T(0), xt, acc[sl]);
+        }
+      }
+      if (active) {
+#pragma unroll
+        for (int sl = 0; sl < NS; ++sl) {
+          const int q = g + LG * sl;
+          if (q < k) X1new[(i0 + r) + (int64_t)q * m] = x[sl];
+        }
+      }
+    }
+  } else {
+    // A group of LG lanes factors one row's system in shared memory (lower triangle,
+    // right-looking Cholesky: at step t the lanes scale column t, then each lane updates
+    // its own columns j > t down from the diagonal), then runs the two triangular solves
+    // on E(i,:) in place.
+    using Lay = RowSolveLayout<T, KP>;
     constexpr int LG = Lay::LG;
     const int ld = Lay::ld(k), P = Lay::pitch(k), R = Lay::rows(k);
     const int grp = tid / LG, g = tid % LG;
     T* M = Ms + (size_t)grp * P;
-    bool bad = false;
     for (int base = 0; base < RP_BM; base += R) {
       const int r = base + grp;
       const bool in = grp < R && r < RP_BM;
@@ -1338,8 +1520,8 @@ row_pass(const T* __restrict__ A, int64_t lda, const T* __restrict__ W1, int64_t
         for (int a = g; a < k; a += LG) X1new[(i0 + r) + (int64_t)a * m] = e[a];
       __syncwarp();
     }
-    if (bad) atomicOr(err, ERRBIT_NOT_SPD);
   }
+  if (bad) atomicOr(err, ERRBIT_NOT_SPD);
   if (fin.ticket != nullptr) {
     // the last block to finish adds the block partials (in block order) into F_p
     __shared__ bool is_last;
@@ -1369,29 +1551,19 @@ row_pass(const T* __restrict__ A, int64_t lda, const T* __restrict__ W1, int64_t
   }
 }
 
-// F_p = w-term + ||A2||^2 - ||B||^2 - sum_{c<s} theta_c, stored in Fhist[*iter], then
-// (*iter)++.  One thread block.
+// Host-side: the row_pass instantiation for k (see row_kp).
 template <typename T>
-__global__ void finalize_objective(const double* __restrict__ wpart, int nw,
-                                   const double* __restrict__ bpart, int nb,
-                                   const double* __restrict__ normA2, const T* __restrict__ theta,
-                                   int s, double* __restrict__ Fhist, int hist_cap,
-                                   int* __restrict__ iter, double* __restrict__ Fcur) {
-  __shared__ double sh[32];
-  double w = 0.0, bn = 0.0;
-  for (int e = threadIdx.x; e < nw; e += blockDim.x) w += wpart[e];
-  for (int e = threadIdx.x; e < nb; e += blockDim.x) bn += bpart[e];
-  w = block_sum_double(w, sh);
-  __syncthreads();
-  bn = block_sum_double(bn, sh);
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int c = 0; c < s; ++c) t += (double)theta[c];
-    const double F = w + (*normA2 - bn - t);
-    const int p = *iter;
-    if (p < hist_cap) Fhist[p] = F;
-    *Fcur = F;
-    *iter = p + 1;
+using RowPassFn = void (*)(const T*, int64_t, const T*, int64_t, const T*, const T*, const T*,
+                           const T*, int, int, int, int, int, T*, double*, int*, FinalizeArgs<T>);
+template <typename T>
+RowPassFn<T> row_pass_fn(int k) {
+  switch (row_kp(k)) {
+    case 8: return row_pass<T, 8>;
+    case 16: return row_pass<T, 16>;
+    case 20: return row_pass<T, 20>;
+    case 24: return row_pass<T, 24>;
+    case 32: return row_pass<T, 32>;
+    default: return row_pass<T, 64>;
   }
 }
 

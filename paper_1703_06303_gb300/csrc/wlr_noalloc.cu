@@ -52,10 +52,13 @@ void* setup_device(int dev, const char** why) {
     return nullptr;
   }
   const int limit = 200 * 1024;  // above the largest row-pass need (k = 64, r - k = 32)
-  if (cudaFuncSetAttribute((const void*)wlr::row_pass<float, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit) != cudaSuccess ||
-      cudaFuncSetAttribute((const void*)wlr::row_pass<float, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit) != cudaSuccess ||
-      cudaFuncSetAttribute((const void*)wlr::row_pass<float, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit) != cudaSuccess ||
-      cudaFuncSetAttribute((const void*)wlr::row_pass<float, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit) != cudaSuccess) {
+  const void* fns[] = {(const void*)wlr::row_pass_fn<float>(8), (const void*)wlr::row_pass_fn<float>(16),
+                       (const void*)wlr::row_pass_fn<float>(20), (const void*)wlr::row_pass_fn<float>(24),
+                       (const void*)wlr::row_pass_fn<float>(32), (const void*)wlr::row_pass_fn<float>(64)};
+  bool ok = true;
+  for (const void* f : fns)
+    ok = ok && cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, limit) == cudaSuccess;
+  if (!ok) {
     *why = "cudaFuncSetAttribute failed";
     return nullptr;
   }
@@ -127,14 +130,8 @@ extern "C" wlr_status wlr_x1_update_noalloc(const float* A, int64_t lda, const f
   wlr::prep_rowpass<float><<<ki, 128, 0, st>>>(C, Vs, ki, n2, s, G, CV);
   const size_t smem = wlr::RowPassSmem<float>::bytes(NP, ki, s);
   const wlr::FinalizeArgs<float> nofin{nullptr, 0, nullptr, nullptr, nullptr, 0, nullptr, nullptr, nullptr};
-  if (ki <= 8)
-    wlr::row_pass<float, 8><<<nblk, 256, smem, st>>>(A, lda, W1, ldw, X1, Z2, G, CV, mi, n2, ki, s, NP, X1_next, wpart, err, nofin);
-  else if (ki <= 16)
-    wlr::row_pass<float, 16><<<nblk, 256, smem, st>>>(A, lda, W1, ldw, X1, Z2, G, CV, mi, n2, ki, s, NP, X1_next, wpart, err, nofin);
-  else if (ki <= 32)
-    wlr::row_pass<float, 32><<<nblk, 256, smem, st>>>(A, lda, W1, ldw, X1, Z2, G, CV, mi, n2, ki, s, NP, X1_next, wpart, err, nofin);
-  else
-    wlr::row_pass<float, 64><<<nblk, 256, smem, st>>>(A, lda, W1, ldw, X1, Z2, G, CV, mi, n2, ki, s, NP, X1_next, wpart, err, nofin);
+  wlr::row_pass_fn<float>(ki)<<<nblk, 256, smem, st>>>(A, lda, W1, ldw, X1, Z2, G, CV, mi, n2, ki, s, NP,
+                                                      X1_next, wpart, err, nofin);
   if (wterm) wlr::reduce_partials<double><<<1, 32, 0, st>>>(wpart, 1, nblk, 1, wterm, nullptr);
   if (status) store_err<<<1, 1, 0, st>>>(err, status);
   if (cudaGetLastError() != cudaSuccess) return fail(WLR_ERR_CUDA, "kernel launch failed");

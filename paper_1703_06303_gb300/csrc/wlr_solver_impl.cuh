@@ -97,10 +97,7 @@ class Solver final : public SolverBase {
     WLR_CUDA(cudaMemsetAsync(fin_ticket_, 0, sizeof(unsigned int), stream_));
     WLR_CUDA(cudaMemsetAsync(G_, 0, sizeof(T) * k * k, stream_));
     // dynamic shared memory limits
-    set_smem((const void*)row_pass<T, 8>, RowPassSmem<T>::bytes(NP, k, s));
-    set_smem((const void*)row_pass<T, 16>, RowPassSmem<T>::bytes(NP, k, s));
-    set_smem((const void*)row_pass<T, 32>, RowPassSmem<T>::bytes(NP, k, s));
-    set_smem((const void*)row_pass<T, 64>, RowPassSmem<T>::bytes(NP, k, s));
+    set_smem((const void*)row_pass_fn<T>(k), RowPassSmem<T>::bytes(NP, k, s));
     set_smem((const void*)x2_pass<T>, x2_smem());
     set_smem((const void*)coef_kernel3<T>, sizeof(T) * (2 * k * k + 16 * 64));
     set_smem((const void*)chol1_kernel<T>, sizeof(double) * (2 * k * k + k));
@@ -804,14 +801,8 @@ class Solver final : public SolverBase {
       Prof pf(this, "row_pass");
       FinalizeArgs<T> fin{bpart_, n2 > 0 ? nblk_coef_ : 0, normA2_, theta_, Fhist_, hist_cap_, iter_, Fcur_,
                           fin_ticket_};
-      if (k <= 8)
-        row_pass<T, 8><<<g, 256, smem, stream_>>>(A_, lda_, W1_, ldw_, X1buf_[xi], Z2_, G_, CV_, m, n2, k, s, NP, X1buf_[xo], wpart_, err_, fin);
-      else if (k <= 16)
-        row_pass<T, 16><<<g, 256, smem, stream_>>>(A_, lda_, W1_, ldw_, X1buf_[xi], Z2_, G_, CV_, m, n2, k, s, NP, X1buf_[xo], wpart_, err_, fin);
-      else if (k <= 32)
-        row_pass<T, 32><<<g, 256, smem, stream_>>>(A_, lda_, W1_, ldw_, X1buf_[xi], Z2_, G_, CV_, m, n2, k, s, NP, X1buf_[xo], wpart_, err_, fin);
-      else
-        row_pass<T, 64><<<g, 256, smem, stream_>>>(A_, lda_, W1_, ldw_, X1buf_[xi], Z2_, G_, CV_, m, n2, k, s, NP, X1buf_[xo], wpart_, err_, fin);
+      row_pass_fn<T>(k)<<<g, 256, smem, stream_>>>(A_, lda_, W1_, ldw_, X1buf_[xi], Z2_, G_, CV_, m, n2, k, s, NP,
+                                                  X1buf_[xo], wpart_, err_, fin);
     }
     count(1);
     // keep the factors of X1_p for Error_p
