@@ -86,6 +86,33 @@ struct WideAcc<double> {
   __device__ __forceinline__ double value() const { return v; }
 };
 
+// Block-wide sum of WideAcc partials, valid in thread 0.  Float pairs are combined with
+// TwoSum inside each warp; only the per-warp results are added in FP64 (FP64 arithmetic
+// runs at a small fraction of the FP32 rate, so it stays off the per-element path).
+__device__ __forceinline__ double block_sum_wide(const WideAcc<float>& a, double* sh) {
+  float hi = a.hi, lo = a.lo;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+    const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+    float s, e;
+    two_sum(hi, h2, s, e);
+    hi = s;
+    lo = (lo + l2) + e;
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[wid] = (double)hi + (double)lo;
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) r += sh[w];
+  return r;
+}
+__device__ __forceinline__ double block_sum_wide(const WideAcc<double>& a, double* sh) {
+  return block_sum_double(a.v, sh);
+}
+
 // Split-m Gram product with hierarchical accumulation:
 //   part[off + c*stride + a + b*P] = sum_{i in rows of chunk c} X[i, a] * Y[i, b]
 // for a < P, b < Q, where column b of Y is Y1[:, b] for b < q1 and Y2[:, b - q1] after
@@ -223,6 +250,35 @@ __global__ void reduce_partials(const T* __restrict__ part, int64_t stride, int 
     for (int c = 0; c < nchunks; ++c) s += (double)part[(int64_t)c * stride + e];
     if (out64) out64[e] = s;
     if (outT) outT[e] = (T)s;
+  }
+}
+
+// out[e] = sum_c part[c*stride + e], e < len, c < nchunks: block = 32 outputs, warp w adds
+// the chunks c = w, w + 8, ... in order, then the 8 warp sums are added in warp order
+// (deterministic, and each thread has only about nchunks / 8 loads in flight).  With Fout,
+// also Fout[e] = out[e] - [e is a diagonal entry] for the leading kf x kf block (the
+// shifted copy S2 - I that the second Cholesky factor reads, formed here in FP64).
+template <typename T, typename TF = T>
+__global__ void __launch_bounds__(256)
+reduce_partials_split(const T* __restrict__ part, int64_t stride, int nchunks, int64_t len,
+                      double* __restrict__ out64, T* __restrict__ outT, int kf = 0,
+                      TF* __restrict__ Fout = nullptr) {
+  __shared__ double sh[8][33];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t e = (int64_t)blockIdx.x * 32 + lane;
+  double s = 0.0;
+  if (e < len)
+#pragma unroll 4
+    for (int c = w; c < nchunks; c += 8) s += (double)part[(int64_t)c * stride + e];
+  sh[w][lane] = s;
+  __syncthreads();
+  if (w == 0 && e < len) {
+    double t = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) t += sh[q][lane];
+    if (out64) out64[e] = t;
+    if (outT) outT[e] = (T)t;
+    if (Fout && e < (int64_t)kf * kf) Fout[e] = (TF)(t - (e % (kf + 1) == 0 ? 1.0 : 0.0));
   }
 }
 
@@ -421,6 +477,100 @@ chol2_kernel(const double* __restrict__ part, int nch, int64_t pstride, int k,
     Rinv[e] = v;
     Nout[e] = Nm[e];
   }
+}
+
+// The same second factor for k <= 32 with one warp; F = S2 - I arrives as T (k x k,
+// column-major, formed where S2 is summed).  Right-looking Cholesky of I + F in difference
+// form: at step t the pivot F_tt (after the updates of steps < t) gives
+// Lambda_tt = F_tt / (1 + sqrt(1 + F_tt)), the rows below take Lambda_it = F_it / (1 +
+// Lambda_tt), and every row i > t updates F(i,j) -= Lambda_it Lambda_jt for j > t with
+// Lambda_jt broadcast from lane j.  Lane i keeps its row of F in registers shifted left by
+// one entry per step (so the pivot column is always entry 0 and every register index is a
+// compile-time constant while the step loop stays rolled: a single warp runs this once, so
+// compact code matters more than unrolling).  Then (I + Lambda) N = -Lambda by forward
+// substitution over the rows, and Rinv = R1inv (I + N)^T.
+template <typename T>
+__global__ void __launch_bounds__(32)
+chol2_warp(const T* __restrict__ Fin, int k, const T* __restrict__ R1inv,
+           T* __restrict__ Nout, T* __restrict__ Rinv, int* __restrict__ err) {
+  constexpr int KP = 32;
+  constexpr unsigned FULL = 0xffffffffu;
+  __shared__ T Ls[KP][KP + 1];   // Lambda, lower with the diagonal, row-major
+  __shared__ T Ns[KP][KP + 1];   // N, lower, row-major
+  __shared__ T rdg_s[KP];        // 1 / (1 + Lambda_tt)
+  const int i = threadIdx.x;
+  const bool live = i < k;
+  T M[KP];
+#pragma unroll
+  for (int j = 0; j < KP; ++j) {
+    const int hi = i > j ? i : j, lo = i > j ? j : i;
+    M[j] = (live && j < k) ? Fin[hi + lo * k] : T(0);
+  }
+  bool flag = false;
+#pragma unroll 1
+  for (int t = 0; t < k; ++t) {
+    const T ftt = __shfl_sync(FULL, M[0], t);
+    T lam = T(0);
+    if (!(T(1) + ftt > T(0)) || !wfinite(ftt)) flag = true;
+    else lam = ftt / (T(1) + wsqrt(T(1) + ftt));
+    const T rden = T(1) / (T(1) + lam);
+    const T lit = i > t ? M[0] * rden : T(0);
+    if (i == t) {
+      Ls[t][t] = lam;
+      rdg_s[t] = rden;
+    }
+    if (i > t) Ls[i][t] = lit;
+#pragma unroll
+    for (int j = 1; j < KP; ++j) {
+      // lane (t + j) mod 32: rows past the end and rows <= t broadcast 0
+      const T ljt = __shfl_sync(FULL, lit, (t + j) & (KP - 1));
+      M[j - 1] = fma(-lit, ljt, M[j]);
+    }
+    M[KP - 1] = T(0);
+  }
+  __syncwarp();
+  // rows of N: rhs = -Lambda (lower, with the diagonal); row l is final at step l and its
+  // entries beyond l are zero, so broadcasting the whole row needs no mask
+  T Nr[KP];
+#pragma unroll
+  for (int c = 0; c < KP; ++c) Nr[c] = (live && c <= i) ? -Ls[i][c] : T(0);
+#pragma unroll 1
+  for (int l = 0; l < k; ++l) {
+    const T f = i > l && live ? Ls[i][l] * rdg_s[l] : T(0);
+#pragma unroll
+    for (int c = 0; c < KP; ++c) {
+      const T v = __shfl_sync(FULL, Nr[c], l);
+      Nr[c] = fma(-f, v, Nr[c]);
+    }
+  }
+  const T rdg = live ? rdg_s[i] : T(1);
+#pragma unroll
+  for (int c = 0; c < KP; ++c) {
+    Nr[c] *= rdg;
+    Ns[i][c] = Nr[c];
+  }
+  __syncwarp();
+  // Rinv(a, b) = R1inv(a, b) + sum_l R1inv(a, l) N(b, l), lane a = row a (R1inv upper and
+  // N lower make the sum run over a <= l <= b by itself)
+  T V[KP];
+#pragma unroll
+  for (int b = 0; b < KP; ++b) V[b] = (live && b < k && b >= i) ? R1inv[i + b * k] : T(0);
+#pragma unroll
+  for (int b = 0; b < KP; ++b) Ls[i][b] = V[b];   // Lambda is no longer needed
+  __syncwarp();
+#pragma unroll 1
+  for (int l = 0; l < k; ++l) {
+    const T ral = Ls[i][l];
+#pragma unroll
+    for (int b = 0; b < KP; ++b) V[b] = fma(ral, Ns[b][l], V[b]);
+  }
+#pragma unroll
+  for (int b = 0; b < KP; ++b)
+    if (live && b < k) {
+      Rinv[i + b * k] = i <= b ? V[b] : T(0);
+      Nout[i + b * k] = Nr[b];
+    }
+  if (flag && i == 0) atomicOr(err, ERRBIT_RANK_DEFICIENT);
 }
 
 // Q1 = X1 R1^{-1} (m x k); R1^{-1} upper triangular.
@@ -1303,17 +1453,19 @@ row_pass(const T* __restrict__ A, int64_t lda, const T* __restrict__ W1, int64_t
     return i0 + r < m ? W1[(i0 + r) + (int64_t)a * ldw] : T(1);
   };
 
-  for (int e = tid; e < k * k; e += 256) Gs[e] = Gm[e];
-  for (int e = tid; e < k * s; e += 256) CVs[e] = CV[e];
+  // G, C V_s and (float) the block's rows of X1old, A1 and W1, copied asynchronously in
+  // the first phase-1 copy group (rows outside the matrix read as zero; phases 2 and 3
+  // never use them).
+  for (int e = tid; e < k * k; e += 256) cp_async_elem(Gs + e, Gm + e, true);
+  for (int e = tid; e < k * s; e += 256) cp_async_elem(CVs + e, CV + e, true);
   if (kStage) {
-    // the block's rows of X1old, A1 and W1 (coalesced down each column)
     for (int e = tid; e < RP_BM * k; e += 256) {
       const int r = e % RP_BM, a = e / RP_BM;
       const int i = i0 + r;
       const bool ok = i < m;
-      Xo[r * kp + a] = ok ? X1old[i + (int64_t)a * m] : T(0);
-      A1s[r * kp + a] = ok ? A[i + (int64_t)a * lda] : T(0);
-      W1s[r * kp + a] = ok ? W1[i + (int64_t)a * ldw] : T(1);
+      cp_async_elem(Xo + r * kp + a, ok ? X1old + i + (int64_t)a * m : X1old, ok);
+      cp_async_elem(A1s + r * kp + a, ok ? A + i + (int64_t)a * lda : A, ok);
+      cp_async_elem(W1s + r * kp + a, ok ? W1 + i + (int64_t)a * ldw : W1, ok);
     }
   }
 
@@ -1342,7 +1494,7 @@ row_pass(const T* __restrict__ A, int64_t lda, const T* __restrict__ W1, int64_t
   __syncthreads();
 
   // ---- phase 2b: E (into Ys[:, :k]) and the weighted objective term
-  double wsum = 0.0;
+  WideAcc<T> wacc;
   for (int e = tid; e < RP_BM * k; e += 256) {
     const int r = e % RP_BM, a = e / RP_BM;
     if (i0 + r >= m) continue;
@@ -1352,10 +1504,10 @@ row_pass(const T* __restrict__ A, int64_t lda, const T* __restrict__ W1, int64_t
     T v = a1 * w * w + Ys[r * (NP + 1) + a];
     for (int c = 0; c < s; ++c) v -= Us[r * (EIG_BMAX + 1) + c] * CVs[a + c * k];
     Ys[r * (NP + 1) + a] = v;
-    const double d = ((double)a1 - (double)xo) * (double)w;
-    wsum += d * d;
+    const T d = (a1 - xo) * w;
+    wacc.add(d * d);
   }
-  wsum = block_sum_double(wsum, sh);
+  const double wsum = block_sum_wide(wacc, sh);
   if (tid == 0) wpart[blockIdx.x] = wsum;
   __syncthreads();
 

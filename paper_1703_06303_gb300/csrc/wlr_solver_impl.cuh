@@ -41,6 +41,7 @@ class Solver final : public SolverBase {
     part64_ = dalloc<double>(std::max<size_t>(part_elems, 1));
     part_elems_ = std::max<size_t>(part_elems, 1);
     S2T_ = dalloc<double>(L);
+    F2_ = dalloc<T>((size_t)k * k);
     R1inv_ = dalloc<T>((size_t)k * k);
     Nm_ = dalloc<T>((size_t)k * k);
     Rinv_ = dalloc<T>((size_t)k * k);
@@ -638,10 +639,11 @@ class Solver final : public SolverBase {
 #undef WLR_GRAM
     count(1);
   }
-  void reduce64(int64_t stride, int nch, int64_t len, double* out64) {
+  void reduce64(int64_t stride, int nch, int64_t len, double* out64, int kf = 0, T* Fout = nullptr) {
     if (len <= 0) return;
     Prof pf(this, "reduce_partials");
-    reduce_partials<double><<<grid1d(len), 256, 0, stream_>>>(part64_, stride, nch, len, out64, nullptr);
+    reduce_partials_split<double, T><<<(unsigned)cdiv(len, 32), 256, 0, stream_>>>(part64_, stride, nch, len, out64,
+                                                                                    nullptr, kf, Fout);
     count(1);
   }
 
@@ -702,10 +704,13 @@ class Solver final : public SolverBase {
       gram(Q1_, m, Q1_, m, k, A2, lda_, k, k + n2, L, ch_T_);
     }
     // Q1^T [Q1 A2] summed over the chunks by all SMs; chol2 and coef read the sum
-    reduce64(L, nchT, L, S2T_);
+    reduce64(L, nchT, L, S2T_, k, k <= 32 ? F2_ : nullptr);
     {
       Prof pf(this, "chol2");
-      chol2_kernel<T><<<1, 256, 3 * sizeof(T) * k * k, stream_>>>(S2T_, 1, L, k, Rpre, Nm_, Rinv_, err_);
+      if (k <= 32)
+        chol2_warp<T><<<1, 32, 0, stream_>>>(F2_, k, Rpre, Nm_, Rinv_, err_);
+      else
+        chol2_kernel<T><<<1, 256, 3 * sizeof(T) * k * k, stream_>>>(S2T_, 1, L, k, Rpre, Nm_, Rinv_, err_);
     }
     count(1);
     if (n2 > 0) {
@@ -890,6 +895,7 @@ class Solver final : public SolverBase {
   T* X1buf_[3] = {nullptr, nullptr, nullptr};
   T *Q1_ = nullptr, *R1inv_ = nullptr, *Nm_ = nullptr, *Rinv_ = nullptr;
   double *part64_ = nullptr, *S2T_ = nullptr;
+  T* F2_ = nullptr;   // S2 - I for the second Cholesky factor (k <= 32)
   T *C_ = nullptr, *Z2_ = nullptr, *Z2prev_ = nullptr;
   double *B64_ = nullptr, *bpart_ = nullptr, *K64_ = nullptr, *prep_part_ = nullptr;
   float *Bh_ = nullptr, *Bl_ = nullptr;
