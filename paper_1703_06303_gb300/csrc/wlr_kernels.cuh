@@ -779,7 +779,7 @@ form_g2_df(const double* __restrict__ K64, const double* __restrict__ B64,
 template <typename T, bool VSMEM>
 __global__ void __launch_bounds__(256)
 eig_mult(const T* __restrict__ G2, const T* __restrict__ V, int n2, int b, T* __restrict__ Z,
-         T* __restrict__ part, unsigned int* __restrict__ ticket, double* __restrict__ HP) {
+         T* __restrict__ part, unsigned int* __restrict__ ticket, T* __restrict__ HP) {
   constexpr int RB = 8;   // one row of Z per warp
   extern __shared__ unsigned char smem_raw[];
   T* Vt = reinterpret_cast<T*>(smem_raw);  // [b][n2] when VSMEM
@@ -853,12 +853,12 @@ eig_mult(const T* __restrict__ G2, const T* __restrict__ V, int n2, int b, T* __
       v3 += __ldcg(&part[(int64_t)(c + 3) * 2 * b * b + e]);
     }
     for (; c < nb; ++c) v0 += __ldcg(&part[(int64_t)c * 2 * b * b + e]);
-    HP[e] = (double)((v0 + v1) + (v2 + v3));
+    HP[e] = (v0 + v1) + (v2 + v3);
   }
   if (threadIdx.x == 0) *ticket = 0u;
 }
 
-// Subspace iteration, small step (one block of 128 threads, b <= 32):
+// Subspace iteration, small step (one warp, b <= 32):
 //  1. H = V^T G2 V and P = Z^T Z (b x b, summed by the last eig_mult block).
 //  2. Rayleigh-Ritz: H = Y Theta Y^T by the parallel cyclic Jacobi method (round-robin
 //     ordering, b/2 disjoint rotations per round), sorted descending.
@@ -869,213 +869,267 @@ eig_mult(const T* __restrict__ G2, const T* __restrict__ V, int n2, int b, T* __
 //     Mz = Y F_z L^{-T}, so that V_next = V Mv + Z Mz has orthonormal columns.
 // Outputs (T, b x b col-major): Y, Mv, Mz; theta (b, descending); resid (b): estimate of
 // ||G2 v_c - theta_c v_c||^2 = (Y^T P Y)_cc - theta_c^2.
+// One warp, no block barriers: a Jacobi round is three warp-synchronous phases (angles by
+// lanes < b/2; row rotations with lane l taking column l; column rotations of H and Y
+// with lane r taking row r).  The Cholesky factor of W^T W and L^{-1} use register rows
+// (lane = row) with per-step broadcasts by shuffle; loops over steps stay rolled, since a
+// single warp runs this code once and compact code matters more than unrolling.
 template <typename T>
-__global__ void __launch_bounds__(128)
-eig_small(const double* __restrict__ HP, int b, int max_sweeps, T* __restrict__ Yout,
+__global__ void __launch_bounds__(32)
+eig_small(const T* __restrict__ HP, int b, int max_sweeps, T* __restrict__ Yout,
           T* __restrict__ Mv, T* __restrict__ Mz, T* __restrict__ theta,
           T* __restrict__ resid, int* __restrict__ err) {
   constexpr int BM = EIG_BMAX;
-  __shared__ T H[BM][BM + 1];
-  __shared__ T P[BM][BM + 1];
-  __shared__ T Y[BM][BM + 1];
-  __shared__ T Wg[BM][BM + 1];
+  constexpr unsigned FULL = 0xffffffffu;
+  __shared__ T Hs[BM][BM + 1];   // H; later P Y; later L (lower)
+  __shared__ T Ps[BM][BM + 1];   // P; later Y^T P Y
+  __shared__ T Ys[BM][BM + 1];   // eigenvectors; later L^{-1} (lower)
+  __shared__ T Ws[BM][BM + 1];   // sorted eigenvectors
   __shared__ T cs[BM / 2][2];
-  __shared__ int pairs[BM / 2][2];
+  __shared__ int pq[BM / 2][2];
   __shared__ int perm[BM];
-  __shared__ T th[BM];
-  __shared__ T fz[BM];
-  __shared__ int usev[BM];
-  const int lane = threadIdx.x, NT = blockDim.x;
-  __shared__ T red[2][4];
+  __shared__ int usev_s[BM];
+  __shared__ T fz_s[BM];
+  const int lane = threadIdx.x;
   const int bb = b * b;
-  for (int e = lane; e < bb; e += NT) {
-    const int r = e % b, q = e / b;
-    H[r][q] = (T)HP[e];
-    P[r][q] = (T)HP[bb + e];
-    Y[r][q] = r == q ? T(1) : T(0);
+  for (int e = lane; e < BM * BM; e += 32) {
+    const int r = e / BM, q = e % BM;
+    Hs[r][q] = T(0);
+    Ps[r][q] = T(0);
+    Ys[r][q] = r == q ? T(1) : T(0);
+    Ws[r][q] = T(0);
   }
-  __syncthreads();
-  for (int e = lane; e < bb; e += NT) {
+  __syncwarp();
+  for (int e = lane; e < bb; e += 32) {
     const int r = e % b, q = e / b;
-    if (r < q) {
-      const T v = T(0.5) * (H[r][q] + H[q][r]);
-      H[r][q] = v;
-      H[q][r] = v;
-    }
+    Hs[r][q] = T(0.5) * (HP[e] + HP[q + r * b]);
+    Ps[r][q] = HP[bb + e];
   }
-  __syncthreads();
+  __syncwarp();
+
   // ---- parallel Jacobi; stop once ||offdiag|| <= 4 b u ||H||
-  const int N = (b + 1) & ~1;
+  const int N = (b + 1) & ~1, half = N / 2;
   const T eps = T(4 * b) * (sizeof(T) == 4 ? T(5.96e-8) : T(1.11e-16));
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     T off = T(0), tot = T(0);
-    for (int e = lane; e < bb; e += NT) {
+    for (int e = lane; e < bb; e += 32) {
       const int r = e % b, q = e / b;
-      const T v = H[r][q];
+      const T v = Hs[r][q];
       tot += v * v;
       if (r != q) off += v * v;
     }
     off = warp_sum(off);
     tot = warp_sum(tot);
-    if ((lane & 31) == 0) {
-      red[0][lane >> 5] = off;
-      red[1][lane >> 5] = tot;
-    }
-    __syncthreads();
-    off = T(0);
-    tot = T(0);
-    for (int q = 0; q < (NT >> 5); ++q) {
-      off += red[0][q];
-      tot += red[1][q];
-    }
-    __syncthreads();
     if (off <= eps * eps * tot) break;
     for (int round = 0; round < N - 1; ++round) {
-      if (lane < N / 2) {
-        const int i = lane;
-        int p = (i == 0) ? N - 1 : (round + i) % (N - 1);
-        int q = (round + N - 1 - i) % (N - 1);
+      if (lane < half) {
+        int p = lane == 0 ? N - 1 : round + lane;
+        if (p >= N - 1 && lane != 0) p -= N - 1;
+        int q = round + N - 1 - lane;
+        if (q >= N - 1) q -= N - 1;
         if (p > q) { const int t = p; p = q; q = t; }
-        pairs[i][0] = p;
-        pairs[i][1] = q;
         T c = T(1), sn = T(0);
         if (q < b) {
-          const T apq = H[p][q];
+          const T apq = Hs[p][q];
           if (apq != T(0)) {
-            const T tau = (H[q][q] - H[p][p]) / (T(2) * apq);
+            const T tau = (Hs[q][q] - Hs[p][p]) / (T(2) * apq);
             const T t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + wsqrt(T(1) + tau * tau));
             c = T(1) / wsqrt(T(1) + t * t);
             sn = t * c;
           }
         }
-        cs[i][0] = c;
-        cs[i][1] = sn;
+        pq[lane][0] = p;
+        pq[lane][1] = q;
+        cs[lane][0] = c;
+        cs[lane][1] = sn;
       }
-      __syncthreads();
-      for (int e = lane; e < (N / 2) * b; e += NT) {   // rows: H <- J^T H
-        const int i = e % (N / 2), l = e / (N / 2);
-        const int p = pairs[i][0], q = pairs[i][1];
-        if (q < b) {
-          const T c = cs[i][0], sn = cs[i][1];
-          const T hp = H[p][l], hq = H[q][l];
-          H[p][l] = c * hp - sn * hq;
-          H[q][l] = sn * hp + c * hq;
+      __syncwarp();
+      // H <- J^T H: lane l rotates rows p, q of column l for every pair
+      if (lane < b) {
+        for (int i0 = 0; i0 < half; i0 += 4) {
+          T hp[4], hq[4], cc[4], ss[4];
+          int pp[4], qq[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int i = i0 + u < half ? i0 + u : half - 1;
+            pp[u] = pq[i][0];
+            qq[u] = pq[i][1];
+            cc[u] = cs[i][0];
+            ss[u] = cs[i][1];
+            const bool ok = i0 + u < half && qq[u] < b;
+            hp[u] = ok ? Hs[pp[u]][lane] : T(0);
+            hq[u] = ok ? Hs[qq[u]][lane] : T(0);
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            if (i0 + u < half && qq[u] < b) {
+              Hs[pp[u]][lane] = cc[u] * hp[u] - ss[u] * hq[u];
+              Hs[qq[u]][lane] = ss[u] * hp[u] + cc[u] * hq[u];
+            }
+          }
         }
       }
-      __syncthreads();
-      for (int e = lane; e < (N / 2) * b; e += NT) {   // columns: H <- H J, Y <- Y J
-        const int i = e % (N / 2), l = e / (N / 2);
-        const int p = pairs[i][0], q = pairs[i][1];
-        if (q < b) {
-          const T c = cs[i][0], sn = cs[i][1];
-          const T hp = H[l][p], hq = H[l][q];
-          H[l][p] = c * hp - sn * hq;
-          H[l][q] = sn * hp + c * hq;
-          const T yp = Y[l][p], yq = Y[l][q];
-          Y[l][p] = c * yp - sn * yq;
-          Y[l][q] = sn * yp + c * yq;
+      __syncwarp();
+      // H <- H J, Y <- Y J: lane r rotates columns p, q of row r for every pair
+      if (lane < b) {
+        for (int i0 = 0; i0 < half; i0 += 4) {
+          T hp[4], hq[4], yp[4], yq[4], cc[4], ss[4];
+          int pp[4], qq[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int i = i0 + u < half ? i0 + u : half - 1;
+            pp[u] = pq[i][0];
+            qq[u] = pq[i][1];
+            cc[u] = cs[i][0];
+            ss[u] = cs[i][1];
+            const bool ok = i0 + u < half && qq[u] < b;
+            hp[u] = ok ? Hs[lane][pp[u]] : T(0);
+            hq[u] = ok ? Hs[lane][qq[u]] : T(0);
+            yp[u] = ok ? Ys[lane][pp[u]] : T(0);
+            yq[u] = ok ? Ys[lane][qq[u]] : T(0);
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            if (i0 + u < half && qq[u] < b) {
+              Hs[lane][pp[u]] = cc[u] * hp[u] - ss[u] * hq[u];
+              Hs[lane][qq[u]] = ss[u] * hp[u] + cc[u] * hq[u];
+              Ys[lane][pp[u]] = cc[u] * yp[u] - ss[u] * yq[u];
+              Ys[lane][qq[u]] = ss[u] * yp[u] + cc[u] * yq[u];
+            }
+          }
         }
       }
-      __syncthreads();
+      __syncwarp();
     }
   }
   // ---- sort descending: lane c's rank = #{d : theta_d > theta_c, or equal with d < c}
   if (lane < b) {
-    const T tc = H[lane][lane];
+    const T tc = Hs[lane][lane];
     int rank = 0;
     for (int d = 0; d < b; ++d) {
-      const T td = H[d][d];
+      const T td = Hs[d][d];
       rank += (td > tc) || (td == tc && d < lane);
     }
     perm[rank] = lane;
     if (!wfinite(tc)) atomicOr(err, ERRBIT_EIG);
   }
-  __syncthreads();
-  if (lane < b) th[lane] = H[perm[lane]][perm[lane]];
-  for (int e = lane; e < bb; e += NT) {
-    const int r = e % b, c = e / b;
-    Wg[r][c] = Y[r][perm[c]];
+  __syncwarp();
+  const T thl = lane < b ? Hs[perm[lane]][perm[lane]] : T(0);   // sorted Ritz value
+  if (lane < b)
+    for (int c = 0; c < b; ++c) Ws[lane][c] = Ys[lane][perm[c]];
+  // P Y into Hs (lane r: row r of P in registers)
+  T pr[BM];
+#pragma unroll
+  for (int l = 0; l < BM; ++l) pr[l] = Ps[lane][l];
+  __syncwarp();
+  for (int c = 0; c < b; ++c) {
+    T v0 = T(0), v1 = T(0);
+#pragma unroll
+    for (int l = 0; l < BM; l += 2) {
+      v0 = fma(pr[l], Ws[l][c], v0);
+      v1 = fma(pr[l + 1], Ws[l + 1][c], v1);
+    }
+    Hs[lane][c] = v0 + v1;
   }
-  __syncthreads();
-  for (int e = lane; e < bb; e += NT) {
-    const int r = e % b, c = e / b;
-    Y[r][c] = Wg[r][c];
+  // Y^T P Y into Ps (lane r: column r of Y in registers)
+#pragma unroll
+  for (int l = 0; l < BM; ++l) pr[l] = Ws[l][lane];
+  __syncwarp();
+  for (int c = 0; c < b; ++c) {
+    T v0 = T(0), v1 = T(0);
+#pragma unroll
+    for (int l = 0; l < BM; l += 2) {
+      v0 = fma(pr[l], Hs[l][c], v0);
+      v1 = fma(pr[l + 1], Hs[l + 1][c], v1);
+    }
+    Ps[lane][c] = v0 + v1;
   }
-  __syncthreads();
-  // H <- P Y, then Wg <- Y^T P Y
-  for (int e = lane; e < bb; e += NT) {
-    const int r = e % b, c = e / b;
-    T v = T(0);
-    for (int l = 0; l < b; ++l) v = fma(P[r][l], Y[l][c], v);
-    H[r][c] = v;
-  }
-  __syncthreads();
-  for (int e = lane; e < bb; e += NT) {
-    const int r = e % b, c = e / b;
-    T v = T(0);
-    for (int l = 0; l < b; ++l) v = fma(Y[l][r], H[l][c], v);
-    Wg[r][c] = v;
-  }
-  __syncthreads();
+  __syncwarp();
+  const T tmax = fabs(__shfl_sync(FULL, thl, 0));
+  const T small = sizeof(T) == 4 ? T(1e-6) : T(1e-13);
+  const T nz2 = lane < b ? Ps[lane][lane] : T(1);
+  const bool use_v = !(thl > small * tmax) || !(nz2 > T(0));
+  const T fzl = use_v ? T(0) : T(1) / wsqrt(nz2);
   if (lane < b) {
-    const int c = lane;
-    const T tmax = fabs(th[0]);
-    const T small = sizeof(T) == 4 ? T(1e-6) : T(1e-13);
-    const T nz2 = Wg[c][c];
-    const bool use_v = !(th[c] > small * tmax) || !(nz2 > T(0));
-    usev[c] = use_v ? 1 : 0;
-    fz[c] = use_v ? T(0) : T(1) / wsqrt(nz2);
-    resid[c] = nz2 - th[c] * th[c];
-    theta[c] = th[c];
+    resid[lane] = nz2 - thl * thl;
+    theta[lane] = thl;
   }
-  __syncthreads();
-  // Gram of W into P: <Vy_a, Vy_b> = delta_ab, <Zy_a, Zy_b> = Wg_ab, mixed pairs 0
-  for (int e = lane; e < bb; e += NT) {
-    const int r = e % b, c = e / b;
+  usev_s[lane] = (use_v || lane >= b) ? 1 : 0;
+  fz_s[lane] = lane < b ? fzl : T(0);
+  __syncwarp();
+  // Gram of W (lane i: row i): <Vy_a, Vy_b> = delta_ab, <Zy_a, Zy_b> = fz_a fz_b (Y^T P Y)_ab,
+  // mixed pairs 0; rows and columns past b are the identity
+  T G[BM];
+#pragma unroll
+  for (int j = 0; j < BM; ++j) {
+    const bool uj = usev_s[j] != 0;
     T g;
-    if (usev[r] && usev[c]) g = r == c ? T(1) : T(0);
-    else if (!usev[r] && !usev[c]) g = fz[r] * fz[c] * Wg[r][c];
-    else g = T(0);
-    P[r][c] = g;
+    if (use_v || lane >= b || j >= b) g = (uj && (use_v || lane >= b)) && j == lane ? T(1) : T(0);
+    else g = uj ? T(0) : fzl * fz_s[j] * Ps[lane][j];
+    G[j] = g;
   }
-  __syncthreads();
-  // Cholesky of the Gram (lower, in place)
+  // Cholesky W^T W = L L^T (lower L into Hs), rows shifted left by one entry per step
   bool bad = false;
   for (int t = 0; t < b; ++t) {
-    T d = P[t][t];
-    if (!(d > T(0)) || !wfinite(d)) { bad = true; d = T(1); }
+    T d = __shfl_sync(FULL, G[0], t);
+    if (!(d > T(0)) || !wfinite(d)) {
+      bad = true;
+      d = T(1);
+    }
     const T rl = wrsqrt(d);
-    const T lt = d * rl;
-    __syncthreads();
-    if (lane == 0) P[t][t] = lt;
-    for (int i = t + 1 + lane; i < b; i += NT) P[i][t] *= rl;
-    __syncthreads();
-    for (int i = t + 1 + lane; i < b; i += NT)
-      for (int j = t + 1; j <= i; ++j) P[i][j] -= P[i][t] * P[j][t];
-    __syncthreads();
+    const T lit = lane > t ? G[0] * rl : T(0);
+    if (lane == t) Hs[t][t] = d * rl;
+    if (lane > t) Hs[lane][t] = lit;
+#pragma unroll
+    for (int j = 1; j < BM; ++j) {
+      const T ljt = __shfl_sync(FULL, lit, (t + j) & (BM - 1));
+      G[j - 1] = fma(-lit, ljt, G[j]);
+    }
+    G[BM - 1] = T(0);
   }
   if (lane == 0 && bad) atomicOr(err, ERRBIT_EIG);
-  // L^{-T} into H (upper): column c solves L^T x = e_c (one lane per column)
-  if (lane < b) {
-    const int c = lane;
-    for (int a = b - 1; a >= 0; --a) {
-      T v = a == c ? T(1) : T(0);
-      for (int l = a + 1; l <= c; ++l) v -= P[l][a] * H[l][c];
-      H[a][c] = a <= c ? v * (T(1) / P[a][a]) : T(0);
+  __syncwarp();
+  // X = L^{-1} (lower, lane = row): row l is final at step l (up to the factor 1 / L_ll)
+  const T rdi = lane < b ? T(1) / Hs[lane][lane] : T(1);
+  T X[BM];
+#pragma unroll
+  for (int c = 0; c < BM; ++c) X[c] = c == lane ? T(1) : T(0);
+  for (int l = 0; l < b; ++l) {
+    const T rdl = __shfl_sync(FULL, rdi, l);
+    const T f = lane > l && lane < b ? Hs[lane][l] * rdl : T(0);
+#pragma unroll
+    for (int c = 0; c < BM; ++c) {
+      const T v = __shfl_sync(FULL, X[c], l);
+      X[c] = fma(-f, v, X[c]);
     }
   }
-  __syncthreads();
-  for (int e = lane; e < bb; e += NT) {
-    const int r = e % b, c = e / b;
-    T mv = T(0), mz = T(0);
-    for (int l = 0; l <= c; ++l) {
-      const T yl = Y[r][l] * H[l][c];
-      if (usev[l]) mv += yl;
-      else mz += yl * fz[l];
+#pragma unroll
+  for (int c = 0; c < BM; ++c) Ys[lane][c] = X[c] * rdi;
+  __syncwarp();
+  // Mv(r, c) = sum_l Y(r, l) [use_v(l)] X(c, l), Mz(r, c) = sum_l Y(r, l) fz(l) X(c, l)
+  if (lane < b) {
+    T ya[BM], yz[BM];
+#pragma unroll
+    for (int l = 0; l < BM; ++l) {
+      const T y = Ws[lane][l];
+      ya[l] = usev_s[l] ? y : T(0);
+      yz[l] = usev_s[l] ? T(0) : y * fz_s[l];
     }
-    Yout[e] = Y[r][c];
-    Mv[e] = mv;
-    Mz[e] = mz;
+    for (int c = 0; c < b; ++c) {
+      T mv0 = T(0), mv1 = T(0), mz0 = T(0), mz1 = T(0);
+#pragma unroll
+      for (int l = 0; l < BM; l += 2) {
+        const T x0 = Ys[c][l], x1 = Ys[c][l + 1];
+        mv0 = fma(ya[l], x0, mv0);
+        mv1 = fma(ya[l + 1], x1, mv1);
+        mz0 = fma(yz[l], x0, mz0);
+        mz1 = fma(yz[l + 1], x1, mz1);
+      }
+      const int e = lane + c * b;
+      Yout[e] = Ws[lane][c];
+      Mv[e] = mv0 + mv1;
+      Mz[e] = mz0 + mz1;
+    }
   }
 }
 

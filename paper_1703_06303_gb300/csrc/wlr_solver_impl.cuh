@@ -68,7 +68,7 @@ class Solver final : public SolverBase {
     Mv_ = dalloc<T>((size_t)bb * bb);
     Mz_ = dalloc<T>((size_t)bb * bb);
     theta_ = dalloc<T>(bb);
-    HP_ = dalloc<double>(2 * (size_t)bb * bb);
+    HP_ = dalloc<T>(2 * (size_t)bb * bb);
     eig_ticket_ = dalloc<unsigned int>(1);
     fin_ticket_ = dalloc<unsigned int>(1);
     resid_ = dalloc<T>(bb);
@@ -739,7 +739,7 @@ class Solver final : public SolverBase {
     }
     {
       Prof pf(this, "eig_small");
-      eig_small<T><<<1, 128, 0, stream_>>>(HP_, b, cold ? (sizeof(T) == 4 ? 12 : 24) : (sizeof(T) == 4 ? 1 : 6), Y_, Mv_, Mz_,
+      eig_small<T><<<1, 32, 0, stream_>>>(HP_, b, cold ? (sizeof(T) == 4 ? 12 : 24) : (sizeof(T) == 4 ? 1 : 6), Y_, Mv_, Mz_,
                                           theta_, resid_, err_);
     }
     Prof pf(this, "eig_update");
@@ -900,7 +900,7 @@ class Solver final : public SolverBase {
   double *B64_ = nullptr, *bpart_ = nullptr, *K64_ = nullptr, *prep_part_ = nullptr;
   float *Bh_ = nullptr, *Bl_ = nullptr;
   unsigned int *prep_ticket_ = nullptr, *eig_ticket_ = nullptr, *fin_ticket_ = nullptr;
-  double* HP_ = nullptr;
+  T* HP_ = nullptr;
   // tensor-core Gram (FP32 path)
   bool use_tc_ = false;
   int64_t ld4_ = 0;
