@@ -1,0 +1,604 @@
+// Step a3 of Algorithm 1 (Dutta & Li, arXiv 1703.06303): one step of the subspace
+// iteration for the top r - k eigenpairs of G2 = (P_perp A2)^T (P_perp A2) = K - B^T B
+// (Theorem 2 / Eckart-Young through the Gram matrix), the Ritz vectors V_s that define
+// D = U_s Sigma_s V_s^T, and the two small products of step a5 that depend on them
+// (G = C C^T and C V_s).
+//
+// Z = G2 V is formed without G2: kv_pair takes K V in double-float on all SMs (K = Kh + Kl
+// is stored as a float pair), and the cluster kernel subtracts B^T (B V) before rounding
+// to T (K and B^T B nearly cancel on the subspace).  The cluster kernel (NC = 16 CTAs where
+// the device allows it, else 8) splits the n2 basis rows; CTA r owns rows
+// [r R, r R + R), R = ceil(n2 / NC):
+//   1. partial B V over the CTA's rows, summed by every CTA through distributed shared
+//      memory; Z(rows) = K V - B^T (B V);
+//   2. partial H = V^T Z and P = Z^T Z, summed by CTA 0, which runs the Rayleigh-Ritz
+//      step (ritz_step) on the b x b problem;
+//   3. every CTA reads Y, Mv, Mz from CTA 0 and forms its rows of the next basis
+//      V Mv + Z Mz and of V_s = (V Y)(:, :s); then the partials of C C^T and C V_s are
+//      summed by CTA 0.
+// All waits are cluster barriers reached unconditionally by every CTA.
+#pragma once
+
+#include <cooperative_groups.h>
+
+#include "wlr_kernels.cuh"
+
+namespace wlr {
+
+namespace cgrp = cooperative_groups;
+
+constexpr int DS_THREADS = 256;
+constexpr int DS_BM = EIG_BMAX;   // largest b
+constexpr int DS_P = DS_BM + 1;   // row pitch of the b x b work arrays
+
+// Sum of products in double-float (float) or plain double: hi + lo.
+template <typename T>
+struct DfAcc;
+template <>
+struct DfAcc<float> {
+  float hi = 0.f, lo = 0.f;
+  // += (xh + xl) y, the product xh y kept exactly (TwoProduct by FMA)
+  __device__ __forceinline__ void add(float xh, float xl, float y) {
+    const float p = xh * y;
+    const float pe = fmaf(xh, y, -p);
+    const float x = fmaf(xl, y, pe);
+    float s, e;
+    two_sum(hi, p, s, e);
+    hi = s;
+    lo += e + x;
+  }
+  // -= (xh + xl)(yh + yl)
+  __device__ __forceinline__ void sub2(float xh, float xl, float yh, float yl) {
+    const float p = xh * yh;
+    const float pe = fmaf(xh, yh, -p);
+    const float x = fmaf(xh, yl, fmaf(xl, yh, pe));
+    float s, e;
+    two_sum(hi, -p, s, e);
+    hi = s;
+    lo += e - x;
+  }
+  __device__ __forceinline__ void add_pair(float h, float l) {
+    float s, e;
+    two_sum(hi, h, s, e);
+    hi = s;
+    lo = (lo + l) + e;
+  }
+  __device__ __forceinline__ void warp_reduce() {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+      const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+      add_pair(h2, l2);
+    }
+  }
+};
+template <>
+struct DfAcc<double> {
+  double hi = 0.0, lo = 0.0;
+  __device__ __forceinline__ void add(double xh, double, double y) { hi = fma(xh, y, hi); }
+  __device__ __forceinline__ void sub2(double xh, double, double yh, double) { hi = fma(-xh, yh, hi); }
+  __device__ __forceinline__ void add_pair(double h, double) { hi += h; }
+  __device__ __forceinline__ void warp_reduce() { hi = warp_sum(hi); }
+};
+
+template <typename T>
+struct DstepArgs {
+  const T* ZKh;  // K V (n2 x b) from kv_pair: high part (the whole product for double)
+  const T* ZKl;  // low part (nullptr: none)
+  const T* Bh;   // B = Q^T A2 (k x n2, column j at B + j*k): high part
+  const T* Bl;   // low part (nullptr: none)
+  T* Z2;         // n2 x NP row-major: C^T in columns < k (read); V_s into columns k..k+s-1
+  T* V;          // n2 x b basis: in, the current one; out, the next one
+  T* Vs;         // n2 x s Ritz vectors
+  T* theta;      // b Ritz values, descending
+  T* resid;      // b residual estimates (Y^T P Y)_cc - theta_c^2
+  T* G;          // k x k, C C^T
+  T* CV;         // k x s, C V_s
+  int* err;
+  int n2, k, b, s, NP;
+  int sweeps;    // Jacobi sweeps of the Rayleigh-Ritz step
+};
+
+// Element offsets of the dynamic shared memory (every CTA has the same layout; the b x b
+// work arrays are used by CTA 0 only).
+struct DsLayout {
+  size_t Vt, Bs, Cs, Zh, Zl, Zr, Vsr, BVp, BV, HPp, Gp, CVp, Ml, Wk, total;
+  __host__ __device__ DsLayout(int n2, int k, int b, int s, int R) {
+    const size_t ss = s > 0 ? s : 1;
+    size_t o = 0;
+    Vt = o;  o += (size_t)b * n2;           // basis, V(j, c) at Vt[c*n2 + j]
+    Bs = o;  o += 2 * (size_t)k * R;        // B(:, rows): high, low
+    Cs = o;  o += (size_t)R * k;            // C(:, rows), C(x, j) at Cs[(j - l0)*k + x]
+    Zh = o;  o += (size_t)R * b;            // (K V)(rows), high, Zh[c*R + rr]
+    Zl = o;  o += (size_t)R * b;            // low
+    Zr = o;  o += (size_t)R * b;            // Z(rows), Zr[rr*b + c]
+    Vsr = o; o += (size_t)R * ss;           // V_s(rows)
+    BVp = o; o += 2 * (size_t)k * b;        // partial B V (high, low)
+    BV = o;  o += 2 * (size_t)k * b;        // B V
+    HPp = o; o += 2 * (size_t)b * b;        // partial H, P
+    Gp = o;  o += (size_t)k * k;            // partial C C^T
+    CVp = o; o += (size_t)k * ss;           // partial C V_s
+    Ml = o;  o += 3 * (size_t)b * b;        // local copies of Y, Mv, Mz
+    Wk = o;  o += 10 * (size_t)DS_BM * DS_P;    // Rayleigh-Ritz work arrays
+    total = o;
+  }
+};
+
+// Rayleigh-Ritz step of the subspace iteration on one CTA (DS_THREADS threads), b <= 32.
+// In: H (=V^T G2 V) and P (=Z^T Z) in wk[0] and wk[4]; out: the sorted eigenvectors Y,
+// Mv and Mz (b x b, column-major, at wk + 7*DS_BM*DS_P, + 8*, + 9*), theta and resid.
+//  - H = Y Theta Y^T by the parallel cyclic Jacobi method (round-robin ordering); a round
+//    computes its b/2 rotation angles, then H <- J^T H J and Y <- Y J element by element
+//    into the other buffer of a pair (two barriers per round).
+//  - Next basis W = [V Y F_v + Z Y F_z], F_z = diag(1/||Z y_c||) for the columns with a
+//    non-negligible Ritz value, F_v = 1 for the others; W^T W = L L^T (Cholesky of the
+//    Gram formed from I, Y^T P Y and Theta); Mv = Y F_v L^{-T}, Mz = Y F_z L^{-T}.
+template <typename T>
+__device__ void ritz_step(T* wk, int b, int max_sweeps, T* __restrict__ theta,
+                          T* __restrict__ resid, int* __restrict__ err) {
+  using Row = T[DS_P];
+  Row* Hc = reinterpret_cast<Row*>(wk);                      // current / next buffers
+  Row* Hn = reinterpret_cast<Row*>(wk + DS_BM * DS_P);
+  Row* Yc = reinterpret_cast<Row*>(wk + 2 * DS_BM * DS_P);
+  Row* Yn = reinterpret_cast<Row*>(wk + 3 * DS_BM * DS_P);
+  Row* Pm = reinterpret_cast<Row*>(wk + 4 * DS_BM * DS_P);
+  Row* Wm = reinterpret_cast<Row*>(wk + 5 * DS_BM * DS_P);   // sorted eigenvectors
+  Row* Gm = reinterpret_cast<Row*>(wk + 6 * DS_BM * DS_P);   // Gram, then its factor
+  T* Yo = wk + 7 * DS_BM * DS_P;                             // outputs, b x b col-major
+  T* Mvo = wk + 8 * DS_BM * DS_P;
+  T* Mzo = wk + 9 * DS_BM * DS_P;
+  __shared__ T cx[DS_BM], sg[DS_BM], th[DS_BM], fz[DS_BM], rdg[DS_BM];
+  __shared__ int partner[DS_BM], perm[DS_BM], usev[DS_BM];
+  __shared__ T red[2][DS_THREADS / 32];
+  __shared__ int bad_s;
+  const int tid = threadIdx.x;
+  const int bb = b * b;
+
+  // symmetric H, Y = I, zero padding of both buffers (the dummy index b of an odd b is
+  // read with a zero coefficient)
+  for (int e = tid; e < DS_BM * DS_P; e += DS_THREADS) {
+    const int r = e / DS_P, c = e % DS_P;
+    const bool in = r < b && c < b;
+    Hn[r][c] = T(0);
+    Yc[r][c] = (r == c && r < b) ? T(1) : T(0);
+    Yn[r][c] = T(0);
+    if (!in) {
+      Hc[r][c] = T(0);
+      Pm[r][c] = T(0);
+    }
+  }
+  if (tid == 0) bad_s = 0;
+  __syncthreads();
+  for (int e = tid; e < bb; e += DS_THREADS) {
+    const int r = e % b, c = e / b;
+    if (r < c) {
+      const T v = T(0.5) * (Hc[r][c] + Hc[c][r]);
+      Hc[r][c] = v;
+      Hc[c][r] = v;
+    }
+  }
+  __syncthreads();
+
+  const int N = (b + 1) & ~1, half = N / 2;
+  const T eps = T(4 * b) * (sizeof(T) == 4 ? T(5.96e-8) : T(1.11e-16));
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    T off = T(0), tot = T(0);
+    for (int e = tid; e < bb; e += DS_THREADS) {
+      const int r = e % b, c = e / b;
+      const T v = Hc[r][c];
+      tot += v * v;
+      if (r != c) off += v * v;
+    }
+    off = warp_sum(off);
+    tot = warp_sum(tot);
+    if ((tid & 31) == 0) {
+      red[0][tid >> 5] = off;
+      red[1][tid >> 5] = tot;
+    }
+    __syncthreads();
+    off = T(0);
+    tot = T(0);
+#pragma unroll
+    for (int w = 0; w < DS_THREADS / 32; ++w) {
+      off += red[0][w];
+      tot += red[1][w];
+    }
+    __syncthreads();
+    if (off <= eps * eps * tot) break;
+    for (int round = 0; round < N - 1; ++round) {
+      if (tid < half) {
+        int p = tid == 0 ? N - 1 : round + tid;
+        if (tid != 0 && p >= N - 1) p -= N - 1;
+        int q = round + N - 1 - tid;
+        if (q >= N - 1) q -= N - 1;
+        if (p > q) { const int t = p; p = q; q = t; }
+        T c = T(1), sn = T(0);
+        if (q < b) {
+          const T apq = Hc[p][q];
+          if (apq != T(0)) {
+            // t = sign(tau) / (|tau| + sqrt(1 + tau^2)), c = 1 / sqrt(1 + t^2), s = t c;
+            // square roots as x rsqrt(x), about 1/(2 tau) once tau^2 would overflow
+            const T tau = (Hc[q][q] - Hc[p][p]) / (T(2) * apq);
+            const T at = fabs(tau), tt = T(1) + tau * tau;
+            const T ta = at > T(1e15) ? T(0.5) * wrcp(at) : wrcp(at + tt * wrsqrt(tt));
+            const T t = tau >= T(0) ? ta : -ta;
+            c = wrsqrt(T(1) + t * t);
+            sn = t * c;
+          }
+        }
+        cx[p] = c;  sg[p] = -sn; partner[p] = q;
+        cx[q] = c;  sg[q] = sn;  partner[q] = p;
+      }
+      __syncthreads();
+      for (int e = tid; e < bb; e += DS_THREADS) {
+        const int r = e % b, c = e / b;
+        const int r2 = partner[r], c2 = partner[c];
+        const T cr = cx[r], sr = sg[r], cc = cx[c], sc = sg[c];
+        const T h00 = Hc[r][c], h01 = Hc[r][c2];
+        const T h10 = Hc[r2][c], h11 = Hc[r2][c2];
+        Hn[r][c] = cr * (cc * h00 + sc * h01) + sr * (cc * h10 + sc * h11);
+        Yn[r][c] = cc * Yc[r][c] + sc * Yc[r][c2];
+      }
+      __syncthreads();
+      Row* t0 = Hc; Hc = Hn; Hn = t0;
+      Row* t1 = Yc; Yc = Yn; Yn = t1;
+    }
+  }
+  Row* H = Hc;
+  Row* Y = Yc;
+  Row* S = Hn;   // scratch: P Y, then the Cholesky factor
+  // ---- sort descending: c's rank = #{d : theta_d > theta_c, or equal with d < c}
+  if (tid < b) {
+    const T tc = H[tid][tid];
+    int rank = 0;
+    for (int d = 0; d < b; ++d) {
+      const T td = H[d][d];
+      rank += (td > tc) || (td == tc && d < tid);
+    }
+    perm[rank] = tid;
+    if (!wfinite(tc)) atomicOr(err, ERRBIT_EIG);
+  }
+  __syncthreads();
+  if (tid < b) th[tid] = H[perm[tid]][perm[tid]];
+  for (int e = tid; e < bb; e += DS_THREADS) {
+    const int r = e % b, c = e / b;
+    Wm[r][c] = Y[r][perm[c]];
+  }
+  __syncthreads();
+  // S = P W, then Pm <- W^T P W
+  for (int e = tid; e < bb; e += DS_THREADS) {
+    const int r = e % b, c = e / b;
+    T v = T(0);
+    for (int l = 0; l < b; ++l) v = fma(Pm[r][l], Wm[l][c], v);
+    S[r][c] = v;
+  }
+  __syncthreads();
+  for (int e = tid; e < bb; e += DS_THREADS) {
+    const int r = e % b, c = e / b;
+    T v = T(0);
+    for (int l = 0; l < b; ++l) v = fma(Wm[l][r], S[l][c], v);
+    Pm[r][c] = v;
+  }
+  __syncthreads();
+  if (tid < b) {
+    const int c = tid;
+    const T tmax = fabs(th[0]);
+    const T small = sizeof(T) == 4 ? T(1e-6) : T(1e-13);
+    const T nz2 = Pm[c][c];
+    const bool use_v = !(th[c] > small * tmax) || !(nz2 > T(0));
+    usev[c] = use_v ? 1 : 0;
+    fz[c] = use_v ? T(0) : T(1) / wsqrt(nz2);
+    resid[c] = nz2 - th[c] * th[c];
+    theta[c] = th[c];
+  }
+  __syncthreads();
+  // Gram of W: <Vy_a, Vy_b> = delta_ab, <Zy_a, Zy_b> = fz_a fz_b (Y^T P Y)_ab, mixed 0
+  for (int e = tid; e < bb; e += DS_THREADS) {
+    const int r = e % b, c = e / b;
+    T g;
+    if (usev[r] && usev[c]) g = r == c ? T(1) : T(0);
+    else if (!usev[r] && !usev[c]) g = fz[r] * fz[c] * Pm[r][c];
+    else g = T(0);
+    Gm[r][c] = g;
+  }
+  __syncthreads();
+  // W^T W = L D L^T by symmetric elimination (step t: the trailing lower triangle takes
+  // G(i,j) -= G(i,t) G(j,t) / G(t,t)); the Cholesky factor is L D^{1/2}
+  for (int t = 0; t < b; ++t) {
+    T d = Gm[t][t];
+    if (!(d > T(0)) || !wfinite(d)) d = T(1);
+    const T rd = T(1) / d;
+    for (int e = tid; e < bb; e += DS_THREADS) {
+      const int i = e % b, j = e / b;
+      if (i >= j && j > t) Gm[i][j] = fma(-Gm[i][t] * rd, Gm[j][t], Gm[i][j]);
+    }
+    __syncthreads();
+  }
+  // S = L D^{1/2} (lower), rdg = 1 / S(t,t)
+  for (int e = tid; e < bb; e += DS_THREADS) {
+    const int i = e % b, t = e / b;
+    T d = Gm[t][t];
+    if (!(d > T(0)) || !wfinite(d)) {
+      if (i == t) bad_s = 1;
+      d = T(1);
+    }
+    const T rl = wrsqrt(d);
+    S[i][t] = i > t ? Gm[i][t] * rl : (i == t ? d * rl : T(0));
+    if (i == t) rdg[t] = rl;
+  }
+  __syncthreads();
+  if (tid == 0 && bad_s) atomicOr(err, ERRBIT_EIG);
+  // X = S^{-1} (lower) into Gm: rows of the identity, row t final at step t up to 1/S(t,t)
+  for (int e = tid; e < bb; e += DS_THREADS) {
+    const int i = e % b, c = e / b;
+    Gm[i][c] = i == c ? T(1) : T(0);
+  }
+  __syncthreads();
+  for (int t = 0; t < b - 1; ++t) {
+    for (int e = tid; e < bb; e += DS_THREADS) {
+      const int i = e % b, c = e / b;
+      if (i > t && c <= t) Gm[i][c] = fma(-S[i][t] * rdg[t], Gm[t][c], Gm[i][c]);
+    }
+    __syncthreads();
+  }
+  // Mv(r, c) = sum_l W(r, l) [use_v(l)] X(c, l), Mz(r, c) = sum_l W(r, l) fz(l) X(c, l)
+  for (int e = tid; e < bb; e += DS_THREADS) {
+    const int r = e % b, c = e / b;
+    T mv = T(0), mz = T(0);
+    for (int l = 0; l <= c; ++l) {
+      const T x = Gm[c][l] * rdg[c];
+      const T y = Wm[r][l] * x;
+      if (usev[l]) mv += y;
+      else mz += y * fz[l];
+    }
+    Yo[e] = Wm[r][c];
+    Mvo[e] = mv;
+    Mzo[e] = mz;
+  }
+  __syncthreads();
+}
+
+// (K V)(l, c) for all rows in double-float.  Block = KV_ROWS rows x 128 threads per row;
+// thread g of a row takes j = g, g + 128, ... (K is symmetric, so row l of K is the
+// contiguous column l) and loads its K and V entries straight from global memory; the 128
+// partial sums of a row are combined by warp shuffles, then across the row's 4 warps in
+// fixed order.
+constexpr int KV_ROWS = 2;
+constexpr int KV_JT = 128;   // threads per row
+constexpr int KV_JMAX = 8;   // j values per thread (n2 <= KV_JT * KV_JMAX = 1024)
+template <typename T, int BC>
+__global__ void __launch_bounds__(KV_ROWS * KV_JT)
+kv_pair(const T* __restrict__ Kh, const T* __restrict__ Kl, const T* __restrict__ V, int n2, int b,
+        T* __restrict__ ZKh, T* __restrict__ ZKl) {
+  __shared__ T red[KV_ROWS][KV_JT / 32][2][BC];
+  const int g = threadIdx.x % KV_JT, u = threadIdx.x / KV_JT;
+  const int lane = threadIdx.x & 31, wr = g >> 5;
+  const int l = blockIdx.x * KV_ROWS + u;
+  const bool live = l < n2;
+  DfAcc<T> acc[BC];
+#pragma unroll
+  for (int q = 0; q < KV_JMAX; ++q) {
+    const int j = g + KV_JT * q;
+    if (j < n2 && live) {
+      const int64_t o = j + (int64_t)l * n2;
+      const T kh = Kh[o];
+      const T kl = Kl ? Kl[o] : T(0);
+#pragma unroll
+      for (int c = 0; c < BC; ++c)
+        if (c < b) acc[c].add(kh, kl, V[j + (int64_t)c * n2]);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < BC; ++c) {
+    if (c < b) {
+      acc[c].warp_reduce();
+      if (lane == 0) {
+        red[u][wr][0][c] = acc[c].hi;
+        red[u][wr][1][c] = acc[c].lo;
+      }
+    }
+  }
+  __syncthreads();
+  if (g < b && live) {
+    DfAcc<T> s;
+#pragma unroll
+    for (int w = 0; w < KV_JT / 32; ++w) s.add_pair(red[u][w][0][g], red[u][w][1][g]);
+    ZKh[l + (int64_t)g * n2] = s.hi;
+    if (ZKl) ZKl[l + (int64_t)g * n2] = s.lo;
+  }
+}
+
+// The cluster kernel (grid = one cluster of NC CTAs, DS_THREADS threads each).
+template <typename T>
+__global__ void __launch_bounds__(DS_THREADS)
+dstep_cluster(DstepArgs<T> a) {
+  extern __shared__ unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  cgrp::cluster_group cluster = cgrp::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int nc = (int)cluster.num_blocks();
+  const int tid = threadIdx.x;
+  const int n2 = a.n2, k = a.k, b = a.b, s = a.s, NP = a.NP;
+  const int R = (n2 + nc - 1) / nc;
+  const int l0 = min(n2, rank * R), l1 = min(n2, l0 + R), nr = l1 - l0;
+  const DsLayout L(n2, k, b, s, R);
+  T* Vt = sm + L.Vt;
+  T* Bs = sm + L.Bs;
+  T* Cs = sm + L.Cs;
+  T* Zh = sm + L.Zh;
+  T* Zl = sm + L.Zl;
+  T* Zr = sm + L.Zr;
+  T* Vsr = sm + L.Vsr;
+  T* BVp = sm + L.BVp;
+  T* BV = sm + L.BV;
+  T* HPp = sm + L.HPp;
+  T* Gp = sm + L.Gp;
+  T* CVp = sm + L.CVp;
+  T* Ml = sm + L.Ml;
+  T* Wk = sm + L.Wk;
+  const int kb = k * b;
+
+  // ---- inputs into shared memory (asynchronous copies, one group): the whole basis,
+  // and for the CTA's rows: B's columns, C (from Z2), K V
+  for (int e = tid; e < b * n2; e += DS_THREADS) cp_async_elem(Vt + e, a.V + e, true);
+  for (int e = tid; e < k * nr; e += DS_THREADS) {
+    cp_async_elem(Bs + e, a.Bh + (int64_t)l0 * k + e, true);
+    if (a.Bl) cp_async_elem(Bs + k * R + e, a.Bl + (int64_t)l0 * k + e, true);
+    const int rr = e / k, x = e % k;
+    cp_async_elem(Cs + e, a.Z2 + (int64_t)(l0 + rr) * NP + x, true);
+  }
+  for (int e = tid; e < b * nr; e += DS_THREADS) {
+    const int c = e / nr, rr = e % nr;
+    cp_async_elem(Zh + c * R + rr, a.ZKh + l0 + rr + (int64_t)c * n2, true);
+    if (a.ZKl) cp_async_elem(Zl + c * R + rr, a.ZKl + l0 + rr + (int64_t)c * n2, true);
+  }
+  cp_async_commit();
+  cp_async_wait<0>();
+  __syncthreads();
+
+  // ---- partial C C^T and B V over the CTA's rows
+  for (int e = tid; e < k * k; e += DS_THREADS) {
+    const int x = e % k, y = e / k;
+    T v = T(0);
+    for (int rr = 0; rr < nr; ++rr) v = fma(Cs[rr * k + x], Cs[rr * k + y], v);
+    Gp[e] = v;
+  }
+  for (int e = tid; e < kb; e += DS_THREADS) {
+    const int x = e % k, c = e / k;
+    DfAcc<T> acc;
+    for (int rr = 0; rr < nr; ++rr)
+      acc.add(Bs[rr * k + x], a.Bl ? Bs[k * R + rr * k + x] : T(0), Vt[c * n2 + l0 + rr]);
+    BVp[e] = acc.hi;
+    BVp[kb + e] = acc.lo;
+  }
+  cluster.sync();
+  // ---- B V: the CTAs' partials in rank order
+  for (int e = tid; e < kb; e += DS_THREADS) {
+    T ph[16], pl[16];
+    DfAcc<T> acc;
+    for (int r0 = 0; r0 < nc; r0 += 16) {
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        if (r0 + u < nc) {
+          const T* rp = cluster.map_shared_rank(BVp, r0 + u);
+          ph[u] = rp[e];
+          pl[u] = rp[kb + e];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 16; ++u)
+        if (r0 + u < nc) acc.add_pair(ph[u], pl[u]);
+    }
+    BV[e] = acc.hi;
+    BV[kb + e] = acc.lo;
+  }
+  __syncthreads();
+  // ---- Z(rows) = K V - B^T (B V), rounded to T after the subtraction
+  for (int e = tid; e < nr * b; e += DS_THREADS) {
+    const int rr = e % nr, c = e / nr;
+    DfAcc<T> acc;
+    acc.hi = Zh[c * R + rr];
+    acc.lo = a.ZKl ? Zl[c * R + rr] : T(0);
+    for (int x = 0; x < k; ++x)
+      acc.sub2(Bs[rr * k + x], a.Bl ? Bs[k * R + rr * k + x] : T(0), BV[x + c * k], BV[kb + x + c * k]);
+    Zr[rr * b + c] = acc.hi + acc.lo;
+  }
+  __syncthreads();
+  // ---- partial H = V^T Z and P = Z^T Z over the CTA's rows
+  for (int e = tid; e < b * b; e += DS_THREADS) {
+    const int c1 = e % b, c2 = e / b;
+    T h = T(0), p = T(0);
+    for (int rr = 0; rr < nr; ++rr) {
+      const T z2 = Zr[rr * b + c2];
+      h = fma(Vt[c1 * n2 + l0 + rr], z2, h);
+      p = fma(Zr[rr * b + c1], z2, p);
+    }
+    HPp[e] = h;
+    HPp[b * b + e] = p;
+  }
+  cluster.sync();
+  // ---- Rayleigh-Ritz on CTA 0
+  if (rank == 0) {
+    for (int e = tid; e < b * b; e += DS_THREADS) {
+      T h = T(0), p = T(0);
+      for (int r = 0; r < nc; ++r) {
+        const T* rp = cluster.map_shared_rank(HPp, r);
+        h += rp[e];
+        p += rp[b * b + e];
+      }
+      const int r_ = e % b, c_ = e / b;
+      Wk[r_ * DS_P + c_] = h;                       // H into work array 0
+      Wk[4 * DS_BM * DS_P + r_ * DS_P + c_] = p;    // P into work array 4
+    }
+    __syncthreads();
+    ritz_step<T>(Wk, b, a.sweeps, a.theta, a.resid, a.err);
+  }
+  cluster.sync();
+  // ---- next basis rows and Ritz vectors (Y, Mv, Mz from CTA 0)
+  {
+    const T* w0 = cluster.map_shared_rank(Wk, 0);
+    T* Yl = Ml;
+    T* Mvl = Ml + b * b;
+    T* Mzl = Ml + 2 * b * b;
+    for (int e = tid; e < b * b; e += DS_THREADS) {
+      Yl[e] = w0[7 * DS_BM * DS_P + e];
+      Mvl[e] = w0[8 * DS_BM * DS_P + e];
+      Mzl[e] = w0[9 * DS_BM * DS_P + e];
+    }
+    __syncthreads();
+    for (int e = tid; e < nr * b; e += DS_THREADS) {
+      const int rr = e % nr, c = e / nr;
+      const int l = l0 + rr;
+      T vr = T(0), vn = T(0);
+      for (int x = 0; x < b; ++x) {
+        const T v = Vt[x * n2 + l], z = Zr[rr * b + x];
+        vr = fma(v, Yl[x + c * b], vr);
+        vn = fma(v, Mvl[x + c * b], vn);
+        vn = fma(z, Mzl[x + c * b], vn);
+      }
+      a.V[l + (int64_t)c * n2] = vn;
+      if (c < s) {
+        a.Vs[l + (int64_t)c * n2] = vr;
+        a.Z2[(int64_t)l * NP + k + c] = vr;
+        Vsr[rr * s + c] = vr;
+      }
+    }
+  }
+  __syncthreads();
+  // ---- partial C V_s over the CTA's rows, then CTA 0 sums C C^T and C V_s
+  for (int e = tid; e < k * s; e += DS_THREADS) {
+    const int x = e % k, c = e / k;
+    T v = T(0);
+    for (int rr = 0; rr < nr; ++rr) v = fma(Cs[rr * k + x], Vsr[rr * s + c], v);
+    CVp[e] = v;
+  }
+  cluster.sync();
+  if (rank == 0) {
+    for (int e = tid; e < k * k; e += DS_THREADS) {
+      double v = 0.0;
+      for (int r = 0; r < nc; ++r) v += (double)cluster.map_shared_rank(Gp, r)[e];
+      a.G[e] = (T)v;
+    }
+    for (int e = tid; e < k * s; e += DS_THREADS) {
+      double v = 0.0;
+      for (int r = 0; r < nc; ++r) v += (double)cluster.map_shared_rank(CVp, r)[e];
+      a.CV[e] = (T)v;
+    }
+  }
+  // every CTA keeps its shared memory until CTA 0 has read it
+  cluster.sync();
+}
+
+// K = Kh + Kl as a float pair (once per problem).
+static __global__ void split_pair(const double* __restrict__ K, int64_t n, float* __restrict__ Kh,
+                           float* __restrict__ Kl) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const double v = K[e];
+    const float h = (float)v;
+    Kh[e] = h;
+    Kl[e] = (float)(v - (double)h);
+  }
+}
+
+}  // namespace wlr

@@ -7,6 +7,7 @@
 
 #include <cudaTypedefs.h>
 
+#include "wlr_dstep.cuh"
 #include "wlr_kernels.cuh"
 #include "wlr_solver.cuh"
 #include "wlr_tc.cuh"
@@ -86,6 +87,7 @@ class Solver final : public SolverBase {
     iter_ = dalloc<int>(1);
     err_ = dalloc<int>(1);
     if (std::is_same<T, float>::value && n2 > 0) setup_tc();
+    setup_dstep();
     WLR_CUDA(cudaMemsetAsync(Z2_, 0, sizeof(T) * std::max<size_t>((size_t)n2 * NP, 1), stream_));
     WLR_CUDA(cudaMemsetAsync(Z2prev_, 0, sizeof(T) * std::max<size_t>((size_t)n2 * NP, 1), stream_));
     WLR_CUDA(cudaMemsetAsync(err_, 0, sizeof(int), stream_));
@@ -242,10 +244,10 @@ class Solver final : public SolverBase {
       begin();
       qr_coef(cur_);
       if (d_.s > 0) {
-        form_g2_launch();
+        if (!use_dstep_) form_g2_launch();
         converge_eig();
       }
-      prep();
+      if (!use_dstep_ || d_.s == 0) prep();
       cd_valid_ = true;
       double e6[6];
       x2_eval(cur_, -1, nullptr, 0, e6);
@@ -661,6 +663,10 @@ class Solver final : public SolverBase {
     count(2);
     gram(A2, lda_, A2, lda_, n2, nullptr, 0, n2, n2, (int64_t)n2 * n2, ch_K_);
     reduce64((int64_t)n2 * n2, ch_K_.nch, (int64_t)n2 * n2, K64_);
+    if (use_dstep_ && Kh_) {
+      split_pair<<<grid1d((int64_t)n2 * n2), 256, 0, stream_>>>(K64_, (int64_t)n2 * n2, Kh_, Kl_);
+      count(1);
+    }
     tc_split_a2();
   }
   double* wpart_scratch(int n) {
@@ -747,6 +753,115 @@ class Solver final : public SolverBase {
                                                     d_.NP, Vs_, Z2_);
     count(3);
   }
+  // The fused cluster kernel of step a3 (and of G, C V_s): used when s > 0, b <= 32, the
+  // device runs a cluster of 16 (or else 8) CTAs with the kernel's shared memory.
+  void setup_dstep() {
+    const int n2 = d_.n2, k = d_.k, b = d_.b, s = d_.s;
+    if (s <= 0 || n2 <= 0 || b > DS_BM) return;
+    if (n2 > KV_JT * KV_JMAX) return;
+    const void* fn = (const void*)dstep_cluster<T>;
+    for (int nc : {16, 8}) {
+      if (n2 < nc) continue;
+      const size_t bytes = sizeof(T) * DsLayout(n2, k, b, s, cdiv(n2, nc)).total;
+      if (bytes > 200 * 1024) continue;
+      if (nc > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+        cudaGetLastError();
+        continue;
+      }
+      if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess) {
+        cudaGetLastError();
+        continue;
+      }
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(nc);
+      cfg.blockDim = dim3(DS_THREADS);
+      cfg.dynamicSmemBytes = bytes;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = nc;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      int ncl = 0;
+      if (cudaOccupancyMaxActiveClusters(&ncl, fn, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        continue;
+      }
+      if (ncl < 1) continue;
+      ds_nc_ = nc;
+      ds_smem_ = bytes;
+      use_dstep_ = true;
+      break;
+    }
+    if (!use_dstep_) return;
+    ZKh_ = dalloc<T>((size_t)n2 * b);
+    if (std::is_same<T, float>::value) {
+      Kh_ = dalloc<float>((size_t)n2 * n2);
+      Kl_ = dalloc<float>((size_t)n2 * n2);
+      ZKl_ = dalloc<T>((size_t)n2 * b);
+    }
+  }
+  // q subspace steps: K V on all SMs, then the cluster kernel (which also leaves
+  // G = C C^T and C V_s for the row pass)
+  void dstep_run(int q, bool cold) {
+    const int n2 = d_.n2, b = d_.b;
+    DstepArgs<T> a;
+    const T *Kh, *Kl;
+    if constexpr (std::is_same<T, float>::value) {
+      Kh = Kh_;
+      Kl = Kl_;
+      a.Bh = Bh_;
+      a.Bl = Bl_;
+    } else {
+      Kh = K64_;
+      Kl = nullptr;
+      a.Bh = B64_;
+      a.Bl = nullptr;
+    }
+    a.ZKh = ZKh_;
+    a.ZKl = ZKl_;
+    a.Z2 = Z2_;
+    a.V = V_;
+    a.Vs = Vs_;
+    a.theta = theta_;
+    a.resid = resid_;
+    a.G = G_;
+    a.CV = CV_;
+    a.err = err_;
+    a.n2 = n2;
+    a.k = d_.k;
+    a.b = b;
+    a.s = d_.s;
+    a.NP = d_.NP;
+    a.sweeps = cold ? (sizeof(T) == 4 ? 12 : 24) : (sizeof(T) == 4 ? 1 : 6);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ds_nc_);
+    cfg.blockDim = dim3(DS_THREADS);
+    cfg.dynamicSmemBytes = ds_smem_;
+    cfg.stream = stream_;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = ds_nc_;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    for (int t = 0; t < q; ++t) {
+      {
+        Prof pf(this, "kv_pair");
+        if (b <= 16)
+          kv_pair<T, 16><<<cdiv(n2, KV_ROWS), KV_ROWS * KV_JT, 0, stream_>>>(Kh, Kl, V_, n2, b, ZKh_, ZKl_);
+        else
+          kv_pair<T, 32><<<cdiv(n2, KV_ROWS), KV_ROWS * KV_JT, 0, stream_>>>(Kh, Kl, V_, n2, b, ZKh_, ZKl_);
+      }
+      {
+        Prof pf(this, "dstep");
+        WLR_CUDA(cudaLaunchKernelEx(&cfg, dstep_cluster<T>, a));
+      }
+      count(2);
+    }
+  }
   void eig_start() {
     eig_random_start<T><<<grid1d((int64_t)d_.n2 * d_.b), 256, 0, stream_>>>(V_, d_.n2, d_.b, o_.seed);
     count(1);
@@ -763,7 +878,6 @@ class Solver final : public SolverBase {
   void compute_cd(int xi, bool warm, bool precond = false) {
     qr_coef(xi, precond);
     if (d_.s > 0) {
-      form_g2_launch();
       int q = warm ? o_.eig_iters : o_.eig_iters_cold;
       bool cold = false;
       if (eig_cold_) {
@@ -772,9 +886,16 @@ class Solver final : public SolverBase {
         eig_cold_ = false;
         cold = true;
       }
-      for (int t = 0; t < q; ++t) eig_iteration(cold);
+      if (use_dstep_) {
+        dstep_run(q, cold);   // also G = C C^T and C V_s
+      } else {
+        form_g2_launch();
+        for (int t = 0; t < q; ++t) eig_iteration(cold);
+        prep();
+      }
+    } else {
+      prep();
     }
-    prep();
     cd_valid_ = true;
   }
   // iterate the subspace step until the wanted Ritz values settle (FP64 scoring)
@@ -786,7 +907,9 @@ class Solver final : public SolverBase {
     const int s = d_.s;
     std::vector<T> prev(s, (T)0), now(s);
     for (int round = 0; round < 400; ++round) {
-      for (int t = 0; t < 10; ++t) eig_iteration(true);
+      if (use_dstep_) dstep_run(10, true);
+      else
+        for (int t = 0; t < 10; ++t) eig_iteration(true);
       WLR_CUDA(cudaMemcpyAsync(hbuf_ + 128, theta_, sizeof(T) * s, cudaMemcpyDeviceToHost, stream_));
       WLR_CUDA(cudaStreamSynchronize(stream_));
       std::memcpy(now.data(), hbuf_ + 128, sizeof(T) * s);
@@ -896,6 +1019,11 @@ class Solver final : public SolverBase {
   T *Q1_ = nullptr, *R1inv_ = nullptr, *Nm_ = nullptr, *Rinv_ = nullptr;
   double *part64_ = nullptr, *S2T_ = nullptr;
   T* F2_ = nullptr;   // S2 - I for the second Cholesky factor (k <= 32)
+  bool use_dstep_ = false;   // fused cluster kernel for step a3
+  int ds_nc_ = 0;
+  size_t ds_smem_ = 0;
+  float *Kh_ = nullptr, *Kl_ = nullptr;   // K as a float pair (float path)
+  T *ZKh_ = nullptr, *ZKl_ = nullptr;     // K V (high, low)
   T *C_ = nullptr, *Z2_ = nullptr, *Z2prev_ = nullptr;
   double *B64_ = nullptr, *bpart_ = nullptr, *K64_ = nullptr, *prep_part_ = nullptr;
   float *Bh_ = nullptr, *Bl_ = nullptr;
