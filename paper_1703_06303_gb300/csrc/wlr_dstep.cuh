@@ -27,7 +27,7 @@ namespace wlr {
 
 namespace cgrp = cooperative_groups;
 
-constexpr int DS_THREADS = 256;
+constexpr int DS_THREADS = 512;
 constexpr int DS_BM = EIG_BMAX;   // largest b
 constexpr int DS_P = DS_BM + 1;   // row pitch of the b x b work arrays
 
@@ -127,12 +127,15 @@ struct DsLayout {
 // Rayleigh-Ritz step of the subspace iteration on one CTA (DS_THREADS threads), b <= 32.
 // In: H (=V^T G2 V) and P (=Z^T Z) in wk[0] and wk[4]; out: the sorted eigenvectors Y,
 // Mv and Mz (b x b, column-major, at wk + 7*DS_BM*DS_P, + 8*, + 9*), theta and resid.
-//  - H = Y Theta Y^T by the parallel cyclic Jacobi method (round-robin ordering); a round
-//    computes its b/2 rotation angles, then H <- J^T H J and Y <- Y J element by element
-//    into the other buffer of a pair (two barriers per round).
+//  - H = Y Theta Y^T by the parallel cyclic Jacobi method (round-robin ordering): a round
+//    applies its b/2 rotations, H <- J^T H J and Y <- Y J element by element into the
+//    other buffer of a pair, while threads tid < b/2 take the next round's angles from the
+//    rotated entries they need (one barrier per round).
 //  - Next basis W = [V Y F_v + Z Y F_z], F_z = diag(1/||Z y_c||) for the columns with a
 //    non-negligible Ritz value, F_v = 1 for the others; W^T W = L L^T (Cholesky of the
 //    Gram formed from I, Y^T P Y and Theta); Mv = Y F_v L^{-T}, Mz = Y F_z L^{-T}.
+// Each thread owns the elements e = tid and tid + DS_THREADS of a b x b array (row
+// e % b, column e / b), indexed once.
 template <typename T>
 __device__ void ritz_step(T* wk, int b, int max_sweeps, T* __restrict__ theta,
                           T* __restrict__ resid, int* __restrict__ err) {
@@ -143,16 +146,38 @@ __device__ void ritz_step(T* wk, int b, int max_sweeps, T* __restrict__ theta,
   Row* Yn = reinterpret_cast<Row*>(wk + 3 * DS_BM * DS_P);
   Row* Pm = reinterpret_cast<Row*>(wk + 4 * DS_BM * DS_P);
   Row* Wm = reinterpret_cast<Row*>(wk + 5 * DS_BM * DS_P);   // sorted eigenvectors
-  Row* Gm = reinterpret_cast<Row*>(wk + 6 * DS_BM * DS_P);   // Gram, then its factor
+  Row* Gm = reinterpret_cast<Row*>(wk + 6 * DS_BM * DS_P);   // Gram, then its elimination
   T* Yo = wk + 7 * DS_BM * DS_P;                             // outputs, b x b col-major
   T* Mvo = wk + 8 * DS_BM * DS_P;
   T* Mzo = wk + 9 * DS_BM * DS_P;
-  __shared__ T cx[DS_BM], sg[DS_BM], th[DS_BM], fz[DS_BM], rdg[DS_BM];
-  __shared__ int partner[DS_BM], perm[DS_BM], usev[DS_BM];
+  // rotation of index x in a round: J(x,x) = c, J(partner, x) = s (one 16-byte load for float)
+  struct alignas(2 * sizeof(T)) Rot {
+    T c, s;
+    int partner, pad;
+  };
+  __shared__ Rot rot[2][DS_BM];
+  __shared__ T th[DS_BM], fz[DS_BM], rdg[DS_BM];
+  __shared__ int perm[DS_BM], usev[DS_BM];
   __shared__ T red[2][DS_THREADS / 32];
   __shared__ int bad_s;
   const int tid = threadIdx.x;
   const int bb = b * b;
+  constexpr int NE = (DS_BM * DS_BM + DS_THREADS - 1) / DS_THREADS;
+  int er[NE], ec[NE];
+#pragma unroll
+  for (int q = 0; q < NE; ++q) {
+    const int e = tid + q * DS_THREADS;
+    er[q] = e % b;
+    ec[q] = e / b;
+  }
+  // f(e, r, c) for each of this thread's elements
+  auto each = [&](auto&& f) {
+#pragma unroll
+    for (int q = 0; q < NE; ++q) {
+      const int e = tid + q * DS_THREADS;
+      if (e < bb) f(e, er[q], ec[q]);
+    }
+  };
 
   // symmetric H, Y = I, zero padding of both buffers (the dummy index b of an odd b is
   // read with a zero coefficient)
@@ -169,26 +194,61 @@ __device__ void ritz_step(T* wk, int b, int max_sweeps, T* __restrict__ theta,
   }
   if (tid == 0) bad_s = 0;
   __syncthreads();
-  for (int e = tid; e < bb; e += DS_THREADS) {
-    const int r = e % b, c = e / b;
+  each([&](int, int r, int c) {
     if (r < c) {
       const T v = T(0.5) * (Hc[r][c] + Hc[c][r]);
       Hc[r][c] = v;
       Hc[c][r] = v;
     }
-  }
+  });
   __syncthreads();
 
   const int N = (b + 1) & ~1, half = N / 2;
   const T eps = T(4 * b) * (sizeof(T) == 4 ? T(5.96e-8) : T(1.11e-16));
+  // pair i of a round of the round-robin order (N even): index N - 1 meets `round`, and
+  // i, j < N - 1 meet when i + j = 2 round (mod N - 1)
+  auto pair_of = [&](int round, int i, int& p, int& q) {
+    p = i == 0 ? N - 1 : round + i;
+    if (i != 0 && p >= N - 1) p -= N - 1;
+    q = round + N - 1 - i;
+    if (q >= N - 1) q -= N - 1;
+    if (p > q) { const int t = p; p = q; q = t; }
+  };
+
+  // rotation annihilating (p, q): t = sign(tau) / (|tau| + sqrt(1 + tau^2)),
+  // c = 1 / sqrt(1 + t^2), s = t c (square roots as x rsqrt(x); t ~ 1/(2 tau) once tau^2
+  // would overflow, which also covers a 1 / (2 a_pq) that overflows)
+  auto set_rot = [&](int cb, int p, int q, T app, T aqq, T apq) {
+    T c = T(1), sn = T(0);
+    if (q < b && apq != T(0)) {
+      const T dq = aqq - app;
+      const T tau = dq == T(0) ? T(0) : dq * wrcp(T(2) * apq);
+      const T at = fabs(tau), tt = T(1) + tau * tau;
+      const T ta = at > T(1e15) ? T(0.5) * wrcp(at) : wrcp(at + tt * wrsqrt(tt));
+      const T t = tau >= T(0) ? ta : -ta;
+      c = wrsqrt(T(1) + t * t);
+      sn = t * c;
+    }
+    rot[cb][p] = Rot{c, -sn, q, 0};
+    rot[cb][q] = Rot{c, sn, p, 0};
+  };
+  // entry (r, c) of J^T H J for the rotation set cb
+  auto rotated = [&](int cb, int r, int c) -> T {
+    const Rot R = rot[cb][r], C = rot[cb][c];
+    return R.c * (C.c * Hc[r][c] + C.s * Hc[r][C.partner]) +
+           R.s * (C.c * Hc[R.partner][c] + C.s * Hc[R.partner][C.partner]);
+  };
+  // pair i's angle is taken by thread 32 i (one per warp, spreading the shared-memory
+  // traffic of the angle computations over the schedulers)
+  const bool angler = (tid & 31) == 0 && (tid >> 5) < half;
+  const int ai = tid >> 5;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     T off = T(0), tot = T(0);
-    for (int e = tid; e < bb; e += DS_THREADS) {
-      const int r = e % b, c = e / b;
+    each([&](int, int r, int c) {
       const T v = Hc[r][c];
       tot += v * v;
       if (r != c) off += v * v;
-    }
+    });
     off = warp_sum(off);
     tot = warp_sum(tot);
     if ((tid & 31) == 0) {
@@ -203,50 +263,36 @@ __device__ void ritz_step(T* wk, int b, int max_sweeps, T* __restrict__ theta,
       off += red[0][w];
       tot += red[1][w];
     }
-    __syncthreads();
     if (off <= eps * eps * tot) break;
+    if (angler) {
+      int p, q;
+      pair_of(0, ai, p, q);
+      set_rot(0, p, q, Hc[p][p], Hc[q][q], Hc[p][q]);
+    }
+    __syncthreads();
+    int cb = 0;
     for (int round = 0; round < N - 1; ++round) {
-      if (tid < half) {
-        int p = tid == 0 ? N - 1 : round + tid;
-        if (tid != 0 && p >= N - 1) p -= N - 1;
-        int q = round + N - 1 - tid;
-        if (q >= N - 1) q -= N - 1;
-        if (p > q) { const int t = p; p = q; q = t; }
-        T c = T(1), sn = T(0);
-        if (q < b) {
-          const T apq = Hc[p][q];
-          if (apq != T(0)) {
-            // t = sign(tau) / (|tau| + sqrt(1 + tau^2)), c = 1 / sqrt(1 + t^2), s = t c;
-            // square roots as x rsqrt(x), about 1/(2 tau) once tau^2 would overflow
-            const T tau = (Hc[q][q] - Hc[p][p]) / (T(2) * apq);
-            const T at = fabs(tau), tt = T(1) + tau * tau;
-            const T ta = at > T(1e15) ? T(0.5) * wrcp(at) : wrcp(at + tt * wrsqrt(tt));
-            const T t = tau >= T(0) ? ta : -ta;
-            c = wrsqrt(T(1) + t * t);
-            sn = t * c;
-          }
-        }
-        cx[p] = c;  sg[p] = -sn; partner[p] = q;
-        cx[q] = c;  sg[q] = sn;  partner[q] = p;
-      }
-      __syncthreads();
-      for (int e = tid; e < bb; e += DS_THREADS) {
-        const int r = e % b, c = e / b;
-        const int r2 = partner[r], c2 = partner[c];
-        const T cr = cx[r], sr = sg[r], cc = cx[c], sc = sg[c];
-        const T h00 = Hc[r][c], h01 = Hc[r][c2];
-        const T h10 = Hc[r2][c], h11 = Hc[r2][c2];
-        Hn[r][c] = cr * (cc * h00 + sc * h01) + sr * (cc * h10 + sc * h11);
-        Yn[r][c] = cc * Yc[r][c] + sc * Yc[r][c2];
+      each([&](int, int r, int c) {
+        const Rot R = rot[cb][r], C = rot[cb][c];
+        Hn[r][c] = R.c * (C.c * Hc[r][c] + C.s * Hc[r][C.partner]) +
+                   R.s * (C.c * Hc[R.partner][c] + C.s * Hc[R.partner][C.partner]);
+        Yn[r][c] = C.c * Yc[r][c] + C.s * Yc[r][C.partner];
+      });
+      if (round + 1 < N - 1 && angler) {
+        int p, q;
+        pair_of(round + 1, ai, p, q);
+        if (q < b) set_rot(cb ^ 1, p, q, rotated(cb, p, p), rotated(cb, q, q), rotated(cb, p, q));
+        else set_rot(cb ^ 1, p, q, T(0), T(0), T(0));
       }
       __syncthreads();
       Row* t0 = Hc; Hc = Hn; Hn = t0;
       Row* t1 = Yc; Yc = Yn; Yn = t1;
+      cb ^= 1;
     }
   }
   Row* H = Hc;
   Row* Y = Yc;
-  Row* S = Hn;   // scratch: P Y, then the Cholesky factor
+  Row* S = Hn;   // scratch: P Y, then L^{-1}
   // ---- sort descending: c's rank = #{d : theta_d > theta_c, or equal with d < c}
   if (tid < b) {
     const T tc = H[tid][tid];
@@ -260,25 +306,20 @@ __device__ void ritz_step(T* wk, int b, int max_sweeps, T* __restrict__ theta,
   }
   __syncthreads();
   if (tid < b) th[tid] = H[perm[tid]][perm[tid]];
-  for (int e = tid; e < bb; e += DS_THREADS) {
-    const int r = e % b, c = e / b;
-    Wm[r][c] = Y[r][perm[c]];
-  }
+  each([&](int, int r, int c) { Wm[r][c] = Y[r][perm[c]]; });
   __syncthreads();
   // S = P W, then Pm <- W^T P W
-  for (int e = tid; e < bb; e += DS_THREADS) {
-    const int r = e % b, c = e / b;
+  each([&](int, int r, int c) {
     T v = T(0);
     for (int l = 0; l < b; ++l) v = fma(Pm[r][l], Wm[l][c], v);
     S[r][c] = v;
-  }
+  });
   __syncthreads();
-  for (int e = tid; e < bb; e += DS_THREADS) {
-    const int r = e % b, c = e / b;
+  each([&](int, int r, int c) {
     T v = T(0);
     for (int l = 0; l < b; ++l) v = fma(Wm[l][r], S[l][c], v);
     Pm[r][c] = v;
-  }
+  });
   __syncthreads();
   if (tid < b) {
     const int c = tid;
@@ -287,66 +328,58 @@ __device__ void ritz_step(T* wk, int b, int max_sweeps, T* __restrict__ theta,
     const T nz2 = Pm[c][c];
     const bool use_v = !(th[c] > small * tmax) || !(nz2 > T(0));
     usev[c] = use_v ? 1 : 0;
-    fz[c] = use_v ? T(0) : T(1) / wsqrt(nz2);
+    fz[c] = use_v ? T(0) : wrsqrt(nz2);
     resid[c] = nz2 - th[c] * th[c];
     theta[c] = th[c];
   }
   __syncthreads();
-  // Gram of W: <Vy_a, Vy_b> = delta_ab, <Zy_a, Zy_b> = fz_a fz_b (Y^T P Y)_ab, mixed 0
-  for (int e = tid; e < bb; e += DS_THREADS) {
-    const int r = e % b, c = e / b;
+  // Gram of W: <Vy_a, Vy_b> = delta_ab, <Zy_a, Zy_b> = fz_a fz_b (Y^T P Y)_ab, mixed 0;
+  // S <- I
+  each([&](int, int r, int c) {
     T g;
     if (usev[r] && usev[c]) g = r == c ? T(1) : T(0);
     else if (!usev[r] && !usev[c]) g = fz[r] * fz[c] * Pm[r][c];
     else g = T(0);
     Gm[r][c] = g;
-  }
+    S[r][c] = r == c ? T(1) : T(0);
+  });
   __syncthreads();
-  // W^T W = L D L^T by symmetric elimination (step t: the trailing lower triangle takes
-  // G(i,j) -= G(i,t) G(j,t) / G(t,t)); the Cholesky factor is L D^{1/2}
+  // W^T W = L D L^T by symmetric elimination, with L^{-1} formed alongside (Gauss-Jordan
+  // on [W^T W | I]): step t takes, for rows i > t with m = G(i,t) / G(t,t),
+  // G(i,j) -= m G(j,t) on the trailing lower triangle (j > t) and X(i,j) -= m X(t,j) for
+  // j <= t.  The Cholesky factor is L D^{1/2}, so its inverse is D^{-1/2} L^{-1}.
   for (int t = 0; t < b; ++t) {
     T d = Gm[t][t];
-    if (!(d > T(0)) || !wfinite(d)) d = T(1);
-    const T rd = T(1) / d;
-    for (int e = tid; e < bb; e += DS_THREADS) {
-      const int i = e % b, j = e / b;
-      if (i >= j && j > t) Gm[i][j] = fma(-Gm[i][t] * rd, Gm[j][t], Gm[i][j]);
-    }
-    __syncthreads();
-  }
-  // S = L D^{1/2} (lower), rdg = 1 / S(t,t)
-  for (int e = tid; e < bb; e += DS_THREADS) {
-    const int i = e % b, t = e / b;
-    T d = Gm[t][t];
     if (!(d > T(0)) || !wfinite(d)) {
-      if (i == t) bad_s = 1;
+      if (tid == 0) bad_s = 1;
       d = T(1);
     }
-    const T rl = wrsqrt(d);
-    S[i][t] = i > t ? Gm[i][t] * rl : (i == t ? d * rl : T(0));
-    if (i == t) rdg[t] = rl;
+    const T rd = wrcp(d);
+    each([&](int, int i, int j) {
+      if (i > t) {
+        const T m = Gm[i][t] * rd;
+        if (j > t) {
+          if (j <= i) Gm[i][j] = fma(-m, Gm[j][t], Gm[i][j]);
+        } else {
+          S[i][j] = fma(-m, S[t][j], S[i][j]);
+        }
+      }
+    });
+    __syncthreads();
+  }
+  if (tid < b) {
+    T d = Gm[tid][tid];
+    if (!(d > T(0)) || !wfinite(d)) d = T(1);
+    rdg[tid] = wrsqrt(d);
   }
   __syncthreads();
   if (tid == 0 && bad_s) atomicOr(err, ERRBIT_EIG);
-  // X = S^{-1} (lower) into Gm: rows of the identity, row t final at step t up to 1/S(t,t)
-  for (int e = tid; e < bb; e += DS_THREADS) {
-    const int i = e % b, c = e / b;
-    Gm[i][c] = i == c ? T(1) : T(0);
-  }
-  __syncthreads();
-  for (int t = 0; t < b - 1; ++t) {
-    for (int e = tid; e < bb; e += DS_THREADS) {
-      const int i = e % b, c = e / b;
-      if (i > t && c <= t) Gm[i][c] = fma(-S[i][t] * rdg[t], Gm[t][c], Gm[i][c]);
-    }
-    __syncthreads();
-  }
-  // Mv(r, c) = sum_l W(r, l) [use_v(l)] X(c, l), Mz(r, c) = sum_l W(r, l) fz(l) X(c, l)
-  for (int e = tid; e < bb; e += DS_THREADS) {
-    const int r = e % b, c = e / b;
+  // Mv(r, c) = sum_l W(r, l) [use_v(l)] X(c, l), Mz(r, c) = sum_l W(r, l) fz(l) X(c, l),
+  // X = D^{-1/2} L^{-1}
+  each([&](int e, int r, int c) {
     T mv = T(0), mz = T(0);
     for (int l = 0; l <= c; ++l) {
-      const T x = Gm[c][l] * rdg[c];
+      const T x = S[c][l] * rdg[c];
       const T y = Wm[r][l] * x;
       if (usev[l]) mv += y;
       else mz += y * fz[l];
@@ -354,63 +387,71 @@ __device__ void ritz_step(T* wk, int b, int max_sweeps, T* __restrict__ theta,
     Yo[e] = Wm[r][c];
     Mvo[e] = mv;
     Mzo[e] = mz;
-  }
+  });
   __syncthreads();
 }
 
-// (K V)(l, c) for all rows in double-float.  Block = KV_ROWS rows x 128 threads per row;
-// thread g of a row takes j = g, g + 128, ... (K is symmetric, so row l of K is the
-// contiguous column l) and loads its K and V entries straight from global memory; the 128
-// partial sums of a row are combined by warp shuffles, then across the row's 4 warps in
-// fixed order.
-constexpr int KV_ROWS = 2;
-constexpr int KV_JT = 128;   // threads per row
-constexpr int KV_JMAX = 8;   // j values per thread (n2 <= KV_JT * KV_JMAX = 1024)
-template <typename T, int BC>
-__global__ void __launch_bounds__(KV_ROWS * KV_JT)
+// Sum over the cluster's CTAs, in rank order, of element e of a shared array (the remote
+// loads are issued together; float sums are compensated).
+template <typename T>
+__device__ __forceinline__ T cluster_sum(cgrp::cluster_group& cl, T* base, int e, int nc) {
+  T v[16];
+#pragma unroll
+  for (int u = 0; u < 16; ++u) v[u] = u < nc ? cl.map_shared_rank(base, u)[e] : T(0);
+  WideAcc<T> acc;
+#pragma unroll
+  for (int u = 0; u < 16; ++u)
+    if (u < nc) acc.add(v[u]);
+  return (T)acc.value();
+}
+
+// (K V)(l, c) for all rows in double-float: one warp per (row l, group of KV_CG columns),
+// the lanes splitting the sum over j (K is symmetric, so row l of K is the contiguous
+// column l).  Each lane loads the K and V entries of KV_JM values of j before using them
+// (one memory round trip per chunk), then the partial sums meet by warp shuffles.
+constexpr int KV_CG = 4;
+constexpr int KV_JM = 8;
+template <typename T>
+__global__ void __launch_bounds__(256)
 kv_pair(const T* __restrict__ Kh, const T* __restrict__ Kl, const T* __restrict__ V, int n2, int b,
         T* __restrict__ ZKh, T* __restrict__ ZKl) {
-  __shared__ T red[KV_ROWS][KV_JT / 32][2][BC];
-  const int g = threadIdx.x % KV_JT, u = threadIdx.x / KV_JT;
-  const int lane = threadIdx.x & 31, wr = g >> 5;
-  const int l = blockIdx.x * KV_ROWS + u;
-  const bool live = l < n2;
-  DfAcc<T> acc[BC];
+  const int lane = threadIdx.x & 31;
+  const int ncg = (b + KV_CG - 1) / KV_CG;
+  const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int l = w / ncg, c0 = (w % ncg) * KV_CG;
+  if (l >= n2) return;   // whole warp
+  DfAcc<T> acc[KV_CG];
+  for (int j0 = 0; j0 < n2; j0 += 32 * KV_JM) {
+    T kh[KV_JM], kl[KV_JM], vv[KV_JM][KV_CG];
 #pragma unroll
-  for (int q = 0; q < KV_JMAX; ++q) {
-    const int j = g + KV_JT * q;
-    if (j < n2 && live) {
+    for (int q = 0; q < KV_JM; ++q) {
+      const int j = j0 + lane + 32 * q;
+      const bool ok = j < n2;
       const int64_t o = j + (int64_t)l * n2;
-      const T kh = Kh[o];
-      const T kl = Kl ? Kl[o] : T(0);
+      kh[q] = ok ? Kh[o] : T(0);
+      kl[q] = (ok && Kl) ? Kl[o] : T(0);
 #pragma unroll
-      for (int c = 0; c < BC; ++c)
-        if (c < b) acc[c].add(kh, kl, V[j + (int64_t)c * n2]);
+      for (int u = 0; u < KV_CG; ++u)
+        vv[q][u] = (ok && c0 + u < b) ? V[j + (int64_t)(c0 + u) * n2] : T(0);
     }
+#pragma unroll
+    for (int q = 0; q < KV_JM; ++q)
+#pragma unroll
+      for (int u = 0; u < KV_CG; ++u) acc[u].add(kh[q], kl[q], vv[q][u]);
   }
 #pragma unroll
-  for (int c = 0; c < BC; ++c) {
-    if (c < b) {
-      acc[c].warp_reduce();
-      if (lane == 0) {
-        red[u][wr][0][c] = acc[c].hi;
-        red[u][wr][1][c] = acc[c].lo;
-      }
+  for (int u = 0; u < KV_CG; ++u) {
+    acc[u].warp_reduce();
+    if (lane == 0 && c0 + u < b) {
+      ZKh[l + (int64_t)(c0 + u) * n2] = acc[u].hi;
+      if (ZKl) ZKl[l + (int64_t)(c0 + u) * n2] = acc[u].lo;
     }
-  }
-  __syncthreads();
-  if (g < b && live) {
-    DfAcc<T> s;
-#pragma unroll
-    for (int w = 0; w < KV_JT / 32; ++w) s.add_pair(red[u][w][0][g], red[u][w][1][g]);
-    ZKh[l + (int64_t)g * n2] = s.hi;
-    if (ZKl) ZKl[l + (int64_t)g * n2] = s.lo;
   }
 }
 
 // The cluster kernel (grid = one cluster of NC CTAs, DS_THREADS threads each).
 template <typename T>
-__global__ void __launch_bounds__(DS_THREADS)
+__global__ void __launch_bounds__(DS_THREADS, 1)
 dstep_cluster(DstepArgs<T> a) {
   extern __shared__ unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
@@ -519,16 +560,11 @@ dstep_cluster(DstepArgs<T> a) {
   cluster.sync();
   // ---- Rayleigh-Ritz on CTA 0
   if (rank == 0) {
-    for (int e = tid; e < b * b; e += DS_THREADS) {
-      T h = T(0), p = T(0);
-      for (int r = 0; r < nc; ++r) {
-        const T* rp = cluster.map_shared_rank(HPp, r);
-        h += rp[e];
-        p += rp[b * b + e];
-      }
-      const int r_ = e % b, c_ = e / b;
-      Wk[r_ * DS_P + c_] = h;                       // H into work array 0
-      Wk[4 * DS_BM * DS_P + r_ * DS_P + c_] = p;    // P into work array 4
+    for (int e = tid; e < 2 * b * b; e += DS_THREADS) {
+      const T v = cluster_sum(cluster, HPp, e, nc);
+      const int f = e % (b * b), r_ = f % b, c_ = f / b;
+      // H into work array 0, P into work array 4
+      Wk[(e < b * b ? 0 : 4 * DS_BM * DS_P) + r_ * DS_P + c_] = v;
     }
     __syncthreads();
     ritz_step<T>(Wk, b, a.sweeps, a.theta, a.resid, a.err);
@@ -573,19 +609,12 @@ dstep_cluster(DstepArgs<T> a) {
     CVp[e] = v;
   }
   cluster.sync();
-  if (rank == 0) {
-    for (int e = tid; e < k * k; e += DS_THREADS) {
-      double v = 0.0;
-      for (int r = 0; r < nc; ++r) v += (double)cluster.map_shared_rank(Gp, r)[e];
-      a.G[e] = (T)v;
-    }
-    for (int e = tid; e < k * s; e += DS_THREADS) {
-      double v = 0.0;
-      for (int r = 0; r < nc; ++r) v += (double)cluster.map_shared_rank(CVp, r)[e];
-      a.CV[e] = (T)v;
-    }
+  // outputs e = rank, rank + nc, ... of G (then of C V_s) summed by this CTA
+  for (int e = rank + nc * tid; e < k * k + k * s; e += nc * DS_THREADS) {
+    if (e < k * k) a.G[e] = cluster_sum(cluster, Gp, e, nc);
+    else a.CV[e - k * k] = cluster_sum(cluster, CVp, e - k * k, nc);
   }
-  // every CTA keeps its shared memory until CTA 0 has read it
+  // every CTA keeps its shared memory until the others have read it
   cluster.sync();
 }
 

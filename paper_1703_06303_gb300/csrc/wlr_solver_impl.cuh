@@ -758,7 +758,6 @@ class Solver final : public SolverBase {
   void setup_dstep() {
     const int n2 = d_.n2, k = d_.k, b = d_.b, s = d_.s;
     if (s <= 0 || n2 <= 0 || b > DS_BM) return;
-    if (n2 > KV_JT * KV_JMAX) return;
     const void* fn = (const void*)dstep_cluster<T>;
     for (int nc : {16, 8}) {
       if (n2 < nc) continue;
@@ -850,10 +849,8 @@ class Solver final : public SolverBase {
     for (int t = 0; t < q; ++t) {
       {
         Prof pf(this, "kv_pair");
-        if (b <= 16)
-          kv_pair<T, 16><<<cdiv(n2, KV_ROWS), KV_ROWS * KV_JT, 0, stream_>>>(Kh, Kl, V_, n2, b, ZKh_, ZKl_);
-        else
-          kv_pair<T, 32><<<cdiv(n2, KV_ROWS), KV_ROWS * KV_JT, 0, stream_>>>(Kh, Kl, V_, n2, b, ZKh_, ZKl_);
+        const int64_t warps = (int64_t)n2 * cdiv(b, KV_CG);
+        kv_pair<T><<<cdiv(warps, 8), 256, 0, stream_>>>(Kh, Kl, V_, n2, b, ZKh_, ZKl_);
       }
       {
         Prof pf(this, "dstep");
