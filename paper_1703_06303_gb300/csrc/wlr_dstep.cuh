@@ -31,6 +31,17 @@ constexpr int DS_THREADS = 512;
 constexpr int DS_BM = EIG_BMAX;   // largest b
 constexpr int DS_P = DS_BM + 1;   // row pitch of the b x b work arrays
 
+// Reciprocal and square root for the short serial chains of the small factorizations:
+// hardware estimate plus one Newton step (float; within a few ulp, about a third of the
+// latency of the correctly rounded operations), exact operations for double.
+__device__ __forceinline__ float qrcp(float x) {
+  const float r = __fdividef(1.0f, x);
+  return fmaf(r, fmaf(-x, r, 1.0f), r);
+}
+__device__ __forceinline__ double qrcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ float qsqrt(float x) { return x > 0.f ? x * wrsqrt(x) : 0.f; }
+__device__ __forceinline__ double qsqrt(double x) { return sqrt(x); }
+
 // Sum of products in double-float (float) or plain double: hi + lo.
 template <typename T>
 struct DfAcc;
@@ -97,15 +108,34 @@ struct DstepArgs {
   int* err;
   int n2, k, b, s, NP;
   int sweeps;    // Jacobi sweeps of the Rayleigh-Ritz step
+  // Steps a1 (second CholeskyQR factor) and a2 first, when `front` is set (k <= 32): the
+  // cluster sums the chunk partials of Q1^T [Q1 A2] itself, CTA 0 factors
+  // Q1^T Q1 = (I + Lambda)(I + Lambda)^T, and every CTA forms B and C for its columns.
+  int front;
+  const double* S2T;   // Q1^T [Q1 A2] summed over the Gram chunks: k x (k + n2) column-major
+  const T* F2;         // S2 - I (k x k, column-major) = leading block of S2T minus I
+  const T* R1inv;      // inverse of the first factor (upper k x k)
+  T* Nout;             // N = (I + Lambda)^{-1} - I (lower k x k)
+  T* Rinv;             // R^{-1} = R1inv (I + N)^T (upper k x k); may be R1inv itself
+  T* Cout;             // C = R^{-1} B (k x n2)
+  double* B64;         // B (k x n2), FP64 path
+  float* Bho;          // B = Bho + Blo, float path
+  float* Blo;
+  double* bpart;       // ||B||^2 over each CTA's columns (nc entries)
 };
 
 // Element offsets of the dynamic shared memory (every CTA has the same layout; the b x b
 // work arrays are used by CTA 0 only).
 struct DsLayout {
-  size_t Vt, Bs, Cs, Zh, Zl, Zr, Vsr, BVp, BV, HPp, Gp, CVp, Ml, Wk, total;
-  __host__ __device__ DsLayout(int n2, int k, int b, int s, int R) {
+  size_t Tq, Vt, Bs, Cs, Zh, Zl, Zr, Vsr, BVp, BV, HPp, Gp, CVp, Ml, Tt, NR, Wk, total;
+  template <typename T>
+  __host__ __device__ static DsLayout make(int n2, int k, int b, int s, int R) {
+    return DsLayout(n2, k, b, s, R, (int)(sizeof(double) / sizeof(T)));
+  }
+  __host__ __device__ DsLayout(int n2, int k, int b, int s, int R, int dw) {
     const size_t ss = s > 0 ? s : 1;
     size_t o = 0;
+    Tq = o;  o += (size_t)dw * k * R;       // (Q1^T A2)(:, rows) in double (front stage)
     Vt = o;  o += (size_t)b * n2;           // basis, V(j, c) at Vt[c*n2 + j]
     Bs = o;  o += 2 * (size_t)k * R;        // B(:, rows): high, low
     Cs = o;  o += (size_t)R * k;            // C(:, rows), C(x, j) at Cs[(j - l0)*k + x]
@@ -119,7 +149,9 @@ struct DsLayout {
     Gp = o;  o += (size_t)k * k;            // partial C C^T
     CVp = o; o += (size_t)k * ss;           // partial C V_s
     Ml = o;  o += 3 * (size_t)b * b;        // local copies of Y, Mv, Mz
-    Wk = o;  o += 10 * (size_t)DS_BM * DS_P;    // Rayleigh-Ritz work arrays
+    Tt = o;  o += (size_t)k * R;            // (Q1^T A2)(:, rows) rounded to T
+    NR = o;  o += 2 * (size_t)k * k;        // local copies of N and R^{-1}
+    Wk = o;  o += 10 * (size_t)DS_BM * DS_P;    // Rayleigh-Ritz / second-factor work arrays
     total = o;
   }
 };
@@ -222,9 +254,12 @@ __device__ void ritz_step(T* wk, int b, int max_sweeps, T* __restrict__ theta,
     T c = T(1), sn = T(0);
     if (q < b && apq != T(0)) {
       const T dq = aqq - app;
-      const T tau = dq == T(0) ? T(0) : dq * wrcp(T(2) * apq);
+      const T a2 = T(2) * apq;
+      const T tau = dq == T(0) ? T(0) : (fabs(a2) < T(1e-30) ? dq / a2 : dq * qrcp(a2));
       const T at = fabs(tau), tt = T(1) + tau * tau;
-      const T ta = at > T(1e15) ? T(0.5) * wrcp(at) : wrcp(at + tt * wrsqrt(tt));
+      T ta;
+      if (at > T(1e15)) ta = at < T(1e30) ? T(0.5) * qrcp(at) : T(0);
+      else ta = qrcp(at + tt * wrsqrt(tt));
       const T t = tau >= T(0) ? ta : -ta;
       c = wrsqrt(T(1) + t * t);
       sn = t * c;
@@ -354,7 +389,7 @@ __device__ void ritz_step(T* wk, int b, int max_sweeps, T* __restrict__ theta,
       if (tid == 0) bad_s = 1;
       d = T(1);
     }
-    const T rd = wrcp(d);
+    const T rd = qrcp(d);
     each([&](int, int i, int j) {
       if (i > t) {
         const T m = Gm[i][t] * rd;
@@ -389,6 +424,93 @@ __device__ void ritz_step(T* wk, int b, int max_sweeps, T* __restrict__ theta,
     Mzo[e] = mz;
   });
   __syncthreads();
+}
+
+// Second CholeskyQR factor on one CTA (k <= 32), the difference form of chol2_warp with
+// the steps spread over the CTA: Q1^T Q1 = I + F = (I + Lambda)(I + Lambda)^T by
+// right-looking elimination (step t: Lambda_tt = F_tt / (1 + sqrt(1 + F_tt)), and the
+// trailing lower triangle takes F_ij -= F_it F_jt / (1 + Lambda_tt)^2, so that
+// Lambda_it = F_it / (1 + Lambda_tt) uses column t as it stands after step t - 1); then
+// (I + Lambda) N = -Lambda by forward elimination over the rows, and
+// R^{-1} = R1inv (I + N)^T.  F arrives as F(i, j) = get(i + j k) (lower part used).
+// Work arrays in wk: F, R1inv, N (row-major, pitch k), R^{-1} (row-major).
+template <typename T, typename Get>
+__device__ void chol2_block(T* wk, int k, Get get, const T* __restrict__ R1inv,
+                            T* __restrict__ Nout, T* __restrict__ Rinv, int* __restrict__ err) {
+  T* F = wk;
+  T* Rm = wk + DS_BM * DS_BM;
+  T* Nm = wk + 2 * DS_BM * DS_BM;
+  T* Ri = wk + 3 * DS_BM * DS_BM;
+  __shared__ T lam_s[DS_BM], rdg_s[DS_BM];
+  __shared__ int flag_s;
+  const int tid = threadIdx.x;
+  const int kk = k * k;
+  // this thread's element (i, j) = (tid / k, tid % k) of a k x k array (k <= 32, so at
+  // most two per thread: tid and tid + DS_THREADS)
+  constexpr int NE = (DS_BM * DS_BM + DS_THREADS - 1) / DS_THREADS;
+  int ei[NE], ej[NE];
+#pragma unroll
+  for (int q = 0; q < NE; ++q) {
+    const int e = tid + q * DS_THREADS;
+    ei[q] = e / k;
+    ej[q] = e % k;
+  }
+  auto each = [&](auto&& f) {
+#pragma unroll
+    for (int q = 0; q < NE; ++q)
+      if (tid + q * DS_THREADS < kk) f(ei[q], ej[q]);
+  };
+  each([&](int i, int j) {
+    F[i * k + j] = get(i + j * k);
+    Rm[i * k + j] = R1inv[i + j * k];
+  });
+  if (tid == 0) flag_s = 0;
+  __syncthreads();
+  for (int t = 0; t < k; ++t) {
+    const T ftt = F[t * k + t];
+    T lam = T(0);
+    const bool bad = !(T(1) + ftt > T(0)) || !wfinite(ftt);
+    if (!bad) lam = ftt * qrcp(T(1) + qsqrt(T(1) + ftt));
+    const T rden = qrcp(T(1) + lam);
+    if (tid == 0) {
+      lam_s[t] = lam;
+      rdg_s[t] = rden;
+      if (bad) flag_s = 1;
+    }
+    const T r2 = rden * rden;
+    each([&](int i, int j) {
+      if (i >= j && j > t) F[i * k + j] = fma(-F[i * k + t] * r2, F[j * k + t], F[i * k + j]);
+    });
+    __syncthreads();
+  }
+  // right-hand sides -Lambda (lower, with the diagonal)
+  each([&](int i, int c) { Nm[i * k + c] = c < i ? -F[i * k + c] * rdg_s[c] : (c == i ? -lam_s[i] : T(0)); });
+  __syncthreads();
+  // row l is final at step l up to the factor 1 / (1 + Lambda_ll)
+  for (int l = 0; l < k - 1; ++l) {
+    const T rl = rdg_s[l];
+    each([&](int i, int c) {
+      if (i > l && c <= l) Nm[i * k + c] = fma(-F[i * k + l] * rl * rl, Nm[l * k + c], Nm[i * k + c]);
+    });
+    __syncthreads();
+  }
+  each([&](int i, int c) {
+    const T v = Nm[i * k + c] * rdg_s[i];
+    Nm[i * k + c] = v;
+    Nout[i + c * k] = v;
+  });
+  __syncthreads();
+  each([&](int a, int b) {
+    T v = T(0);
+    if (a <= b) {
+      v = Rm[a * k + b];
+      for (int l = a; l <= b; ++l) v = fma(Rm[a * k + l], Nm[b * k + l], v);
+    }
+    Ri[a * k + b] = v;
+    Rinv[a + b * k] = v;
+  });
+  __syncthreads();
+  if (tid == 0 && flag_s) atomicOr(err, ERRBIT_RANK_DEFICIENT);
 }
 
 // Sum over the cluster's CTAs, in rank order, of element e of a shared array (the remote
@@ -462,7 +584,7 @@ dstep_cluster(DstepArgs<T> a) {
   const int n2 = a.n2, k = a.k, b = a.b, s = a.s, NP = a.NP;
   const int R = (n2 + nc - 1) / nc;
   const int l0 = min(n2, rank * R), l1 = min(n2, l0 + R), nr = l1 - l0;
-  const DsLayout L(n2, k, b, s, R);
+  const DsLayout L = DsLayout::make<T>(n2, k, b, s, R);
   T* Vt = sm + L.Vt;
   T* Bs = sm + L.Bs;
   T* Cs = sm + L.Cs;
@@ -480,13 +602,16 @@ dstep_cluster(DstepArgs<T> a) {
   const int kb = k * b;
 
   // ---- inputs into shared memory (asynchronous copies, one group): the whole basis,
-  // and for the CTA's rows: B's columns, C (from Z2), K V
+  // and for the CTA's rows: K V, and (unless the front stage makes them) B's columns and
+  // C (from Z2)
   for (int e = tid; e < b * n2; e += DS_THREADS) cp_async_elem(Vt + e, a.V + e, true);
-  for (int e = tid; e < k * nr; e += DS_THREADS) {
-    cp_async_elem(Bs + e, a.Bh + (int64_t)l0 * k + e, true);
-    if (a.Bl) cp_async_elem(Bs + k * R + e, a.Bl + (int64_t)l0 * k + e, true);
-    const int rr = e / k, x = e % k;
-    cp_async_elem(Cs + e, a.Z2 + (int64_t)(l0 + rr) * NP + x, true);
+  if (!a.front) {
+    for (int e = tid; e < k * nr; e += DS_THREADS) {
+      cp_async_elem(Bs + e, a.Bh + (int64_t)l0 * k + e, true);
+      if (a.Bl) cp_async_elem(Bs + k * R + e, a.Bl + (int64_t)l0 * k + e, true);
+      const int rr = e / k, x = e % k;
+      cp_async_elem(Cs + e, a.Z2 + (int64_t)(l0 + rr) * NP + x, true);
+    }
   }
   for (int e = tid; e < b * nr; e += DS_THREADS) {
     const int c = e / nr, rr = e % nr;
@@ -494,6 +619,66 @@ dstep_cluster(DstepArgs<T> a) {
     if (a.ZKl) cp_async_elem(Zl + c * R + rr, a.ZKl + l0 + rr + (int64_t)c * n2, true);
   }
   cp_async_commit();
+
+  if (a.front) {
+    double* Tq = reinterpret_cast<double*>(sm + L.Tq);
+    T* Tt = sm + L.Tt;
+    T* Nl = sm + L.NR;
+    T* Rl = Nl + k * k;
+    // ---- a1/a2 (1): t = Q1^T A2 for this CTA's columns (column k + j of the sums)
+    for (int v = tid; v < k * nr; v += DS_THREADS) {
+      const double sum = __ldcg(&a.S2T[(int64_t)(k + l0) * k + v]);
+      Tq[v] = sum;
+      Tt[v] = (T)sum;
+    }
+    // ---- (2) the second factor on CTA 0 (from the reduced S2 - I in global memory)
+    if (rank == 0) chol2_block<T>(Wk, k, [&](int e) { return a.F2[e]; }, a.R1inv, a.Nout, a.Rinv, a.err);
+    cluster.sync();
+    // ---- (3) B = (I + N) t and C = R^{-1} B for this CTA's columns
+    {
+      const T* w0 = cluster.map_shared_rank(Wk, 0);
+      for (int e = tid; e < k * k; e += DS_THREADS) {
+        Nl[e] = w0[2 * DS_BM * DS_BM + e];
+        Rl[e] = w0[3 * DS_BM * DS_BM + e];
+      }
+    }
+    __syncthreads();
+    double bn = 0.0;
+    for (int v = tid; v < k * nr; v += DS_THREADS) {
+      const int x = v % k, jj = v / k;
+      T corr = T(0);
+      for (int l = 0; l <= x; ++l) corr = fma(Nl[x * k + l], Tt[jj * k + l], corr);
+      const double bv = Tq[v] + (double)corr;
+      const int64_t o = (int64_t)(l0 + jj) * k + x;
+      if (a.B64) a.B64[o] = bv;
+      if constexpr (sizeof(T) == 4) {
+        const float hi = (float)bv, lo = (float)(bv - (double)hi);
+        a.Bho[o] = hi;
+        a.Blo[o] = lo;
+        Bs[v] = hi;
+        Bs[k * R + v] = lo;
+      } else {
+        Bs[v] = (T)bv;
+      }
+      bn += bv * bv;
+    }
+    __syncthreads();
+    for (int v = tid; v < k * nr; v += DS_THREADS) {
+      const int x = v % k, jj = v / k;
+      T cv = T(0);
+      for (int l = x; l < k; ++l) {
+        const T bl = sizeof(T) == 4 ? Bs[jj * k + l] + Bs[k * R + jj * k + l] : Bs[jj * k + l];
+        cv = fma(Rl[x * k + l], bl, cv);
+      }
+      Cs[v] = cv;
+      const int64_t o = (int64_t)(l0 + jj) * k + x;
+      a.Cout[o] = cv;
+      a.Z2[(int64_t)(l0 + jj) * NP + x] = cv;
+    }
+    __shared__ double bsh[32];
+    bn = block_sum_double(bn, bsh);
+    if (tid == 0) a.bpart[rank] = bn;
+  }
   cp_async_wait<0>();
   __syncthreads();
 

@@ -678,7 +678,9 @@ class Solver final : public SolverBase {
   // previous iteration's R (X1 moves little per iteration, so X1 R_prev^{-1} is already
   // nearly orthonormal and the second factor recovers the exact R = R2 R_prev); else a
   // full CholeskyQR2 from S1 = X1^T X1.
-  void qr_coef(int xi, bool precond = false) {
+  // fused: stop after the summed Gram (the D-step cluster kernel takes the second factor
+  // and B, C); front_rpre_ tells it which first factor to use
+  void qr_coef(int xi, bool precond = false, bool fused = false) {
     const int m = d_.m, k = d_.k, n2 = d_.n2, NP = d_.NP;
     const T* X1 = X1buf_[xi];
     const T* A2 = A_ + (int64_t)k * lda_;
@@ -711,6 +713,10 @@ class Solver final : public SolverBase {
     }
     // Q1^T [Q1 A2] summed over the chunks by all SMs; chol2 and coef read the sum
     reduce64(L, nchT, L, S2T_, k, k <= 32 ? F2_ : nullptr);
+    if (fused) {
+      front_rpre_ = Rpre;
+      return;
+    }
     {
       Prof pf(this, "chol2");
       if (k <= 32)
@@ -761,7 +767,7 @@ class Solver final : public SolverBase {
     const void* fn = (const void*)dstep_cluster<T>;
     for (int nc : {16, 8}) {
       if (n2 < nc) continue;
-      const size_t bytes = sizeof(T) * DsLayout(n2, k, b, s, cdiv(n2, nc)).total;
+      const size_t bytes = sizeof(T) * DsLayout::make<T>(n2, k, b, s, cdiv(n2, nc)).total;
       if (bytes > 200 * 1024) continue;
       if (nc > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
         cudaGetLastError();
@@ -794,6 +800,12 @@ class Solver final : public SolverBase {
       break;
     }
     if (!use_dstep_) return;
+    // the front stage (second factor, B, C inside the cluster) for k <= 32
+    fuse_front_ = k <= 32;
+    if (fuse_front_) {
+      bpart_ = dalloc<double>(std::max(nblk_coef_, ds_nc_));
+      WLR_CUDA(cudaMemsetAsync(bpart_, 0, sizeof(double) * std::max(nblk_coef_, ds_nc_), stream_));
+    }
     ZKh_ = dalloc<T>((size_t)n2 * b);
     if (std::is_same<T, float>::value) {
       Kh_ = dalloc<float>((size_t)n2 * n2);
@@ -803,9 +815,9 @@ class Solver final : public SolverBase {
   }
   // q subspace steps: K V on all SMs, then the cluster kernel (which also leaves
   // G = C C^T and C V_s for the row pass)
-  void dstep_run(int q, bool cold) {
+  void dstep_run(int q, bool cold, bool front = false) {
     const int n2 = d_.n2, b = d_.b;
-    DstepArgs<T> a;
+    DstepArgs<T> a = {};
     const T *Kh, *Kl;
     if constexpr (std::is_same<T, float>::value) {
       Kh = Kh_;
@@ -834,6 +846,22 @@ class Solver final : public SolverBase {
     a.s = d_.s;
     a.NP = d_.NP;
     a.sweeps = cold ? (sizeof(T) == 4 ? 12 : 24) : (sizeof(T) == 4 ? 1 : 6);
+    a.S2T = S2T_;
+    a.F2 = F2_;
+    a.R1inv = front_rpre_;
+    a.Nout = Nm_;
+    a.Rinv = Rinv_;
+    a.Cout = C_;
+    a.bpart = bpart_;
+    if constexpr (std::is_same<T, float>::value) {
+      a.B64 = nullptr;
+      a.Bho = Bh_;
+      a.Blo = Bl_;
+    } else {
+      a.B64 = B64_;
+      a.Bho = nullptr;
+      a.Blo = nullptr;
+    }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(ds_nc_);
     cfg.blockDim = dim3(DS_THREADS);
@@ -852,6 +880,7 @@ class Solver final : public SolverBase {
         const int64_t warps = (int64_t)n2 * cdiv(b, KV_CG);
         kv_pair<T><<<cdiv(warps, 8), 256, 0, stream_>>>(Kh, Kl, V_, n2, b, ZKh_, ZKl_);
       }
+      a.front = front && t == 0 ? 1 : 0;
       {
         Prof pf(this, "dstep");
         WLR_CUDA(cudaLaunchKernelEx(&cfg, dstep_cluster<T>, a));
@@ -873,7 +902,7 @@ class Solver final : public SolverBase {
   }
   // steps a1..a3 (+ the small products for a4/a5) for X1 = X1buf_[xi]
   void compute_cd(int xi, bool warm, bool precond = false) {
-    qr_coef(xi, precond);
+    qr_coef(xi, precond, fuse_front_);
     if (d_.s > 0) {
       int q = warm ? o_.eig_iters : o_.eig_iters_cold;
       bool cold = false;
@@ -884,7 +913,7 @@ class Solver final : public SolverBase {
         cold = true;
       }
       if (use_dstep_) {
-        dstep_run(q, cold);   // also G = C C^T and C V_s
+        dstep_run(q, cold, fuse_front_);   // also G = C C^T and C V_s
       } else {
         form_g2_launch();
         for (int t = 0; t < q; ++t) eig_iteration(cold);
@@ -924,7 +953,7 @@ class Solver final : public SolverBase {
     const int g = nblk_row_;
     {
       Prof pf(this, "row_pass");
-      FinalizeArgs<T> fin{bpart_, n2 > 0 ? nblk_coef_ : 0, normA2_, theta_, Fhist_, hist_cap_, iter_, Fcur_,
+      FinalizeArgs<T> fin{bpart_, n2 > 0 ? (fuse_front_ ? ds_nc_ : nblk_coef_) : 0, normA2_, theta_, Fhist_, hist_cap_, iter_, Fcur_,
                           fin_ticket_};
       row_pass_fn<T>(k)<<<g, 256, smem, stream_>>>(A_, lda_, W1_, ldw_, X1buf_[xi], Z2_, G_, CV_, m, n2, k, s, NP,
                                                   X1buf_[xo], wpart_, err_, fin);
@@ -1017,6 +1046,8 @@ class Solver final : public SolverBase {
   double *part64_ = nullptr, *S2T_ = nullptr;
   T* F2_ = nullptr;   // S2 - I for the second Cholesky factor (k <= 32)
   bool use_dstep_ = false;   // fused cluster kernel for step a3
+  bool fuse_front_ = false;  // ... with the second factor and B, C in front (k <= 32)
+  const T* front_rpre_ = nullptr;
   int ds_nc_ = 0;
   size_t ds_smem_ = 0;
   float *Kh_ = nullptr, *Kl_ = nullptr;   // K as a float pair (float path)
