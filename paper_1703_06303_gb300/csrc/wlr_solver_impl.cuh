@@ -26,6 +26,9 @@ class Solver final : public SolverBase {
  public:
   Solver(const Dims& d, const wlr_options& o, cudaStream_t us) : d_(d), o_(o), ustream_(us) {
     WLR_CUDA(cudaStreamCreateWithFlags(&stream_, cudaStreamNonBlocking));
+    WLR_CUDA(cudaStreamCreateWithFlags(&stream2_, cudaStreamNonBlocking));
+    WLR_CUDA(cudaEventCreateWithFlags(&ev_fork_, cudaEventDisableTiming));
+    WLR_CUDA(cudaEventCreateWithFlags(&ev_join_, cudaEventDisableTiming));
     WLR_CUDA(cudaEventCreateWithFlags(&ev_in_, cudaEventDisableTiming));
     WLR_CUDA(cudaEventCreateWithFlags(&ev_out_, cudaEventDisableTiming));
     WLR_CUDA(cudaHostAlloc((void**)&hbuf_, 4096, cudaHostAllocDefault));
@@ -120,6 +123,9 @@ class Solver final : public SolverBase {
     cudaEventDestroy(ev_in_);
     cudaEventDestroy(ev_out_);
     cudaStreamDestroy(stream_);
+    cudaStreamDestroy(stream2_);
+    cudaEventDestroy(ev_fork_);
+    cudaEventDestroy(ev_join_);
   }
 
   // ------------------------------------------------------------------ ABI methods
@@ -599,13 +605,14 @@ class Solver final : public SolverBase {
     count(1);
   }
   // part64 <- chunk partials of Q1^T [Q1 A2] with Q1 = X1 Rpre (k x (k + n2) per chunk)
-  void tc_gram(const T* X1, const T* Rpre) {
+  void tc_gram(const T* X1, const T* Rpre, bool fork = false) {
     const int m = d_.m, k = d_.k, n2 = d_.n2;
     {
       Prof pf(this, "form_q_split");
       tc::form_q_split<<<grid1d((int64_t)m * k), 256, sizeof(float) * k * k, stream_>>>(
           (const float*)X1, m, (const float*)Rpre, m, k, Q1h_, Q1l_, ld4_);
     }
+    if (fork) fork_kv();
     {
       Prof pf(this, "gram_tf32x3_t");
       dim3 g(1 + cdiv(n2, 128), ch_tc_.nch);
@@ -698,7 +705,7 @@ class Solver final : public SolverBase {
     int nchT = ch_T_.nch;
     if (use_tc_) {
       // tensor cores (tcgen05 + TMA), Q1 = X1 Rpre split into TF32 hi + lo
-      tc_gram(X1, Rpre);
+      tc_gram(X1, Rpre, fused);
       nchT = ch_tc_.nch;
     } else if (std::is_same<T, float>::value) {
       // Q1 = X1 Rpre formed slab by slab inside the Gram kernel
@@ -815,18 +822,39 @@ class Solver final : public SolverBase {
   }
   // q subspace steps: K V on all SMs, then the cluster kernel (which also leaves
   // G = C C^T and C V_s for the row pass)
-  void dstep_run(int q, bool cold, bool front = false) {
+  // K V for the current basis (all SMs)
+  void kv_launch(cudaStream_t st) {
     const int n2 = d_.n2, b = d_.b;
-    DstepArgs<T> a = {};
     const T *Kh, *Kl;
     if constexpr (std::is_same<T, float>::value) {
       Kh = Kh_;
       Kl = Kl_;
-      a.Bh = Bh_;
-      a.Bl = Bl_;
     } else {
       Kh = K64_;
       Kl = nullptr;
+    }
+    const int64_t warps = (int64_t)n2 * cdiv(b, KV_CG);
+    kv_pair<T><<<cdiv(warps, 8), 256, 0, st>>>(Kh, Kl, V_, n2, b, ZKh_, ZKl_);
+    count(1);
+  }
+  // K V of step a3 depends only on the basis V, which nothing changes before the D-step:
+  // start it on the side stream next to the Gram kernel of step a1 (one CTA per SM, which
+  // leaves room beside it); dstep_run waits for it
+  void fork_kv() {
+    if (!use_dstep_ || eig_cold_ || prof_ || kv_pending_) return;
+    WLR_CUDA(cudaEventRecord(ev_fork_, stream_));
+    WLR_CUDA(cudaStreamWaitEvent(stream2_, ev_fork_, 0));
+    kv_launch(stream2_);
+    WLR_CUDA(cudaEventRecord(ev_join_, stream2_));
+    kv_pending_ = true;
+  }
+  void dstep_run(int q, bool cold, bool front = false) {
+    const int n2 = d_.n2, b = d_.b;
+    DstepArgs<T> a = {};
+    if constexpr (std::is_same<T, float>::value) {
+      a.Bh = Bh_;
+      a.Bl = Bl_;
+    } else {
       a.Bh = B64_;
       a.Bl = nullptr;
     }
@@ -875,17 +903,20 @@ class Solver final : public SolverBase {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     for (int t = 0; t < q; ++t) {
-      {
+      if (t == 0 && kv_pending_) {
+        // K V was started on the side stream when the iteration began (V has not changed)
+        WLR_CUDA(cudaStreamWaitEvent(stream_, ev_join_, 0));
+        kv_pending_ = false;
+      } else {
         Prof pf(this, "kv_pair");
-        const int64_t warps = (int64_t)n2 * cdiv(b, KV_CG);
-        kv_pair<T><<<cdiv(warps, 8), 256, 0, stream_>>>(Kh, Kl, V_, n2, b, ZKh_, ZKl_);
+        kv_launch(stream_);
       }
       a.front = front && t == 0 ? 1 : 0;
       {
         Prof pf(this, "dstep");
         WLR_CUDA(cudaLaunchKernelEx(&cfg, dstep_cluster<T>, a));
       }
-      count(2);
+      count(1);
     }
   }
   void eig_start() {
@@ -951,6 +982,7 @@ class Solver final : public SolverBase {
     const int m = d_.m, k = d_.k, n2 = d_.n2, s = d_.s, NP = d_.NP;
     const size_t smem = RowPassSmem<T>::bytes(NP, k, s);
     const int g = nblk_row_;
+
     {
       Prof pf(this, "row_pass");
       FinalizeArgs<T> fin{bpart_, n2 > 0 ? (fuse_front_ ? ds_nc_ : nblk_coef_) : 0, normA2_, theta_, Fhist_, hist_cap_, iter_, Fcur_,
@@ -1046,6 +1078,9 @@ class Solver final : public SolverBase {
   double *part64_ = nullptr, *S2T_ = nullptr;
   T* F2_ = nullptr;   // S2 - I for the second Cholesky factor (k <= 32)
   bool use_dstep_ = false;   // fused cluster kernel for step a3
+  cudaStream_t stream2_ = nullptr;   // side stream for K V
+  cudaEvent_t ev_fork_ = nullptr, ev_join_ = nullptr;
+  bool kv_pending_ = false;
   bool fuse_front_ = false;  // ... with the second factor and B, C in front (k <= 32)
   const T* front_rpre_ = nullptr;
   int ds_nc_ = 0;
