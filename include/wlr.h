@@ -160,6 +160,24 @@ wlr_status wlr_get_history(wlr_handle h, double* F, double* rel_err, int32_t cap
 /* Iterations performed since wlr_set_init. */
 wlr_status wlr_get_iteration(wlr_handle h, int32_t* p_out);
 
+/* Checkpoint of the iteration, into host memory: the current X1_p, the factors of the
+ * last (C, D) step that the next loop body of Algorithm 1 reads (C, Z2 = [C^T | V_s],
+ * C C^T, C V_s, the Ritz values), the subspace basis and the R^{-1} that this build
+ * carries from one iteration to the next, the iteration count and the history.  A handle
+ * restored from it continues the same iteration bit for bit.  The paper has no
+ * counterpart (its loop state is X1_p and p); the layout is private to this library and
+ * versioned.  With buf == NULL only *size_out (bytes) is set; otherwise cap must be at
+ * least that size (else WLR_ERR_INVALID_ARG).  WLR_ERR_NOT_READY before wlr_set_init.
+ * Synchronises. */
+wlr_status wlr_get_state(wlr_handle h, void* buf, int64_t cap, int64_t* size_out);
+
+/* Restore a checkpoint made by wlr_get_state.  The handle must have the same m, n, k, r,
+ * options and precision and must already hold the same data (wlr_set_data; the data is
+ * not part of the state).  WLR_ERR_INVALID_ARG for a foreign, truncated or mismatched
+ * buffer; WLR_ERR_NOT_READY before wlr_set_data.  Replaces any wlr_set_init.
+ * Synchronises. */
+wlr_status wlr_set_state(wlr_handle h, const void* buf, int64_t size);
+
 /* Release the handle and all its device memory.  NULL is accepted. */
 wlr_status wlr_destroy(wlr_handle h);
 

@@ -180,6 +180,24 @@ wlr_status wlr_get_iteration(wlr_handle h, int32_t* p_out) {
   });
 }
 
+wlr_status wlr_get_state(wlr_handle h, void* buf, int64_t cap, int64_t* size_out) {
+  return guarded(h, [&] {
+    const int64_t need = h->impl->state_bytes();
+    if (size_out) *size_out = need;
+    if (!buf) return WLR_OK;
+    if (cap < need) throw wlr::Fail{WLR_ERR_INVALID_ARG, "cap is smaller than the state size"};
+    h->impl->get_state(buf);
+    return WLR_OK;
+  });
+}
+
+wlr_status wlr_set_state(wlr_handle h, const void* buf, int64_t size) {
+  return guarded(h, [&] {
+    h->impl->set_state(buf, size);
+    return WLR_OK;
+  });
+}
+
 wlr_status wlr_destroy(wlr_handle h) {
   if (!h) return WLR_OK;
   delete h->impl;

@@ -55,6 +55,9 @@ class SolverBase {
   virtual int get_history(double* F, double* rel_err, int cap) = 0;
   virtual int iteration() = 0;
   virtual int64_t launches() const = 0;
+  virtual int64_t state_bytes() = 0;
+  virtual void get_state(void* buf) = 0;
+  virtual void set_state(const void* buf, int64_t size) = 0;
   virtual std::vector<ProfEntry> profile(int reps) = 0;
 };
 

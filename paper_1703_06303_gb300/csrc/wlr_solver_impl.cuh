@@ -334,6 +334,137 @@ class Solver final : public SolverBase {
 
   int64_t launches() const override { return launches_; }
 
+  // ---- checkpoint: everything the next iteration reads (Algorithm 1's loop state plus
+  // the build's carried state), so that a restored handle continues bit for bit
+  struct StateHeader {
+    char magic[4];     // "WLRS"
+    int32_t version;   // 1
+    int32_t tbytes;    // sizeof(T)
+    int32_t m, n, k, r, b, NP, nbpart;
+    int32_t iters_host, p_device, eig_cold, cd_valid, n_rel;
+  };
+  struct StateArrays {
+    size_t x1, z2, g, cv, theta, resid, c, rinv, v, vs, bpart, fhist, rel;
+  };
+  StateArrays state_counts(int p_device, int n_rel) const {
+    const int m = d_.m, k = d_.k, n2 = d_.n2, s = d_.s, b = std::max(d_.b, 1), NP = d_.NP;
+    StateArrays c;
+    c.x1 = (size_t)m * k;
+    c.z2 = (size_t)std::max(n2, 1) * NP;
+    c.g = (size_t)k * k;
+    c.cv = (size_t)k * std::max(s, 1);
+    c.theta = b;
+    c.resid = b;
+    c.c = (size_t)k * std::max(n2, 1);
+    c.rinv = (size_t)k * k;
+    c.v = (size_t)std::max(n2, 1) * b;
+    c.vs = (size_t)std::max(n2, 1) * std::max(s, 1);
+    c.bpart = nbpart();
+    c.fhist = std::min(p_device, hist_cap_);
+    c.rel = n_rel;
+    return c;
+  }
+  int nbpart() const { return std::max(fuse_front_ ? ds_nc_ : nblk_coef_, 1); }
+  static size_t state_size(const StateArrays& c) {
+    return sizeof(StateHeader) +
+           sizeof(T) * (c.x1 + c.z2 + c.g + c.cv + c.theta + c.resid + c.c + c.rinv + c.v + c.vs) +
+           sizeof(double) * (c.bpart + c.fhist + c.rel);
+  }
+  int64_t state_bytes() override {
+    need_init();
+    WLR_CUDA(cudaStreamSynchronize(stream_));
+    int p = 0;
+    WLR_CUDA(cudaMemcpy(&p, iter_, sizeof(int), cudaMemcpyDeviceToHost));
+    return (int64_t)state_size(state_counts(p, (int)rel_err_hist_.size()));
+  }
+  void get_state(void* buf) override {
+    need_init();
+    WLR_CUDA(cudaStreamSynchronize(stream_));
+    int p = 0;
+    WLR_CUDA(cudaMemcpy(&p, iter_, sizeof(int), cudaMemcpyDeviceToHost));
+    const StateArrays c = state_counts(p, (int)rel_err_hist_.size());
+    StateHeader h;
+    std::memcpy(h.magic, "WLRS", 4);
+    h.version = 1;
+    h.tbytes = (int32_t)sizeof(T);
+    h.m = d_.m; h.n = d_.n; h.k = d_.k; h.r = d_.r; h.b = d_.b; h.NP = d_.NP;
+    h.nbpart = (int32_t)c.bpart;
+    h.iters_host = iters_host_;
+    h.p_device = p;
+    h.eig_cold = eig_cold_ ? 1 : 0;
+    h.cd_valid = cd_valid_ ? 1 : 0;
+    h.n_rel = (int32_t)c.rel;
+    unsigned char* o = (unsigned char*)buf;
+    std::memcpy(o, &h, sizeof(h));
+    o += sizeof(h);
+    auto dl = [&](const void* src, size_t bytes) {
+      if (bytes) WLR_CUDA(cudaMemcpy(o, src, bytes, cudaMemcpyDeviceToHost));
+      o += bytes;
+    };
+    dl(X1buf_[cur_], sizeof(T) * c.x1);
+    dl(Z2_, sizeof(T) * c.z2);
+    dl(G_, sizeof(T) * c.g);
+    dl(CV_, sizeof(T) * c.cv);
+    dl(theta_, sizeof(T) * c.theta);
+    dl(resid_, sizeof(T) * c.resid);
+    dl(C_, sizeof(T) * c.c);
+    dl(Rinv_, sizeof(T) * c.rinv);
+    dl(V_, sizeof(T) * c.v);
+    dl(Vs_, sizeof(T) * c.vs);
+    dl(bpart_, sizeof(double) * c.bpart);
+    dl(Fhist_, sizeof(double) * c.fhist);
+    if (c.rel) std::memcpy(o, rel_err_hist_.data(), sizeof(double) * c.rel);
+  }
+  void set_state(const void* buf, int64_t size) override {
+    need_data();
+    StateHeader h;
+    if (!buf || size < (int64_t)sizeof(h)) throw Fail{WLR_ERR_INVALID_ARG, "state buffer too small"};
+    std::memcpy(&h, buf, sizeof(h));
+    if (std::memcmp(h.magic, "WLRS", 4) != 0 || h.version != 1)
+      throw Fail{WLR_ERR_INVALID_ARG, "not a state buffer of this library (magic/version)"};
+    if (h.tbytes != (int32_t)sizeof(T) || h.m != d_.m || h.n != d_.n || h.k != d_.k || h.r != d_.r ||
+        h.b != d_.b || h.NP != d_.NP || h.nbpart != nbpart())
+      throw Fail{WLR_ERR_INVALID_ARG, "state was saved by a handle with other sizes or precision"};
+    if (h.p_device < 0 || h.n_rel < 0 || h.iters_host < 0)
+      throw Fail{WLR_ERR_INVALID_ARG, "corrupt state header"};
+    const StateArrays c = state_counts(h.p_device, h.n_rel);
+    if (size < (int64_t)state_size(c)) throw Fail{WLR_ERR_INVALID_ARG, "state buffer truncated"};
+    begin();
+    const unsigned char* o = (const unsigned char*)buf + sizeof(h);
+    auto ul = [&](void* dst, size_t bytes) {
+      if (bytes) WLR_CUDA(cudaMemcpy(dst, o, bytes, cudaMemcpyHostToDevice));
+      o += bytes;
+    };
+    ul(X1buf_[0], sizeof(T) * c.x1);
+    ul(Z2_, sizeof(T) * c.z2);
+    ul(G_, sizeof(T) * c.g);
+    ul(CV_, sizeof(T) * c.cv);
+    ul(theta_, sizeof(T) * c.theta);
+    ul(resid_, sizeof(T) * c.resid);
+    ul(C_, sizeof(T) * c.c);
+    ul(Rinv_, sizeof(T) * c.rinv);
+    ul(V_, sizeof(T) * c.v);
+    ul(Vs_, sizeof(T) * c.vs);
+    ul(bpart_, sizeof(double) * c.bpart);
+    ul(Fhist_, sizeof(double) * c.fhist);
+    rel_err_hist_.assign((const double*)o, (const double*)o + c.rel);
+    WLR_CUDA(cudaMemcpy(iter_, &h.p_device, sizeof(int), cudaMemcpyHostToDevice));
+    if (c.fhist > 0) {
+      double Fl = 0.0;
+      WLR_CUDA(cudaMemcpy(&Fl, Fhist_ + (c.fhist - 1), sizeof(double), cudaMemcpyDeviceToHost));
+      WLR_CUDA(cudaMemcpy(Fcur_, &Fl, sizeof(double), cudaMemcpyHostToDevice));
+    }
+    WLR_CUDA(cudaMemsetAsync(err_, 0, sizeof(int), stream_));
+    cur_ = 0;
+    prev_ = -1;
+    iters_host_ = h.iters_host;
+    eig_cold_ = h.eig_cold != 0;
+    cd_valid_ = h.cd_valid != 0;
+    graphs_clear();
+    have_init_ = true;
+    end();
+  }
+
   // Run reps iterations without graphs, each kernel bracketed by CUDA events on the
   // solver's stream; per kernel name: total milliseconds and launch count.
   std::vector<ProfEntry> profile(int reps) override {

@@ -74,6 +74,8 @@ def _load():
         "wlr_get_factors": (i32, [H, P, P, P]),
         "wlr_get_history": (i32, [H, P, P, i32, ct.POINTER(i32)]),
         "wlr_get_iteration": (i32, [H, ct.POINTER(i32)]),
+        "wlr_get_state": (i32, [H, P, i64, ct.POINTER(i64)]),
+        "wlr_set_state": (i32, [H, P, i64]),
         "wlr_destroy": (i32, [H]),
         "wlr_status_string": (ct.c_char_p, [i32]),
         "wlr_last_error": (ct.c_char_p, [H]),
@@ -92,7 +94,8 @@ _lib = _load()
 EXPORTED = (
     "wlr_default_options", "wlr_create", "wlr_set_data", "wlr_set_init", "wlr_step",
     "wlr_solve", "wlr_objective", "wlr_get_result", "wlr_get_factors", "wlr_get_history",
-    "wlr_get_iteration", "wlr_destroy", "wlr_status_string", "wlr_last_error",
+    "wlr_get_iteration", "wlr_get_state", "wlr_set_state", "wlr_destroy", "wlr_status_string",
+    "wlr_last_error",
     "wlr_kernel_launches", "wlr_profile", "wlr_x1_update_noalloc",
 )
 
@@ -255,6 +258,22 @@ def wlr_get_iteration(h):
     return p.value
 
 
+def wlr_get_state(h):
+    """Checkpoint of the iteration as bytes (host copy of the library's state)."""
+    n = ct.c_int64(0)
+    _check(_lib.wlr_get_state(h, None, 0, ct.byref(n)), h)
+    buf = ct.create_string_buffer(max(n.value, 1))
+    _check(_lib.wlr_get_state(h, buf, n.value, ct.byref(n)), h)
+    return buf.raw[:n.value]
+
+
+def wlr_set_state(h, state):
+    """Restore a checkpoint made by wlr_get_state (same sizes, options and data)."""
+    b = bytes(state)
+    buf = ct.create_string_buffer(b, max(len(b), 1))
+    _check(_lib.wlr_set_state(h, buf, len(b)), h)
+
+
 def wlr_destroy(h):
     if h:
         _lib.wlr_destroy(h)
@@ -349,6 +368,12 @@ class Solver:
 
     def iteration(self):
         return wlr_get_iteration(self.h)
+
+    def get_state(self):
+        return wlr_get_state(self.h)
+
+    def set_state(self, state):
+        return wlr_set_state(self.h, state)
 
     def launches(self):
         return wlr_kernel_launches(self.h)
