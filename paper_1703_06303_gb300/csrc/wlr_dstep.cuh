@@ -166,9 +166,9 @@ struct DsLayout {
 //  - Next basis W = [V Y F_v + Z Y F_z], F_z = diag(1/||Z y_c||) for the columns with a
 //    non-negligible Ritz value, F_v = 1 for the others; W^T W = L L^T (Cholesky of the
 //    Gram formed from I, Y^T P Y and Theta); Mv = Y F_v L^{-T}, Mz = Y F_z L^{-T}.
-// Each thread owns the elements e = tid and tid + DS_THREADS of a b x b array (row
-// e % b, column e / b), indexed once.
-template <typename T>
+// Each thread owns the elements e = tid + q DS_THREADS, q < NE, of a b x b array (row
+// e % b, column e / b; NE DS_THREADS >= b^2), indexed once.
+template <typename T, int NE>
 __device__ void ritz_step(T* wk, int b, int max_sweeps, T* __restrict__ theta,
                           T* __restrict__ resid, int* __restrict__ err) {
   using Row = T[DS_P];
@@ -194,7 +194,6 @@ __device__ void ritz_step(T* wk, int b, int max_sweeps, T* __restrict__ theta,
   __shared__ int bad_s;
   const int tid = threadIdx.x;
   const int bb = b * b;
-  constexpr int NE = (DS_BM * DS_BM + DS_THREADS - 1) / DS_THREADS;
   int er[NE], ec[NE];
 #pragma unroll
   for (int q = 0; q < NE; ++q) {
@@ -430,11 +429,12 @@ __device__ void ritz_step(T* wk, int b, int max_sweeps, T* __restrict__ theta,
 // the steps spread over the CTA: Q1^T Q1 = I + F = (I + Lambda)(I + Lambda)^T by
 // right-looking elimination (step t: Lambda_tt = F_tt / (1 + sqrt(1 + F_tt)), and the
 // trailing lower triangle takes F_ij -= F_it F_jt / (1 + Lambda_tt)^2, so that
-// Lambda_it = F_it / (1 + Lambda_tt) uses column t as it stands after step t - 1); then
-// (I + Lambda) N = -Lambda by forward elimination over the rows, and
-// R^{-1} = R1inv (I + N)^T.  F arrives as F(i, j) = get(i + j k) (lower part used).
+// Lambda_it = F_it / (1 + Lambda_tt) uses column t as it stands after step t - 1); the
+// forward elimination for (I + Lambda) N = -Lambda runs alongside (its step t needs only
+// column t of Lambda), and R^{-1} = R1inv (I + N)^T.  F arrives as F(i, j) = get(i + j k)
+// (lower part used).
 // Work arrays in wk: F, R1inv, N (row-major, pitch k), R^{-1} (row-major).
-template <typename T, typename Get>
+template <typename T, int NE, typename Get>
 __device__ void chol2_block(T* wk, int k, Get get, const T* __restrict__ R1inv,
                             T* __restrict__ Nout, T* __restrict__ Rinv, int* __restrict__ err) {
   T* F = wk;
@@ -445,9 +445,8 @@ __device__ void chol2_block(T* wk, int k, Get get, const T* __restrict__ R1inv,
   __shared__ int flag_s;
   const int tid = threadIdx.x;
   const int kk = k * k;
-  // this thread's element (i, j) = (tid / k, tid % k) of a k x k array (k <= 32, so at
-  // most two per thread: tid and tid + DS_THREADS)
-  constexpr int NE = (DS_BM * DS_BM + DS_THREADS - 1) / DS_THREADS;
+  // this thread's elements (i, j) = (e / k, e % k), e = tid + q DS_THREADS, q < NE, of a
+  // k x k array (NE DS_THREADS >= k^2)
   int ei[NE], ej[NE];
 #pragma unroll
   for (int q = 0; q < NE; ++q) {
@@ -466,6 +465,9 @@ __device__ void chol2_block(T* wk, int k, Get get, const T* __restrict__ R1inv,
   });
   if (tid == 0) flag_s = 0;
   __syncthreads();
+  // rhs of (I + Lambda) N = -Lambda, filled column by column as Lambda's columns appear
+  each([&](int i, int c) { Nm[i * k + c] = T(0); });
+  __syncthreads();
   for (int t = 0; t < k; ++t) {
     const T ftt = F[t * k + t];
     T lam = T(0);
@@ -478,19 +480,18 @@ __device__ void chol2_block(T* wk, int k, Get get, const T* __restrict__ R1inv,
       if (bad) flag_s = 1;
     }
     const T r2 = rden * rden;
+    // one phase: the trailing update of the factorization, and step t of the forward
+    // elimination for N (row t of the rhs is final up to 1 / (1 + Lambda_tt); its entry t
+    // is -Lambda_tt, the rows below take their entry t = -Lambda_it first)
     each([&](int i, int j) {
       if (i >= j && j > t) F[i * k + j] = fma(-F[i * k + t] * r2, F[j * k + t], F[i * k + j]);
-    });
-    __syncthreads();
-  }
-  // right-hand sides -Lambda (lower, with the diagonal)
-  each([&](int i, int c) { Nm[i * k + c] = c < i ? -F[i * k + c] * rdg_s[c] : (c == i ? -lam_s[i] : T(0)); });
-  __syncthreads();
-  // row l is final at step l up to the factor 1 / (1 + Lambda_ll)
-  for (int l = 0; l < k - 1; ++l) {
-    const T rl = rdg_s[l];
-    each([&](int i, int c) {
-      if (i > l && c <= l) Nm[i * k + c] = fma(-F[i * k + l] * rl * rl, Nm[l * k + c], Nm[i * k + c]);
+      if (i > t && j <= t) {
+        const T lit = F[i * k + t] * rden;                 // Lambda_it
+        const T rtj = j == t ? -lam : Nm[t * k + j];       // raw row t of the rhs
+        const T base = j == t ? -lit : Nm[i * k + j];
+        Nm[i * k + j] = fma(-lit * rden, rtj, base);
+      }
+      if (i == t && j == t) Nm[t * k + t] = -lam;
     });
     __syncthreads();
   }
@@ -572,7 +573,9 @@ kv_pair(const T* __restrict__ Kh, const T* __restrict__ Kl, const T* __restrict_
 }
 
 // The cluster kernel (grid = one cluster of NC CTAs, DS_THREADS threads each).
-template <typename T>
+// NE: elements of a b x b (and k x k) array per thread, 1 when both fit in one pass (a
+// second pass doubles the straight-line code of the serial phases on CTA 0).
+template <typename T, int NE>
 __global__ void __launch_bounds__(DS_THREADS, 1)
 dstep_cluster(DstepArgs<T> a) {
   extern __shared__ unsigned char smem_raw[];
@@ -632,7 +635,7 @@ dstep_cluster(DstepArgs<T> a) {
       Tt[v] = (T)sum;
     }
     // ---- (2) the second factor on CTA 0 (from the reduced S2 - I in global memory)
-    if (rank == 0) chol2_block<T>(Wk, k, [&](int e) { return a.F2[e]; }, a.R1inv, a.Nout, a.Rinv, a.err);
+    if (rank == 0) chol2_block<T, NE>(Wk, k, [&](int e) { return a.F2[e]; }, a.R1inv, a.Nout, a.Rinv, a.err);
     cluster.sync();
     // ---- (3) B = (I + N) t and C = R^{-1} B for this CTA's columns
     {
@@ -752,7 +755,7 @@ dstep_cluster(DstepArgs<T> a) {
       Wk[(e < b * b ? 0 : 4 * DS_BM * DS_P) + r_ * DS_P + c_] = v;
     }
     __syncthreads();
-    ritz_step<T>(Wk, b, a.sweeps, a.theta, a.resid, a.err);
+    ritz_step<T, NE>(Wk, b, a.sweeps, a.theta, a.resid, a.err);
   }
   cluster.sync();
   // ---- next basis rows and Ritz vectors (Y, Mv, Mz from CTA 0)

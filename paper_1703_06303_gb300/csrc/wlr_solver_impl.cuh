@@ -590,6 +590,7 @@ class Solver final : public SolverBase {
     if (e & ERRBIT_RANK_DEFICIENT) throw Fail{WLR_ERR_RANK_DEFICIENT, "Cholesky of X1^T X1 broke down: X1 is not of rank k (Eq. 8 assumes rank k)"};
     if (e & ERRBIT_NOT_SPD) throw Fail{WLR_ERR_NOT_SPD, "a row system diag(W1(i,:)^2) + C C^T was not positive definite"};
     if (e & ERRBIT_EIG) throw Fail{WLR_ERR_RANK_DEFICIENT, "the subspace basis for the rank-(r-k) SVD step lost rank"};
+    if (e & tc::ERRBIT_TIMEOUT) throw Fail{WLR_ERR_DEVICE_TIMEOUT, "a bounded wait of the tensor-core pipeline gave up"};
   }
   void raise_err_async() {}
 
@@ -726,6 +727,25 @@ class Solver final : public SolverBase {
     }
     WLR_CUDA(cudaFuncSetAttribute((const void*)tc::gram_tf32x3_t, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   tc::T_SMEM_BYTES));
+    // K = A2^T A2: the column-block pairs bi <= bj, about one CTA per SM over the chunks
+    {
+      if (!mk(&mA2h64_, A2h_, n2, tc::KN) || !mk(&mA2l64_, A2l_, n2, tc::KN)) return;
+      // blocks (bi, bj) of 128 x 64 columns holding entries c1 <= c2
+      std::vector<int2> pr;
+      for (int bi = 0; bi < cdiv(n2, 128); ++bi)
+        for (int bj = 2 * bi; bj < cdiv(n2, tc::KN); ++bj) pr.push_back(make_int2(bi, bj));
+      kk_npairs_ = (int)pr.size();
+      kk_pairs_ = dalloc<int2>(pr.size());
+      WLR_CUDA(cudaMemcpy(kk_pairs_, pr.data(), sizeof(int2) * pr.size(), cudaMemcpyHostToDevice));
+      ch_kk_ = chunking(m, (size_t)kk_npairs_, 152);
+      const size_t needk = (size_t)ch_kk_.nch * kk_npairs_ * tc::K_TILE;
+      if (needk > part_elems_) {
+        part64_ = dalloc<double>(needk);
+        part_elems_ = needk;
+      }
+      WLR_CUDA(cudaFuncSetAttribute((const void*)tc::gram_kk_tf32x3, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    tc::K_SMEM_BYTES));
+    }
     use_tc_ = true;
   }
   void tc_split_a2() {
@@ -799,13 +819,28 @@ class Solver final : public SolverBase {
     sumsq_partial<T><<<nb, 256, 0, stream_>>>(A2, lda_, m, n2, wpart_scratch(nb));
     reduce_partials<double><<<1, 32, 0, stream_>>>(wpart_scratch(nb), 1, nb, 1, normA2_, nullptr);
     count(2);
-    gram(A2, lda_, A2, lda_, n2, nullptr, 0, n2, n2, (int64_t)n2 * n2, ch_K_);
-    reduce64((int64_t)n2 * n2, ch_K_.nch, (int64_t)n2 * n2, K64_);
+    tc_split_a2();
+    if (use_tc_) {
+      tc_gram_k();
+    } else {
+      gram(A2, lda_, A2, lda_, n2, nullptr, 0, n2, n2, (int64_t)n2 * n2, ch_K_);
+      reduce64((int64_t)n2 * n2, ch_K_.nch, (int64_t)n2 * n2, K64_);
+    }
     if (use_dstep_ && Kh_) {
       split_pair<<<grid1d((int64_t)n2 * n2), 256, 0, stream_>>>(K64_, (int64_t)n2 * n2, Kh_, Kl_);
       count(1);
     }
-    tc_split_a2();
+  }
+  // K = A2^T A2 on the tensor cores (3xTF32, from the split copies of A2)
+  void tc_gram_k() {
+    const int n2 = d_.n2;
+    Prof pf(this, "gram_kk_tf32x3");
+    tc::gram_kk_tf32x3<<<dim3(kk_npairs_, ch_kk_.nch), tc::K_THREADS, tc::K_SMEM_BYTES, stream_>>>(
+        mA2h_, mA2l_, mA2h64_, mA2l64_, d_.m, ch_kk_.rows, kk_pairs_, kk_npairs_, part64_, err_);
+    WLR_CUDA(cudaGetLastError());
+    tc::reduce_kk<<<grid1d((int64_t)kk_npairs_ * tc::K_TILE), 256, 0, stream_>>>(part64_, ch_kk_.nch, kk_pairs_,
+                                                                              kk_npairs_, n2, K64_);
+    count(2);
   }
   double* wpart_scratch(int n) {
     if (!sumsq_part_) sumsq_part_ = dalloc<double>(std::max(n, 304));
@@ -902,7 +937,8 @@ class Solver final : public SolverBase {
   void setup_dstep() {
     const int n2 = d_.n2, k = d_.k, b = d_.b, s = d_.s;
     if (s <= 0 || n2 <= 0 || b > DS_BM) return;
-    const void* fn = (const void*)dstep_cluster<T>;
+    ds_ne_ = std::max(b * b, k * k) <= DS_THREADS ? 1 : 2;
+    const void* fn = ds_ne_ == 1 ? (const void*)dstep_cluster<T, 1> : (const void*)dstep_cluster<T, 2>;
     for (int nc : {16, 8}) {
       if (n2 < nc) continue;
       const size_t bytes = sizeof(T) * DsLayout::make<T>(n2, k, b, s, cdiv(n2, nc)).total;
@@ -1045,7 +1081,10 @@ class Solver final : public SolverBase {
       a.front = front && t == 0 ? 1 : 0;
       {
         Prof pf(this, "dstep");
-        WLR_CUDA(cudaLaunchKernelEx(&cfg, dstep_cluster<T>, a));
+        if (ds_ne_ == 1)
+          WLR_CUDA(cudaLaunchKernelEx(&cfg, dstep_cluster<T, 1>, a));
+        else
+          WLR_CUDA(cudaLaunchKernelEx(&cfg, dstep_cluster<T, 2>, a));
       }
       count(1);
     }
@@ -1214,7 +1253,7 @@ class Solver final : public SolverBase {
   bool kv_pending_ = false;
   bool fuse_front_ = false;  // ... with the second factor and B, C in front (k <= 32)
   const T* front_rpre_ = nullptr;
-  int ds_nc_ = 0;
+  int ds_nc_ = 0, ds_ne_ = 1;
   size_t ds_smem_ = 0;
   float *Kh_ = nullptr, *Kl_ = nullptr;   // K as a float pair (float path)
   T *ZKh_ = nullptr, *ZKl_ = nullptr;     // K V (high, low)
@@ -1228,7 +1267,10 @@ class Solver final : public SolverBase {
   int64_t ld4_ = 0;
   size_t part_elems_ = 0;
   float *A2h_ = nullptr, *A2l_ = nullptr, *Q1h_ = nullptr, *Q1l_ = nullptr;
-  CUtensorMap mA2h_, mA2l_, mQh128_, mQl128_, mQh32_, mQl32_;
+  CUtensorMap mA2h_, mA2l_, mQh128_, mQl128_, mQh32_, mQl32_, mA2h64_, mA2l64_;
+  int2* kk_pairs_ = nullptr;   // column-block pairs of the tensor-core K
+  int kk_npairs_ = 0;
+  Chunk ch_kk_{1, 32};
   Chunk ch_tc_{1, 32};
   int nblk_prep_ = 0;
   bool eig_vsmem_ = false;

@@ -337,5 +337,176 @@ gram_tf32x3_t(const __grid_constant__ CUtensorMap mY1h, const __grid_constant__ 
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tacc), "r"(T_TMEM_COLS) : "memory");
 }
 
+// ------------------------------------------------------------------------------------
+// K = A2^T A2 (step a0, once per clip) on the tensor cores: part[c][p] = the 128 x 64 block
+// (bi, bj) = pairs[p] (columns 128 bi .. + 127 by 64 bj .. + 63 of K, the blocks that hold
+// entries on or above the diagonal) of A2(rows of chunk c)^T A2(rows of chunk c), in
+// 3xTF32 like gram_tf32x3_t.  M = 128 columns on the TMEM lanes, N = 64; the tensor cores
+// accumulate a 128-row slab (4 stages of 32 rows) in FP32 into one of two 64-column TMEM
+// buffers while the other is read back by the 8 epilogue warps (warp w: lane quadrant
+// w % 4, columns 32 (w / 4) .. + 31) and added into float hi + lo pairs with TwoSum; warp 8
+// issues the TMA loads, warp 9 the MMAs.  chunk_rows is a multiple of 32, so only the last
+// chunk runs past m (TMA fills zeros).
+constexpr int KN = 64;                                      // MMA N
+constexpr int K_STAGES = 4;
+constexpr int K_B_BYTES = KN * BK * 4;                      // 8 KB
+constexpr int K_STAGE_BYTES = 2 * T_A_BYTES + 2 * K_B_BYTES;  // A hi, A lo, B hi, B lo
+constexpr int K_SMEM_BYTES = K_STAGES * K_STAGE_BYTES + 1024;
+constexpr int K_SLAB = 4;                                   // stages per TMEM slab (128 rows)
+constexpr unsigned K_TMEM_COLS = 128;                       // two 64-column accumulators
+constexpr int K_THREADS = 320;
+constexpr int K_TILE = 128 * KN;                            // partial entries per (chunk, pair)
+
+static __global__ void __launch_bounds__(K_THREADS, 1)
+gram_kk_tf32x3(const __grid_constant__ CUtensorMap mh, const __grid_constant__ CUtensorMap ml,
+               const __grid_constant__ CUtensorMap mh64, const __grid_constant__ CUtensorMap ml64, int m,
+               int chunk_rows, const int2* __restrict__ pairs, int npairs, double* __restrict__ part,
+               int* __restrict__ err) {
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t full[K_STAGES], empty[K_STAGES], accf[2], acce[2];
+  __shared__ unsigned tmem_base;
+  __shared__ int fail;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int p = blockIdx.x, c = blockIdx.y;
+  const int2 pb = pairs[p];
+  const int i_begin = c * chunk_rows;
+  const int i_end = min(m, i_begin + chunk_rows);
+  const int nkb = (i_end - i_begin + BK - 1) / BK;
+  const int nslab = (nkb + K_SLAB - 1) / K_SLAB;
+  const unsigned base = (smem_u32(smem_raw) + 1023u) & ~1023u;
+  unsigned char* base_ptr = smem_raw + (base - smem_u32(smem_raw));
+  auto a_addr = [&](int s, int lo) { return base + (unsigned)(s * K_STAGE_BYTES + lo * T_A_BYTES); };
+  auto b_addr = [&](int s, int lo) {
+    return base + (unsigned)(s * K_STAGE_BYTES + 2 * T_A_BYTES + lo * K_B_BYTES);
+  };
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < K_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&accf[b], 1);
+      mbar_init(&acce[b], 8);
+    }
+    fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(K_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const unsigned tacc = tmem_base;
+
+  if (warp == 8) {
+    if (lane == 0) {
+      for (int kb = 0; kb < nkb; ++kb) {
+        const int s = kb % K_STAGES;
+        if (kb >= K_STAGES && !mbar_wait(&empty[s], (unsigned)((kb / K_STAGES - 1) & 1))) {
+          atomicOr(&fail, 1);
+          break;
+        }
+        if (*(volatile int*)&fail) break;
+        mbar_expect_tx(&full[s], K_STAGE_BYTES);
+        const int x = i_begin + kb * BK;
+        tma_load_2d(base_ptr + (a_addr(s, 0) - base), &mh, &full[s], x, pb.x * 128);
+        tma_load_2d(base_ptr + (a_addr(s, 1) - base), &ml, &full[s], x, pb.x * 128);
+        tma_load_2d(base_ptr + (b_addr(s, 0) - base), &mh64, &full[s], x, pb.y * KN);
+        tma_load_2d(base_ptr + (b_addr(s, 1) - base), &ml64, &full[s], x, pb.y * KN);
+      }
+    }
+  } else if (warp == 9) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_tf32(128, KN);
+      for (int kb = 0; kb < nkb; ++kb) {
+        const int s = kb % K_STAGES, slab = kb / K_SLAB, b = slab & 1;
+        const bool first = kb % K_SLAB == 0;
+        if (!mbar_wait(&full[s], (unsigned)((kb / K_STAGES) & 1)) ||
+            (first && slab >= 2 && !mbar_wait(&acce[b], (unsigned)((slab / 2 - 1) & 1)))) {
+          atomicOr(&fail, 1);
+          break;
+        }
+        fence_after();
+        const uint64_t ah = sdesc_sw128(a_addr(s, 0)), al = sdesc_sw128(a_addr(s, 1));
+        const uint64_t bh = sdesc_sw128(b_addr(s, 0)), bl = sdesc_sw128(b_addr(s, 1));
+        const unsigned d = tacc + (unsigned)(b * KN);
+#pragma unroll
+        for (int ks = 0; ks < BK / 8; ++ks) {
+          const uint64_t adv = (uint64_t)((ks * 32) >> 4);
+          mma_tf32(d, ah + adv, bh + adv, idesc, (first && ks == 0) ? 0u : 1u);
+          mma_tf32(d, ah + adv, bl + adv, idesc, 1u);
+          mma_tf32(d, al + adv, bh + adv, idesc, 1u);
+        }
+        mma_commit(&empty[s]);
+        if (kb % K_SLAB == K_SLAB - 1 || kb == nkb - 1) mma_commit(&accf[b]);
+      }
+    }
+  } else {
+    // warps 0-7: TMEM lanes 32 (warp % 4) .. +31 (M = columns of block bi), 32 columns of N
+    const int q = warp & 3, h = warp >> 2;
+    float hi[32], lo[32];
+#pragma unroll
+    for (int a = 0; a < 32; ++a) {
+      hi[a] = 0.f;
+      lo[a] = 0.f;
+    }
+    bool ok = true;
+    for (int slab = 0; slab < nslab; ++slab) {
+      const int b = slab & 1;
+      if (!mbar_wait(&accf[b], (unsigned)((slab / 2) & 1))) {
+        ok = false;
+        break;
+      }
+      fence_after();
+      float v[32];
+      tmem_ld32(tacc + ((unsigned)(32 * q) << 16) + (unsigned)(b * KN + h * 32), v);
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acce[b]);
+#pragma unroll
+      for (int a = 0; a < 32; ++a) {
+        float sres, e;
+        two_sum_f(hi[a], v[a], sres, e);
+        hi[a] = sres;
+        lo[a] += e;
+      }
+    }
+    if (!ok || *(volatile int*)&fail) {
+      if (lane == 0) atomicOr(err, ERRBIT_TIMEOUT);
+    } else {
+      double* out = part + ((int64_t)c * npairs + p) * K_TILE + (int64_t)(32 * q + lane) * KN + h * 32;
+#pragma unroll
+      for (int a = 0; a < 32; ++a) out[a] = (double)hi[a] + (double)lo[a];
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tacc), "r"(K_TMEM_COLS) : "memory");
+}
+
+// K (n2 x n2, FP64) from the chunk partials of gram_kk_tf32x3: the entries with c1 <= c2 of
+// every block, summed over the chunks in order, written to both triangles.
+static __global__ void reduce_kk(const double* __restrict__ part, int nch, const int2* __restrict__ pairs,
+                                 int npairs, int n2, double* __restrict__ K) {
+  const int64_t total = (int64_t)npairs * K_TILE;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int p = (int)(e / K_TILE), rc = (int)(e % K_TILE);
+    const int r = rc / KN, col = rc % KN;
+    const int c1 = pairs[p].x * 128 + r, c2 = pairs[p].y * KN + col;
+    if (c1 >= n2 || c2 >= n2 || c1 > c2) continue;
+    double v = 0.0;
+    for (int c = 0; c < nch; ++c) v += __ldcg(&part[((int64_t)c * npairs + p) * K_TILE + rc]);
+    K[c1 + (int64_t)c2 * n2] = v;
+    K[c2 + (int64_t)c1 * n2] = v;
+  }
+}
+
 }  // namespace tc
 }  // namespace wlr
