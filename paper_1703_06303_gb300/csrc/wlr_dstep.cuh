@@ -128,14 +128,16 @@ struct DstepArgs {
 // work arrays are used by CTA 0 only).
 struct DsLayout {
   size_t Tq, Vt, Bs, Cs, Zh, Zl, Zr, Vsr, BVp, BV, HPp, Gp, CVp, Ml, Tt, NR, Wk, total;
+  // front: room for the front stage (second factor, B, C); without it Tq, Tt and NR are empty
   template <typename T>
-  __host__ __device__ static DsLayout make(int n2, int k, int b, int s, int R) {
-    return DsLayout(n2, k, b, s, R, (int)(sizeof(double) / sizeof(T)));
+  __host__ __device__ static DsLayout make(int n2, int k, int b, int s, int R, bool front) {
+    return DsLayout(n2, k, b, s, R, (int)(sizeof(double) / sizeof(T)), front);
   }
-  __host__ __device__ DsLayout(int n2, int k, int b, int s, int R, int dw) {
+  __host__ __device__ DsLayout(int n2, int k, int b, int s, int R, int dw, bool front) {
     const size_t ss = s > 0 ? s : 1;
+    const size_t kf = front ? k : 0;
     size_t o = 0;
-    Tq = o;  o += (size_t)dw * k * R;       // (Q1^T A2)(:, rows) in double (front stage)
+    Tq = o;  o += (size_t)dw * kf * R;      // (Q1^T A2)(:, rows) in double (front stage)
     Vt = o;  o += (size_t)b * n2;           // basis, V(j, c) at Vt[c*n2 + j]
     Bs = o;  o += 2 * (size_t)k * R;        // B(:, rows): high, low
     Cs = o;  o += (size_t)R * k;            // C(:, rows), C(x, j) at Cs[(j - l0)*k + x]
@@ -149,8 +151,8 @@ struct DsLayout {
     Gp = o;  o += (size_t)k * k;            // partial C C^T
     CVp = o; o += (size_t)k * ss;           // partial C V_s
     Ml = o;  o += 3 * (size_t)b * b;        // local copies of Y, Mv, Mz
-    Tt = o;  o += (size_t)k * R;            // (Q1^T A2)(:, rows) rounded to T
-    NR = o;  o += 2 * (size_t)k * k;        // local copies of N and R^{-1}
+    Tt = o;  o += kf * R;                   // (Q1^T A2)(:, rows) rounded to T
+    NR = o;  o += 2 * kf * k;               // local copies of N and R^{-1}
     Wk = o;  o += 10 * (size_t)DS_BM * DS_P;    // Rayleigh-Ritz / second-factor work arrays
     total = o;
   }
@@ -587,7 +589,7 @@ dstep_cluster(DstepArgs<T> a) {
   const int n2 = a.n2, k = a.k, b = a.b, s = a.s, NP = a.NP;
   const int R = (n2 + nc - 1) / nc;
   const int l0 = min(n2, rank * R), l1 = min(n2, l0 + R), nr = l1 - l0;
-  const DsLayout L = DsLayout::make<T>(n2, k, b, s, R);
+  const DsLayout L = DsLayout::make<T>(n2, k, b, s, R, a.front);
   T* Vt = sm + L.Vt;
   T* Bs = sm + L.Bs;
   T* Cs = sm + L.Cs;

@@ -1257,12 +1257,12 @@ inline int row_kp(int k) {
 
 // Register row solve (phase 3 of row_pass) for a system padded to KP x KP: LG lanes
 // share one row system, lane g holding the NS = KP / LG matrix rows q = g + LG*s in
-// registers.  Off for double beyond KP = 16 and for KP = 64 (register budget), where the
-// shared-memory solve below runs instead.
+// registers (KP = 64: a whole warp per system, two rows per lane).  Off for double beyond
+// KP = 16 (register budget), where the shared-memory solve below runs instead.
 template <typename T, int KP>
 struct RegSolve {
-  static constexpr bool on = sizeof(T) == 4 ? KP <= 32 : KP <= 16;
-  static constexpr int LG = (KP <= 8 || (sizeof(T) == 4 && KP <= 20)) ? 4 : 8;
+  static constexpr bool on = sizeof(T) == 4 ? true : KP <= 16;
+  static constexpr int LG = (KP <= 8 || (sizeof(T) == 4 && KP <= 20)) ? 4 : (KP <= 32 ? 8 : 32);
   static constexpr int NS = KP / LG;
 };
 
@@ -1470,6 +1470,57 @@ __device__ __forceinline__ void rp_phase1(const T* __restrict__ A2, int64_t lda,
     for (int v = 0; v < NPU; ++v) Ys[(4 * rg + u) * (NP + 1) + cg * NPU + v] = acc[u][v];
 }
 
+// Gauss-Jordan steps t0 <= t < t1 of a row system held by a whole warp (phase 3 of
+// row_pass for KP = 64): lane g holds rows q = g + 32 sl (sl < NS) shifted so that
+// R[sl][jj] = M(q, t + jj) at step t, i.e. the pivot column is always R[sl][0] and the loop
+// body does not depend on t.  The pivot rows of these steps sit in slot ST (lane t - 32 ST).
+// Step t: d_t = M(t,t), and every row q != t (above the pivot too) takes
+// M(q, j) -= M(q,t) M(t,j) / d_t for j > t and e_q -= M(q,t) e_t / d_t, while all rows shift
+// one place left.  After the last step M is diagonal with the pivots d_q of the steps, so
+// x_q = e_q / d_q (rd holds 1 / d_q); no factor has to be kept for a back substitution.
+template <typename T, int KP, int NS, int ST>
+__device__ __forceinline__ void gj_steps(T (&R)[NS][KP], T (&e)[NS], T (&rd)[NS], int t0, int t1, int k,
+                                         int g, bool active, bool& bad) {
+  constexpr unsigned FULL = 0xffffffffu;
+#pragma unroll 1
+  for (int t = t0; t < t1; ++t) {
+    const int ot = t - 32 * ST;
+    T d = __shfl_sync(FULL, R[ST][0], ot);
+    if (!(d > T(0)) || !wfinite(d)) {
+      bad = bad || active;
+      d = T(1);
+    }
+    const T rdt = wrcp(d);
+    if (g == ot) rd[ST] = rdt;
+    const T et = __shfl_sync(FULL, e[ST], ot);
+    T f[NS];
+#pragma unroll
+    for (int sl = 0; sl < NS; ++sl) {
+      f[sl] = (g + 32 * sl != t) ? R[sl][0] * rdt : T(0);
+      e[sl] = fma(-f[sl], et, e[sl]);
+    }
+    // columns t .. k - 1 remain (positions 0 .. rem - 1).  Groups of 8 positions: the 8
+    // shuffles of a group are in flight together; positions of the last group beyond rem
+    // take values that no later step reads.
+    const int rem = k - t;
+#pragma unroll
+    for (int j0 = 1; j0 < KP; j0 += 8) {
+      if (j0 < rem) {
+        T mj[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (j0 + u < KP) mj[u] = __shfl_sync(FULL, R[ST][j0 + u], ot);
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (j0 + u < KP) {
+#pragma unroll
+            for (int sl = 0; sl < NS; ++sl) R[sl][j0 + u - 1] = fma(-f[sl], mj[u], R[sl][j0 + u]);
+          }
+      }
+    }
+  }
+}
+
 template <typename T, int KP>
 __global__ void __launch_bounds__(256)
 row_pass(const T* __restrict__ A, int64_t lda, const T* __restrict__ W1, int64_t ldw,
@@ -1568,7 +1619,39 @@ row_pass(const T* __restrict__ A, int64_t lda, const T* __restrict__ W1, int64_t
   // ---- phase 3: row solves M x = e, M = diag(W1(i,:)^2) + C C^T (symmetric positive
   // definite), e = E(i,:)^T.
   bool bad = false;
-  if constexpr (RegSolve<T, KP>::on) {
+  if constexpr (RegSolve<T, KP>::on && RegSolve<T, KP>::LG == 32) {
+    // one warp per row system, Gauss-Jordan in registers (gj_steps), 8 systems per pass
+    constexpr int NS = RegSolve<T, KP>::NS;
+    const int g = tid & 31, grp = tid >> 5;
+#pragma unroll 1
+    for (int base = 0; base < RP_BM; base += 8) {
+      const int r = base + grp;
+      const bool active = i0 + r < m;
+      T R[NS][KP], e[NS], rd[NS];
+#pragma unroll
+      for (int sl = 0; sl < NS; ++sl) {
+        const int q = g + 32 * sl;
+        const bool qk = q < k;
+        const T w = (active && qk) ? w1_at(r, q) : T(1);
+#pragma unroll
+        for (int j = 0; j < KP; ++j) {
+          const T gv = (qk && j < k) ? Gs[q + j * k] : T(0);
+          R[sl][j] = q == j ? gv + w * w : gv;
+        }
+        e[sl] = (active && qk) ? Ys[r * (NP + 1) + q] : T(0);
+        rd[sl] = T(1);
+      }
+      gj_steps<T, KP, NS, 0>(R, e, rd, 0, min(k, 32), k, g, active, bad);
+      gj_steps<T, KP, NS, 1>(R, e, rd, 32, k, k, g, active, bad);
+      if (active) {
+#pragma unroll
+        for (int sl = 0; sl < NS; ++sl) {
+          const int q = g + 32 * sl;
+          if (q < k) X1new[(i0 + r) + (int64_t)q * m] = e[sl] * rd[sl];
+        }
+      }
+    }
+  } else if constexpr (RegSolve<T, KP>::on) {
     // Symmetric Gaussian elimination (LDL^T, no square roots) on the system padded to
     // KP x KP with an identity block.  Step t: the pivot d_t = M(t,t) and the entries
     // M(j,t) of column t (j > t) are broadcast from the lanes holding rows t and j; every

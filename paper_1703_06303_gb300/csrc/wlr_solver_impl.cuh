@@ -694,7 +694,6 @@ class Solver final : public SolverBase {
   // (each iteration), TMA tensor maps built once for these library-owned buffers.
   void setup_tc() {
     const int m = d_.m, k = d_.k, n2 = d_.n2;
-    if (k > tc::TN) return;  // the transposed kernel takes up to 32 columns of X
     void* fn = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &fn, cudaEnableDefault, &q) != cudaSuccess || !fn) {
@@ -705,8 +704,6 @@ class Solver final : public SolverBase {
     ld4_ = ((m + 3) / 4) * 4;
     A2h_ = dalloc<float>((size_t)ld4_ * n2);
     A2l_ = dalloc<float>((size_t)ld4_ * n2);
-    Q1h_ = dalloc<float>((size_t)ld4_ * k);
-    Q1l_ = dalloc<float>((size_t)ld4_ * k);
     auto mk = [&](CUtensorMap* map, const float* p, int cols, int boxc) {
       cuuint64_t dims[2] = {(cuuint64_t)m, (cuuint64_t)cols};
       cuuint64_t strides[1] = {(cuuint64_t)ld4_ * 4};
@@ -716,21 +713,12 @@ class Solver final : public SolverBase {
                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
     };
-    bool ok = mk(&mA2h_, A2h_, n2, 128) && mk(&mA2l_, A2l_, n2, 128) && mk(&mQh128_, Q1h_, k, 128) &&
-              mk(&mQl128_, Q1l_, k, 128) && mk(&mQh32_, Q1h_, k, tc::TN) && mk(&mQl32_, Q1l_, k, tc::TN);
-    if (!ok) return;
-    ch_tc_ = chunking(m, (size_t)(1 + cdiv(n2, 128)), 152);
-    const size_t need = (size_t)ch_tc_.nch * ((size_t)k * k + (size_t)k * n2);
-    if (need > part_elems_) {
-      part64_ = dalloc<double>(need);
-      part_elems_ = need;
-    }
-    WLR_CUDA(cudaFuncSetAttribute((const void*)tc::gram_tf32x3_t, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  tc::T_SMEM_BYTES));
-    // K = A2^T A2: the column-block pairs bi <= bj, about one CTA per SM over the chunks
+    // K = A2^T A2 (any k): blocks (bi, bj) of 128 x 64 columns holding entries c1 <= c2,
+    // about one CTA per SM over the row chunks
+    if (!mk(&mA2h_, A2h_, n2, 128) || !mk(&mA2l_, A2l_, n2, 128) || !mk(&mA2h64_, A2h_, n2, tc::KN) ||
+        !mk(&mA2l64_, A2l_, n2, tc::KN))
+      return;
     {
-      if (!mk(&mA2h64_, A2h_, n2, tc::KN) || !mk(&mA2l64_, A2l_, n2, tc::KN)) return;
-      // blocks (bi, bj) of 128 x 64 columns holding entries c1 <= c2
       std::vector<int2> pr;
       for (int bi = 0; bi < cdiv(n2, 128); ++bi)
         for (int bj = 2 * bi; bj < cdiv(n2, tc::KN); ++bj) pr.push_back(make_int2(bi, bj));
@@ -746,10 +734,31 @@ class Solver final : public SolverBase {
       WLR_CUDA(cudaFuncSetAttribute((const void*)tc::gram_kk_tf32x3, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     tc::K_SMEM_BYTES));
     }
+    use_tc_k_ = true;
+    // Q1^T [Q1 A2] each iteration: the transposed kernel takes up to 64 columns of X
+    if (k > 2 * tc::TN) return;
+    tn_ = k <= tc::TN ? tc::TN : 2 * tc::TN;
+    Q1h_ = dalloc<float>((size_t)ld4_ * k);
+    Q1l_ = dalloc<float>((size_t)ld4_ * k);
+    if (!mk(&mQh128_, Q1h_, k, 128) || !mk(&mQl128_, Q1l_, k, 128) || !mk(&mQh32_, Q1h_, k, tn_) ||
+        !mk(&mQl32_, Q1l_, k, tn_))
+      return;
+    ch_tc_ = chunking(m, (size_t)(1 + cdiv(n2, 128)), 152);
+    const size_t need = (size_t)ch_tc_.nch * ((size_t)k * k + (size_t)k * n2);
+    if (need > part_elems_) {
+      part64_ = dalloc<double>(need);
+      part_elems_ = need;
+    }
+    if (tn_ == tc::TN)
+      WLR_CUDA(cudaFuncSetAttribute((const void*)tc::gram_tf32x3_t<tc::TN>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, tc::t_smem_bytes(tc::TN)));
+    else
+      WLR_CUDA(cudaFuncSetAttribute((const void*)tc::gram_tf32x3_t<2 * tc::TN>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, tc::t_smem_bytes(2 * tc::TN)));
     use_tc_ = true;
   }
   void tc_split_a2() {
-    if (!use_tc_) return;
+    if (!use_tc_k_) return;
     const int m = d_.m, k = d_.k, n2 = d_.n2;
     tc::split_tf32<<<grid1d((int64_t)m * n2), 256, 0, stream_>>>((const float*)(A_ + (int64_t)k * lda_), lda_, m, n2,
                                                                   A2h_, A2l_, ld4_);
@@ -767,9 +776,13 @@ class Solver final : public SolverBase {
     {
       Prof pf(this, "gram_tf32x3_t");
       dim3 g(1 + cdiv(n2, 128), ch_tc_.nch);
-      tc::gram_tf32x3_t<<<g, 192, tc::T_SMEM_BYTES, stream_>>>(mQh128_, mQl128_, mA2h_, mA2l_, mQh32_, mQl32_, m, k,
-                                                               k, n2, ch_tc_.rows, part64_,
-                                                               (int64_t)k * k + (int64_t)k * n2, err_);
+      const int64_t pstride = (int64_t)k * k + (int64_t)k * n2;
+      if (tn_ == tc::TN)
+        tc::gram_tf32x3_t<tc::TN><<<g, tc::t_threads(tc::TN), tc::t_smem_bytes(tc::TN), stream_>>>(
+            mQh128_, mQl128_, mA2h_, mA2l_, mQh32_, mQl32_, m, k, k, n2, ch_tc_.rows, part64_, pstride, err_);
+      else
+        tc::gram_tf32x3_t<2 * tc::TN><<<g, tc::t_threads(2 * tc::TN), tc::t_smem_bytes(2 * tc::TN), stream_>>>(
+            mQh128_, mQl128_, mA2h_, mA2l_, mQh32_, mQl32_, m, k, k, n2, ch_tc_.rows, part64_, pstride, err_);
     }
     count(2);
   }
@@ -820,7 +833,7 @@ class Solver final : public SolverBase {
     reduce_partials<double><<<1, 32, 0, stream_>>>(wpart_scratch(nb), 1, nb, 1, normA2_, nullptr);
     count(2);
     tc_split_a2();
-    if (use_tc_) {
+    if (use_tc_k_) {
       tc_gram_k();
     } else {
       gram(A2, lda_, A2, lda_, n2, nullptr, 0, n2, n2, (int64_t)n2 * n2, ch_K_);
@@ -937,12 +950,14 @@ class Solver final : public SolverBase {
   void setup_dstep() {
     const int n2 = d_.n2, k = d_.k, b = d_.b, s = d_.s;
     if (s <= 0 || n2 <= 0 || b > DS_BM) return;
-    ds_ne_ = std::max(b * b, k * k) <= DS_THREADS ? 1 : 2;
+    // the front stage (second factor, B, C inside the cluster) for k <= 32
+    const bool front = k <= 32;
+    ds_ne_ = std::max(b * b, front ? k * k : 0) <= DS_THREADS ? 1 : 2;
     const void* fn = ds_ne_ == 1 ? (const void*)dstep_cluster<T, 1> : (const void*)dstep_cluster<T, 2>;
     for (int nc : {16, 8}) {
       if (n2 < nc) continue;
-      const size_t bytes = sizeof(T) * DsLayout::make<T>(n2, k, b, s, cdiv(n2, nc)).total;
-      if (bytes > 200 * 1024) continue;
+      const size_t bytes = sizeof(T) * DsLayout::make<T>(n2, k, b, s, cdiv(n2, nc), front).total;
+      if (bytes > 225 * 1024) continue;
       if (nc > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
         cudaGetLastError();
         continue;
@@ -974,8 +989,7 @@ class Solver final : public SolverBase {
       break;
     }
     if (!use_dstep_) return;
-    // the front stage (second factor, B, C inside the cluster) for k <= 32
-    fuse_front_ = k <= 32;
+    fuse_front_ = front;
     if (fuse_front_) {
       bpart_ = dalloc<double>(std::max(nblk_coef_, ds_nc_));
       WLR_CUDA(cudaMemsetAsync(bpart_, 0, sizeof(double) * std::max(nblk_coef_, ds_nc_), stream_));
@@ -1263,7 +1277,9 @@ class Solver final : public SolverBase {
   unsigned int *prep_ticket_ = nullptr, *eig_ticket_ = nullptr, *fin_ticket_ = nullptr;
   T* HP_ = nullptr;
   // tensor-core Gram (FP32 path)
-  bool use_tc_ = false;
+  bool use_tc_ = false;     // Q1^T [Q1 A2] on the tensor cores (k <= 32)
+  bool use_tc_k_ = false;   // K = A2^T A2 on the tensor cores
+  int tn_ = 32;             // MMA N of the Q1^T [Q1 A2] kernel (32 or 64 columns of Q1)
   int64_t ld4_ = 0;
   size_t part_elems_ = 0;
   float *A2h_ = nullptr, *A2l_ = nullptr, *Q1h_ = nullptr, *Q1l_ = nullptr;

@@ -159,19 +159,21 @@ static __global__ void form_q_split(const float* __restrict__ X1, int64_t ldx, c
 // Transposed form with per-slab read-back (the one the solver uses):
 //   part[c*pstride + a + col*P] = sum over the rows of chunk c of Y(i, col) X(i, a)
 // computed as D = Y^T X with the columns of Y on the 128 MMA rows (all TMEM lanes carry
-// data) and the P <= 32 columns of X as N = 32.  Each 32-row slab is accumulated by the
-// tensor cores in FP32 into one of two TMEM buffers; while the MMA fills the other one,
-// warps 0-3 read the slab back (tcgen05.ld) and add it into a float hi + lo pair per entry
-// (TwoSum), so the chunk sum keeps about FP64 accuracy, as the SIMT Gram does.
-// Warp 4 issues the TMA loads, warp 5 the MMAs.  Column tile 0 uses Y1 (= Q1, q1 columns)
-// as Y, tiles t >= 1 use columns (t-1)*128 .. of Y2 (= A2).
-constexpr int TN = 32;                                   // MMA N (columns of X, padded)
+// data) and the P <= TNV columns of X as N = TNV (32 or 64).  Each 32-row slab is
+// accumulated by the tensor cores in FP32 into one of two TMEM buffers; while the MMA
+// fills the other one, the epilogue warps read the slab back (tcgen05.ld) and add it into
+// a float hi + lo pair per entry (TwoSum), so the chunk sum keeps about FP64 accuracy, as
+// the SIMT Gram does.  Epilogue warp w (of 4 TNV / 32) reads TMEM lanes 32 (w % 4) ..
+// + 31 and columns 32 (w / 4) .. + 31; the next warp issues the TMA loads, the one after it
+// the MMAs.  Column tile 0 uses Y1 (= Q1, q1 columns) as Y, tiles t >= 1 use columns
+// (t-1)*128 .. of Y2 (= A2).
+constexpr int TN = 32;                                   // MMA N for up to 32 columns of X
 constexpr int T_STAGES = 3;
 constexpr int T_A_BYTES = 128 * BK * 4;                  // Y tile: 128 columns x 32 rows
-constexpr int T_B_BYTES = TN * BK * 4;                   // X tile: 32 columns x 32 rows
-constexpr int T_STAGE_BYTES = 2 * T_A_BYTES + 2 * T_B_BYTES;
-constexpr int T_SMEM_BYTES = T_STAGES * T_STAGE_BYTES + 1024;
-constexpr unsigned T_TMEM_COLS = 64;                     // two 32-column accumulators
+__host__ __device__ constexpr int t_b_bytes(int tnv) { return tnv * BK * 4; }   // X tile
+__host__ __device__ constexpr int t_stage_bytes(int tnv) { return 2 * T_A_BYTES + 2 * t_b_bytes(tnv); }
+__host__ __device__ constexpr int t_smem_bytes(int tnv) { return T_STAGES * t_stage_bytes(tnv) + 1024; }
+__host__ __device__ constexpr int t_threads(int tnv) { return 32 * (4 * (tnv / 32) + 2); }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
@@ -198,12 +200,16 @@ __device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) 
   e = (a - ap) + (b - bp);
 }
 
-static __global__ void __launch_bounds__(192)
+template <int TNV>
+static __global__ void __launch_bounds__(t_threads(TNV))
 gram_tf32x3_t(const __grid_constant__ CUtensorMap mY1h, const __grid_constant__ CUtensorMap mY1l,
               const __grid_constant__ CUtensorMap mY2h, const __grid_constant__ CUtensorMap mY2l,
               const __grid_constant__ CUtensorMap mXh, const __grid_constant__ CUtensorMap mXl,
               int m, int P, int q1, int q2, int chunk_rows, double* __restrict__ part, int64_t pstride,
               int* __restrict__ err) {
+  constexpr int NEPI = 4 * (TNV / 32);                  // epilogue warps
+  constexpr int T_B_BYTES = t_b_bytes(TNV), T_STAGE_BYTES = t_stage_bytes(TNV);
+  constexpr unsigned T_TMEM_COLS = 2 * TNV;             // two TNV-column accumulators
   extern __shared__ unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full[T_STAGES], empty[T_STAGES], accf[2], acce[2];
   __shared__ unsigned tmem_base;
@@ -232,7 +238,7 @@ gram_tf32x3_t(const __grid_constant__ CUtensorMap mY1h, const __grid_constant__ 
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&accf[b], 1);
-      mbar_init(&acce[b], 4);
+      mbar_init(&acce[b], NEPI);
     }
     fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -248,7 +254,7 @@ gram_tf32x3_t(const __grid_constant__ CUtensorMap mY1h, const __grid_constant__ 
   fence_after();
   const unsigned tacc = tmem_base;
 
-  if (warp == 4) {
+  if (warp == NEPI) {
     if (lane == 0) {
       for (int kb = 0; kb < nkb; ++kb) {
         const int s = kb % T_STAGES;
@@ -265,9 +271,9 @@ gram_tf32x3_t(const __grid_constant__ CUtensorMap mY1h, const __grid_constant__ 
         tma_load_2d(base_ptr + (b_addr(s, 1) - base), &mXl, &full[s], x, 0);
       }
     }
-  } else if (warp == 5) {
+  } else if (warp == NEPI + 1) {
     if (lane == 0) {
-      constexpr uint32_t idesc = idesc_tf32(128, TN);
+      constexpr uint32_t idesc = idesc_tf32(128, TNV);
       for (int kb = 0; kb < nkb; ++kb) {
         const int s = kb % T_STAGES, b = kb & 1;
         if (!mbar_wait(&full[s], (unsigned)((kb / T_STAGES) & 1)) ||
@@ -278,7 +284,7 @@ gram_tf32x3_t(const __grid_constant__ CUtensorMap mY1h, const __grid_constant__ 
         fence_after();
         const uint64_t yhd = sdesc_sw128(a_addr(s, 0)), yld = sdesc_sw128(a_addr(s, 1));
         const uint64_t xhd = sdesc_sw128(b_addr(s, 0)), xld = sdesc_sw128(b_addr(s, 1));
-        const unsigned d = tacc + (unsigned)(b * TN);
+        const unsigned d = tacc + (unsigned)(b * TNV);
 #pragma unroll
         for (int ks = 0; ks < BK / 8; ++ks) {
           const uint64_t adv = (uint64_t)((ks * 32) >> 4);
@@ -291,10 +297,12 @@ gram_tf32x3_t(const __grid_constant__ CUtensorMap mY1h, const __grid_constant__ 
       }
     }
   } else {
-    // warps 0-3: TMEM lanes 32 warp .. +31 = columns col = 32 warp + lane of this tile
-    float hi[TN], lo[TN];
+    // epilogue warp w: TMEM lanes 32 (w % 4) .. + 31 = columns col = 32 (w % 4) + lane of
+    // this tile, X columns a = 32 (w / 4) .. + 31
+    const int qd = warp & 3, hf = warp >> 2;
+    float hi[32], lo[32];
 #pragma unroll
-    for (int a = 0; a < TN; ++a) {
+    for (int a = 0; a < 32; ++a) {
       hi[a] = 0.f;
       lo[a] = 0.f;
     }
@@ -306,13 +314,13 @@ gram_tf32x3_t(const __grid_constant__ CUtensorMap mY1h, const __grid_constant__ 
         break;
       }
       fence_after();
-      float v[TN];
-      tmem_ld32(tacc + ((unsigned)(32 * warp) << 16) + (unsigned)(b * TN), v);
+      float v[32];
+      tmem_ld32(tacc + ((unsigned)(32 * qd) << 16) + (unsigned)(b * TNV + 32 * hf), v);
       fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&acce[b]);
 #pragma unroll
-      for (int a = 0; a < TN; ++a) {
+      for (int a = 0; a < 32; ++a) {
         float sres, e;
         two_sum_f(hi[a], v[a], sres, e);
         hi[a] = sres;
@@ -322,12 +330,12 @@ gram_tf32x3_t(const __grid_constant__ CUtensorMap mY1h, const __grid_constant__ 
     if (!ok || *(volatile int*)&fail) {
       if (lane == 0) atomicOr(err, ERRBIT_TIMEOUT);
     } else {
-      const int j = 32 * warp + lane;
+      const int j = 32 * qd + lane;
       if (j < ncols) {
-        double* out = part + (int64_t)c * pstride + (int64_t)(gcol0 + j) * P;
+        double* out = part + (int64_t)c * pstride + (int64_t)(gcol0 + j) * P + 32 * hf;
 #pragma unroll
-        for (int a = 0; a < TN; ++a)
-          if (a < P) out[a] = (double)hi[a] + (double)lo[a];
+        for (int a = 0; a < 32; ++a)
+          if (32 * hf + a < P) out[a] = (double)hi[a] + (double)lo[a];
       }
     }
   }

@@ -158,10 +158,12 @@ def test_random_init_matches_counter_generator(wlr):
 
 
 # ------------------------------------------------------------------ FP32 parity
-def test_fp32_step_config2_full_size(wlr):
-    """Full-size FP32 step at the 160x120, n=400, k=20, r=25 workload: every entry of
-    X1_{p+1} and F_p against one FP64 oracle step from the same X1_p."""
-    spec = synth.CONFIGS[2]
+@pytest.mark.parametrize("config", [2, 3])
+def test_fp32_step_full_size(wlr, config):
+    """Full-size FP32 step at the 160x120, n=400, k=20, r=25 workload and at the
+    320x240, n=1000, k=50, r=60 one: every entry of X1_{p+1} and F_p against one FP64
+    oracle step from the same X1_p."""
+    spec = synth.CONFIGS[config]
     clip = synth.make_clip(spec)
     A = clip["A"].astype(np.float32).astype(np.float64)
     W1 = clip["W1"].astype(np.float32).astype(np.float64)
@@ -176,6 +178,27 @@ def test_fp32_step_config2_full_size(wlr):
     s.set_init(wlr.WLR_INIT_USER, X.astype(np.float32))
     F = s.step()
     X1 = _x1(s, spec.m, spec.k)
+    assert abs(F - st.F) <= 1e-4 * st.F
+    assert _rel(X1, st.X1_next) < 2e-3
+    s.close()
+
+
+@pytest.mark.parametrize("k", [33, 64])
+def test_fp32_step_wide_k(wlr, k):
+    """FP32 step with 32 < k <= 64 (one warp per row system, Gauss-Jordan in registers;
+    Q1^T [Q1 A2] with N = 64 on the tensor cores) on a ragged problem against the oracle."""
+    m, n, r = 1000, k + 150, k + 6
+    A, W1, X0 = _problem(21 + k, m, n, k, r, rank=4)
+    A = A.astype(np.float32).astype(np.float64)
+    W1 = W1.astype(np.float32).astype(np.float64)
+    X = A[:, :k] + 0.01 * X0
+    X = X.astype(np.float32).astype(np.float64)
+    st = oracle.swlr_step(A, W1, X, r)
+    s = _solver(wlr, (m, n, k, r), wlr.WLR_PREC_FP32, eig_iters_cold=300)
+    s.set_data(_dev(A.astype(np.float32)), _dev(W1.astype(np.float32)))
+    s.set_init(wlr.WLR_INIT_USER, X.astype(np.float32))
+    F = s.step()
+    X1 = _x1(s, m, k)
     assert abs(F - st.F) <= 1e-4 * st.F
     assert _rel(X1, st.X1_next) < 2e-3
     s.close()
