@@ -178,6 +178,25 @@ wlr_status wlr_get_state(wlr_handle h, void* buf, int64_t cap, int64_t* size_out
  * Synchronises. */
 wlr_status wlr_set_state(wlr_handle h, const void* buf, int64_t size);
 
+/* Batched solve: `iters` further iterations of Algorithm 1 (Section 3) on each of `count`
+ * independent problems, which may differ in m, n, k, r and precision.  Each handle must
+ * hold its data and an initial X1 (wlr_set_data, wlr_set_init).  The first iterations
+ * after wlr_set_init run on each handle alone (the full-CholeskyQR warm-up and the cold
+ * start of the subspace iteration); after that the iterations of all handles are joined
+ * into one CUDA graph, with one child graph of three iterations per handle and no edges
+ * between handles, and one graph launch advances every problem by three iterations.
+ * Each handle computes exactly what wlr_solve(h, tol, iters, ...) computes with
+ * WLR_STOP_NONE (no stopping test; the objective history is recorded).  Needs
+ * use_graph = 1 on every handle for the joined launches; handles without it run alone.
+ * handles: `count` distinct non-NULL handles (host array, borrowed); count == 0 is a
+ * no-op.  failed_index (may be NULL): index of the handle whose error is returned, -1
+ * if none or if the failure was not tied to one handle (its message is then on
+ * handles[0]).  WLR_ERR_INVALID_ARG for a NULL or repeated handle, count < 0 or
+ * iters < 0; WLR_ERR_NOT_READY when a handle lacks data or init; device errors of a
+ * handle as wlr_step reports them.  Synchronises. */
+wlr_status wlr_solve_batched(wlr_handle* handles, int32_t count, int32_t iters,
+                             int32_t* failed_index);
+
 /* Release the handle and all its device memory.  NULL is accepted. */
 wlr_status wlr_destroy(wlr_handle h);
 

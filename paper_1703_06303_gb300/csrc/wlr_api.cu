@@ -5,6 +5,8 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
+#include <climits>
 
 #include "wlr_solver.cuh"
 
@@ -138,6 +140,124 @@ wlr_status wlr_solve(wlr_handle h, double tol, int32_t max_iter, int32_t* iters_
     if (st == WLR_ERR_NO_CONVERGENCE) h->last_error = "max_iter reached before the stopping rule held";
     return st;
   });
+}
+
+wlr_status wlr_solve_batched(wlr_handle* hs, int32_t count, int32_t iters, int32_t* failed_index) {
+  if (failed_index) *failed_index = -1;
+  if (count < 0 || iters < 0) return fail(nullptr, WLR_ERR_INVALID_ARG, "count and iters must be >= 0");
+  if (count == 0) return WLR_OK;
+  if (!hs) return fail(nullptr, WLR_ERR_INVALID_ARG, "handles must be non-NULL");
+  for (int i = 0; i < count; ++i) {
+    if (!hs[i] || !hs[i]->impl) return fail(nullptr, WLR_ERR_INVALID_ARG, "NULL handle in the batch");
+    for (int j = 0; j < i; ++j)
+      if (hs[j] == hs[i]) return fail(hs[0], WLR_ERR_INVALID_ARG, "a handle appears twice in the batch");
+  }
+  auto at = [&](int i, wlr_status st) {
+    if (failed_index) *failed_index = i;
+    return st;
+  };
+  // warm-up on each handle alone
+  std::vector<int> left(count, iters);
+  std::vector<char> joined(count, 0);
+  for (int i = 0; i < count; ++i) {
+    wlr::SolverBase* s = hs[i]->impl;
+    const wlr_status st = guarded(hs[i], [&] {
+      while (left[i] > 0 && !s->batch_ready()) {
+        s->batch_iterate();
+        --left[i];
+      }
+      joined[i] = s->batch_ready() ? 1 : 0;
+      return WLR_OK;
+    });
+    if (st != WLR_OK) return at(i, st);
+  }
+  int nb = INT32_MAX;
+  for (int i = 0; i < count; ++i)
+    if (joined[i]) nb = std::min(nb, left[i] / 3);
+  if (nb == INT32_MAX) nb = 0;
+  if (nb > 0) {
+    cudaStream_t bs = nullptr;
+    cudaGraph_t parent = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    auto cleanup = [&] {
+      if (bs) cudaStreamSynchronize(bs);
+      cudaGetLastError();
+      if (exec) cudaGraphExecDestroy(exec);
+      if (parent) cudaGraphDestroy(parent);
+      if (bs) cudaStreamDestroy(bs);
+    };
+    auto cuda_fail = [&](cudaError_t e, const char* what) {
+      cleanup();
+      return fail(hs[0], WLR_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    };
+    cudaError_t e = cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(e, "batch stream");
+    e = cudaGraphCreate(&parent, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "batch graph");
+    for (int i = 0; i < count; ++i) {
+      if (!joined[i]) continue;
+      cudaGraph_t g = nullptr;
+      const wlr_status st = guarded(hs[i], [&] {
+        g = hs[i]->impl->batch_capture(3);
+        return WLR_OK;
+      });
+      if (st != WLR_OK) {
+        cleanup();
+        return at(i, st);
+      }
+      cudaGraphNode_t node;
+      e = cudaGraphAddChildGraphNode(&node, parent, nullptr, 0, g);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return cuda_fail(e, "batch graph node");
+    }
+    e = cudaGraphInstantiate(&exec, parent, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "batch graph instantiation");
+    for (int i = 0; i < count; ++i) {
+      if (!joined[i]) continue;
+      const wlr_status st = guarded(hs[i], [&] {
+        hs[i]->impl->batch_enter(bs);
+        return WLR_OK;
+      });
+      if (st != WLR_OK) {
+        cleanup();
+        return at(i, st);
+      }
+    }
+    for (int b = 0; b < nb && e == cudaSuccess; ++b) e = cudaGraphLaunch(exec, bs);
+    if (e != cudaSuccess) return cuda_fail(e, "batch graph launch");
+    for (int i = 0; i < count; ++i) {
+      if (!joined[i]) continue;
+      const wlr_status st = guarded(hs[i], [&] {
+        for (int b = 0; b < nb; ++b) hs[i]->impl->batch_advance(3);
+        hs[i]->impl->batch_leave(bs);
+        return WLR_OK;
+      });
+      left[i] -= 3 * nb;
+      if (st != WLR_OK) {
+        cleanup();
+        return at(i, st);
+      }
+    }
+    e = cudaStreamSynchronize(bs);
+    cudaGraphExecDestroy(exec);
+    exec = nullptr;
+    cudaGraphDestroy(parent);
+    parent = nullptr;
+    cudaStreamDestroy(bs);
+    bs = nullptr;
+    if (e != cudaSuccess) return fail(hs[0], WLR_ERR_CUDA, std::string("batch: ") + cudaGetErrorString(e));
+  }
+  // the rest on each handle alone, then every handle's device-side status
+  for (int i = 0; i < count; ++i) {
+    wlr::SolverBase* s = hs[i]->impl;
+    const wlr_status st = guarded(hs[i], [&] {
+      for (; left[i] > 0; --left[i]) s->batch_iterate();
+      s->batch_finish();
+      return WLR_OK;
+    });
+    if (st != WLR_OK) return at(i, st);
+  }
+  return WLR_OK;
 }
 
 wlr_status wlr_objective(wlr_handle h, double* F_out) {

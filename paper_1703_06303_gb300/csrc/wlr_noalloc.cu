@@ -55,9 +55,14 @@ void* setup_device(int dev, const char** why) {
   const void* fns[] = {(const void*)wlr::row_pass_fn<float>(8), (const void*)wlr::row_pass_fn<float>(16),
                        (const void*)wlr::row_pass_fn<float>(20), (const void*)wlr::row_pass_fn<float>(24),
                        (const void*)wlr::row_pass_fn<float>(32), (const void*)wlr::row_pass_fn<float>(64)};
+  // raise, never lower: the limit is shared with the solver handles of the process
   bool ok = true;
-  for (const void* f : fns)
-    ok = ok && cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, limit) == cudaSuccess;
+  for (const void* f : fns) {
+    cudaFuncAttributes fa;
+    ok = ok && cudaFuncGetAttributes(&fa, f) == cudaSuccess;
+    if (ok && fa.maxDynamicSharedSizeBytes < limit)
+      ok = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, limit) == cudaSuccess;
+  }
   if (!ok) {
     *why = "cudaFuncSetAttribute failed";
     return nullptr;

@@ -59,6 +59,21 @@ class SolverBase {
   virtual void get_state(void* buf) = 0;
   virtual void set_state(const void* buf, int64_t size) = 0;
   virtual std::vector<ProfEntry> profile(int reps) = 0;
+
+  // Batched solve (wlr_solve_batched).  batch_ready: the next iterations replay as a
+  // graph (data and init set, warm-up done).  batch_iterate: one iteration on the handle's
+  // own stream.  batch_capture: n iterations captured into a graph that is not run; the
+  // caller joins the graphs of all handles and launches them.  batch_advance: the host
+  // bookkeeping after one launch of that graph.  batch_enter / batch_leave order the batch
+  // stream after this handle's earlier work and the handle's later work after the batch.
+  // batch_finish: synchronise and raise the handle's device-side errors.
+  virtual bool batch_ready() = 0;
+  virtual void batch_iterate() = 0;
+  virtual cudaGraph_t batch_capture(int n) = 0;
+  virtual void batch_advance(int n) = 0;
+  virtual void batch_enter(cudaStream_t bs) = 0;
+  virtual void batch_leave(cudaStream_t bs) = 0;
+  virtual void batch_finish() = 0;
 };
 
 SolverBase* make_solver_f32(const Dims& d, const wlr_options& o, cudaStream_t user_stream);

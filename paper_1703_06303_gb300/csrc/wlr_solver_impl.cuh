@@ -2,6 +2,7 @@
 // Included by wlr_solver_f32.cu and wlr_solver_f64.cu, one instantiation each.
 #pragma once
 
+#include <mutex>
 #include <algorithm>
 #include <type_traits>
 
@@ -31,6 +32,7 @@ class Solver final : public SolverBase {
     WLR_CUDA(cudaEventCreateWithFlags(&ev_join_, cudaEventDisableTiming));
     WLR_CUDA(cudaEventCreateWithFlags(&ev_in_, cudaEventDisableTiming));
     WLR_CUDA(cudaEventCreateWithFlags(&ev_out_, cudaEventDisableTiming));
+    WLR_CUDA(cudaEventCreateWithFlags(&ev_batch_, cudaEventDisableTiming));
     WLR_CUDA(cudaHostAlloc((void**)&hbuf_, 4096, cudaHostAllocDefault));
     const int m = d_.m, k = d_.k, n2 = d_.n2, s = d_.s, b = d_.b, NP = d_.NP;
     for (int q = 0; q < 3; ++q) X1buf_[q] = dalloc<T>((size_t)m * k);
@@ -122,6 +124,7 @@ class Solver final : public SolverBase {
     if (hbuf_) cudaFreeHost(hbuf_);
     cudaEventDestroy(ev_in_);
     cudaEventDestroy(ev_out_);
+    cudaEventDestroy(ev_batch_);
     cudaStreamDestroy(stream_);
     cudaStreamDestroy(stream2_);
     cudaEventDestroy(ev_fork_);
@@ -513,9 +516,20 @@ class Solver final : public SolverBase {
     allocs_.push_back(p);
     return (U*)p;
   }
+  // The dynamic shared-memory limit is an attribute of the kernel, shared by every handle
+  // of the process: raise it to `bytes` if it is lower, never lower it (a smaller problem
+  // set up after a larger one must not break the larger one's launches).
+  static cudaError_t raise_smem_limit(const void* fn, size_t bytes) {
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lock(mu);
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, fn);
+    if (e != cudaSuccess) return e;
+    if ((size_t)fa.maxDynamicSharedSizeBytes >= bytes) return cudaSuccess;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  }
   static void set_smem(const void* fn, size_t bytes) {
-    if (bytes > 48 * 1024)
-      WLR_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    if (bytes > 48 * 1024) WLR_CUDA(raise_smem_limit(fn, bytes));
   }
   // row chunks for a split-m Gram with `tiles` output tiles: about `target` blocks in
   // all, at most 64 chunks (each chunk is a partial the consumer sums).
@@ -962,7 +976,7 @@ class Solver final : public SolverBase {
         cudaGetLastError();
         continue;
       }
-      if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess) {
+      if (raise_smem_limit(fn, bytes) != cudaSuccess) {
         cudaGetLastError();
         continue;
       }
@@ -1224,6 +1238,60 @@ class Solver final : public SolverBase {
     graphs_.clear();
   }
 
+  // ------------------------------------------------------------------ batched solve
+  bool batch_ready() override {
+    need_init();
+    return o_.use_graph && cd_valid_ && !eig_cold_ && iters_host_ >= kFullQrIters;
+  }
+  void batch_iterate() override {
+    need_init();
+    begin();
+    if (!cd_valid_) compute_cd(cur_, false);
+    iterate_once();
+    end();
+  }
+  cudaGraph_t batch_capture(int n) override {
+    if (!batch_ready()) throw Fail{WLR_ERR_NOT_READY, "handle not warmed up for batched replay"};
+    cudaGraph_t graph = nullptr;
+    const int64_t before = launches_;
+    WLR_CUDA(cudaStreamBeginCapture(stream_, cudaStreamCaptureModeThreadLocal));
+    try {
+      for (int q = 0; q < n; ++q) {
+        const int xi = (cur_ + q) % 3;
+        iteration_body(xi, (xi + 1) % 3, true);
+      }
+    } catch (...) {
+      cudaStreamEndCapture(stream_, &graph);
+      if (graph) cudaGraphDestroy(graph);
+      launches_ = before;
+      throw;
+    }
+    WLR_CUDA(cudaStreamEndCapture(stream_, &graph));
+    batch_launch_count_ = launches_ - before;
+    launches_ = before;
+    return graph;
+  }
+  void batch_advance(int n) override {
+    prev_ = (cur_ + n - 1) % 3;
+    cur_ = (cur_ + n) % 3;
+    iters_host_ += n;
+    launches_ += batch_launch_count_;
+  }
+  void batch_enter(cudaStream_t bs) override {
+    begin();
+    WLR_CUDA(cudaEventRecord(ev_batch_, stream_));
+    WLR_CUDA(cudaStreamWaitEvent(bs, ev_batch_, 0));
+  }
+  void batch_leave(cudaStream_t bs) override {
+    WLR_CUDA(cudaEventRecord(ev_batch_, bs));
+    WLR_CUDA(cudaStreamWaitEvent(stream_, ev_batch_, 0));
+    end();
+  }
+  void batch_finish() override {
+    WLR_CUDA(cudaStreamSynchronize(stream_));
+    raise_err();
+  }
+
   // exact evaluation of the current (and previous) iterate; result sums in e6
   void x2_eval(int xi, int xp, T* out, int64_t ldo, double* e6) {
     const int m = d_.m, k = d_.k, n2 = d_.n2, s = d_.s, NP = d_.NP;
@@ -1242,10 +1310,10 @@ class Solver final : public SolverBase {
   Dims d_;
   wlr_options o_;
   cudaStream_t ustream_ = nullptr, stream_ = nullptr;
-  cudaEvent_t ev_in_ = nullptr, ev_out_ = nullptr;
+  cudaEvent_t ev_in_ = nullptr, ev_out_ = nullptr, ev_batch_ = nullptr;
   unsigned char* hbuf_ = nullptr;
   std::vector<void*> allocs_;
-  int64_t launches_ = 0, graph_launch_count_ = 0;
+  int64_t launches_ = 0, graph_launch_count_ = 0, batch_launch_count_ = 0;
 
   const T* A_ = nullptr;
   int64_t lda_ = 0;

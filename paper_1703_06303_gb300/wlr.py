@@ -50,9 +50,10 @@ class wlr_options(ct.Structure):
 
 
 class WlrError(RuntimeError):
-    def __init__(self, status: int, message: str):
+    def __init__(self, status: int, message: str, index: int = -1):
         super().__init__(f"{status_string(status)}: {message}")
         self.status = status
+        self.index = index   # failing handle of a batched call, -1 otherwise
 
 
 def _load():
@@ -76,6 +77,7 @@ def _load():
         "wlr_get_iteration": (i32, [H, ct.POINTER(i32)]),
         "wlr_get_state": (i32, [H, P, i64, ct.POINTER(i64)]),
         "wlr_set_state": (i32, [H, P, i64]),
+        "wlr_solve_batched": (i32, [ct.POINTER(H), i32, i32, ct.POINTER(i32)]),
         "wlr_destroy": (i32, [H]),
         "wlr_status_string": (ct.c_char_p, [i32]),
         "wlr_last_error": (ct.c_char_p, [H]),
@@ -94,7 +96,8 @@ _lib = _load()
 EXPORTED = (
     "wlr_default_options", "wlr_create", "wlr_set_data", "wlr_set_init", "wlr_step",
     "wlr_solve", "wlr_objective", "wlr_get_result", "wlr_get_factors", "wlr_get_history",
-    "wlr_get_iteration", "wlr_get_state", "wlr_set_state", "wlr_destroy", "wlr_status_string",
+    "wlr_get_iteration", "wlr_get_state", "wlr_set_state", "wlr_solve_batched", "wlr_destroy",
+    "wlr_status_string",
     "wlr_last_error",
     "wlr_kernel_launches", "wlr_profile", "wlr_x1_update_noalloc",
 )
@@ -272,6 +275,27 @@ def wlr_set_state(h, state):
     b = bytes(state)
     buf = ct.create_string_buffer(b, max(len(b), 1))
     _check(_lib.wlr_set_state(h, buf, len(b)), h)
+
+
+def wlr_solve_batched(handles, iters):
+    """`iters` iterations on every handle of the list, joined into one graph launch per
+    three iterations once each handle is warmed up (see include/wlr.h)."""
+    hs = list(handles)
+    arr = (ct.c_void_p * max(len(hs), 1))(*hs)
+    failed = ct.c_int32(-1)
+    st = _lib.wlr_solve_batched(arr, len(hs), int(iters), ct.byref(failed))
+    if st != WLR_OK:
+        h = hs[failed.value] if 0 <= failed.value < len(hs) else (hs[0] if hs and hs[0] else None)
+        msg = _lib.wlr_last_error(h).decode()
+        if not msg and h is not None:
+            msg = _lib.wlr_last_error(None).decode()
+        raise WlrError(st, msg, failed.value)
+    return st
+
+
+def solve_batched(solvers, iters):
+    """wlr_solve_batched over Solver objects."""
+    return wlr_solve_batched([s.h for s in solvers], iters)
 
 
 def wlr_destroy(h):
