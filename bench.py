@@ -50,6 +50,13 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--p-star", type=int, default=0,
                     help="use this iteration count instead of calibrating it (profiling runs)")
+    ap.add_argument("--workload", default="clip160x120",
+                    choices=["clip160x120", "clip320x240", "batched96"],
+                    help="clip160x120: the headline time-to-rel-obj run (default); "
+                         "clip320x240: iterations/s on the 320x240, n=1000, k=50, r=60 clip; "
+                         "batched96: clip-iterations/s of wlr_solve_batched on 96 uneven clips")
+    ap.add_argument("--iters", type=int, default=0,
+                    help="iterations per timed step of the clip320x240 / batched96 workloads")
     return ap.parse_args()
 
 
@@ -201,6 +208,111 @@ def run_reference(a):
                                    f"(+1 warm-up), projected to p*={p_star} iterations"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
+    print(json.dumps(line))
+    return 0
+
+
+# --------------------------------------------------------------------- secondary workloads
+def run_secondary(a):
+    """Throughput of the iteration on the 320x240 clip (k = 50 > 32: the one-warp row
+    systems, the N = 64 tensor-core Gram) or of the batched solve on 96 uneven clips.
+    One timed step = `iters` iterations (every clip); inputs are larger than L2."""
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    import __graft_entry__ as g
+    g.build()
+    from paper_1703_06303_gb300 import synth, wlr
+    stream = torch.cuda.current_stream(dev)
+    sampler = ClockSampler(0)
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
+
+    def load(spec):
+        c = synth.make_clip(spec)
+        tA = torch.from_numpy(np.asfortranarray(c["A"].astype(np.float32))).to(dev)
+        tW = torch.from_numpy(np.asfortranarray(c["W1"].astype(np.float32))).to(dev)
+        sv = wlr.Solver(spec.m, spec.n, spec.k, spec.r, precision=wlr.WLR_PREC_FP32,
+                        stop=wlr.WLR_STOP_NONE, stream=stream)
+        sv.set_data(tA, tW)
+        sv.set_init(wlr.WLR_INIT_A1)
+        sv._keep = (tA, tW)
+        return sv
+
+    def timed(fn):
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / 1e3
+
+    if a.workload == "clip320x240":
+        spec = synth.CONFIGS[3]
+        iters = a.iters or 200
+        sv = load(spec)
+        for _ in range(a.warmup):
+            sv.solve(0.0, iters)
+        sampler.start()
+        l0 = sv.launches()
+        times = [timed(lambda: sv.solve(0.0, iters)) for _ in range(a.steps)]
+        launches = sv.launches() - l0
+        clocks = sampler.stop()
+        t = statistics.mean(times)
+        prof = sv.profile(50)
+        kk = prof.pop("gram_kk_tf32x3", None)
+        prof.pop("reduce_kk", None)
+        tot = sum(v[0] for v in prof.values())
+        line = {"metric": "sWLR iterations per second, FP32 GPU path", "value": iters / t,
+                "unit": "iterations/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+                "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": f"sWLR clip {spec.H}x{spec.W} px, n={spec.n}, k={spec.k}, r={spec.r}",
+                           "m": spec.m, "n": spec.n, "k": spec.k, "r": spec.r,
+                           "iterations_per_step": iters, "ms_per_iteration": t / iters * 1e3,
+                           "l2": "inputs larger than L2 (A is 307 MB)",
+                           "kernel_shares": {kn: {"share": v[0] / tot, "ms_per_launch": v[0] / v[1]}
+                                             for kn, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}},
+                "gpu_launches": launches, "clocks": clocks,
+                "gemm": _gemm_report(kk, prof.get("gram_tf32x3_t"), spec.m, spec.n - spec.k, spec.k,
+                                     peaks, hbm_peak, hbm_src)}
+        sv.close()
+    else:
+        specs = synth.batched_specs(96)
+        iters = a.iters or 30
+        hs = [load(sp) for sp in specs]
+        wlr.solve_batched(hs, 3)           # warm-up iterations, each clip alone
+        for _ in range(a.warmup):
+            wlr.solve_batched(hs, iters)
+        sampler.start()
+        l0 = sum(h.launches() for h in hs)
+        times = [timed(lambda: wlr.solve_batched(hs, iters)) for _ in range(a.steps)]
+        launches = sum(h.launches() for h in hs) - l0
+        clocks = sampler.stop()
+        alone = [timed(lambda: [h.solve(0.0, iters) for h in hs]) for _ in range(max(1, a.steps // 2))]
+        t, ta = statistics.mean(times), statistics.mean(alone)
+        ms = sorted({sp.m for sp in specs})
+        line = {"metric": "clip-iterations per second, wlr_solve_batched, FP32", "value": 96 * iters / t,
+                "unit": "clip-iterations/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+                "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": f"96 uneven clips, m in {ms}, n~U[100,800], k~U[5,40], r=k+U[3,10]",
+                           "iterations_per_step": iters,
+                           "one_clip_at_a_time": {"value": 96 * iters / ta, "ms_per_step": ta * 1e3},
+                           "l2": "inputs larger than L2 (6.4 GB of clips)"},
+                "gpu_launches": launches, "clocks": clocks}
+        for h in hs:
+            h.close()
     print(json.dumps(line))
     return 0
 
@@ -363,6 +475,9 @@ def run_ours(a):
 
     # ---- per-kernel durations (CUDA events on the library's launching stream)
     prof = s.profile(200)
+    # the setup Gram K (timed once by the profile call) is not part of an iteration
+    kk = prof.pop("gram_kk_tf32x3", None)
+    prof.pop("reduce_kk", None)
     tot = sum(v[0] for v in prof.values())
     top = max(prof.items(), key=lambda kv: kv[1][0])
     name, (ms_tot, nl) = top
@@ -432,6 +547,7 @@ def run_ours(a):
         roof = {"bound": None, "kernel": name, "ms_per_launch": ms_launch}
     kernels = {kn: {"share": v[0] / tot, "ms_per_launch": v[0] / v[1], "launches": v[1]}
                for kn, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}
+    gemm = _gemm_report(kk, prof.get("gram_tf32x3_t"), m, n2, k, peaks, hbm_peak, hbm_src)
 
     # ---- CPU baseline (rank 0, N = 1 only)
     cpu = None
@@ -465,6 +581,7 @@ def run_ours(a):
             "gpu_launches": launches,
             "roofline": roof,
             "roofline_row_pass": secondary,
+            "gemm": gemm,
             "cpu_baseline": cpu,
             "clocks": clocks,
         }
@@ -473,6 +590,42 @@ def run_ours(a):
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def _gemm_report(kk, gt, m, n2, k, peaks, hbm_peak, hbm_src):
+    """TFLOP/s of the two tensor-core contractions against the TF32 peak (the measured
+    bf16 peak x the nominal TF32/BF16 ratio 1.1/2.25).
+    kk: (ms, launches) of the setup Gram K = A2^T A2 (3xTF32 on 128 x 64 blocks of the
+    upper triangle); algorithmic flops m n2 (n2 + 1) (the symmetric half), tensor-core
+    flops 3 x 2 m x 128 x 64 per block.  gt: (ms, launches) of the per-iteration
+    Q1^T [Q1 A2] (3xTF32, HBM-bound: it reads the hi/lo copies of A2 and Q1)."""
+    if "bf16_tflops" in peaks:
+        tf32 = peaks["bf16_tflops"] * 1.1 / 2.25
+        src = "measured bf16_tflops x 1.1/2.25 (nominal TF32/BF16)"
+    else:
+        tf32 = 1900.0 * 1.1 / 2.25
+        src = "fallback 1900 bf16 TFLOP/s x 1.1/2.25"
+    out = {"peak_tf32_tflops": tf32, "peak_source": src}
+    if kk:
+        ms = kk[0] / kk[1]
+        nb128, nb64 = -(-n2 // 128), -(-n2 // 64)
+        blocks = sum(nb64 - 2 * bi for bi in range(nb128))
+        f_alg = m * n2 * (n2 + 1)
+        f_mma = 3 * 2 * m * blocks * 128 * 64
+        out["a0_K"] = {"kernel": "gram_kk_tf32x3", "ms": ms, "algorithmic_flops": f_alg,
+                       "tflops": f_alg / ms / 1e9, "frac": f_alg / ms / 1e9 / tf32,
+                       "tensor_flops": f_mma, "tensor_tflops": f_mma / ms / 1e9,
+                       "tensor_frac": f_mma / ms / 1e9 / tf32}
+    if gt:
+        ms = gt[0] / gt[1]
+        f_alg = 2 * m * k * (k + n2)
+        b_ = 8 * m * (n2 + k)
+        out["a2_Q1tQ1A2"] = {"kernel": "gram_tf32x3_t", "ms": ms, "algorithmic_flops": f_alg,
+                             "tflops": f_alg / ms / 1e9, "frac": f_alg / ms / 1e9 / tf32,
+                             "bytes": b_, "gbs": b_ / ms / 1e6, "hbm_frac": b_ / ms / 1e6 / hbm_peak,
+                             "hbm_peak_source": f"{hbm_src} hbm_gbs",
+                             "note": "HBM-bound: 2 k (k + n2) flops per 8 (n2 + k) bytes of a row"}
+    return out
 
 
 def _recorded_traffic():
@@ -504,7 +657,13 @@ def main():
     if a.warmup < 3:
         a.warmup = 3
     if a.impl == "reference":
+        if a.workload != "clip160x120":
+            print(json.dumps({"impl": "reference",
+                              "unavailable": "the oracle is timed on the clip160x120 workload only"}))
+            return 0
         return run_reference(a)
+    if a.workload != "clip160x120":
+        return run_secondary(a)
     return run_ours(a)
 
 

@@ -207,7 +207,8 @@ const char* wlr_status_string(wlr_status s);
 const char* wlr_last_error(wlr_handle h);
 
 /* Measurement aid: run reps further sWLR iterations without CUDA graphs, each kernel
- * bracketed by CUDA events on the handle's stream.  For up to max_kernels distinct
+ * bracketed by CUDA events on the handle's stream, then (reps > 0, FP32) recompute the
+ * setup Gram K = A2^T A2 once the same way (same values).  For up to max_kernels distinct
  * kernels: names ('\n'-separated, NUL-terminated, at most names_cap bytes), total
  * milliseconds and launch counts.  Advances the iterate like wlr_solve.  Synchronises. */
 wlr_status wlr_profile(wlr_handle h, int32_t reps, char* names, int32_t names_cap,

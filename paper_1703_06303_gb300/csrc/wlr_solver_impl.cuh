@@ -482,6 +482,8 @@ class Solver final : public SolverBase {
     o_.use_graph = 0;
     try {
       for (int q = 0; q < reps; ++q) iterate_once();
+      // the setup Gram K = A2^T A2 once more (deterministic: the same K)
+      if (reps > 0 && use_tc_k_) tc_gram_k();
     } catch (...) {
       prof_ = false;
       o_.use_graph = saved_graph;
@@ -861,12 +863,17 @@ class Solver final : public SolverBase {
   // K = A2^T A2 on the tensor cores (3xTF32, from the split copies of A2)
   void tc_gram_k() {
     const int n2 = d_.n2;
-    Prof pf(this, "gram_kk_tf32x3");
-    tc::gram_kk_tf32x3<<<dim3(kk_npairs_, ch_kk_.nch), tc::K_THREADS, tc::K_SMEM_BYTES, stream_>>>(
-        mA2h_, mA2l_, mA2h64_, mA2l64_, d_.m, ch_kk_.rows, kk_pairs_, kk_npairs_, part64_, err_);
-    WLR_CUDA(cudaGetLastError());
-    tc::reduce_kk<<<grid1d((int64_t)kk_npairs_ * tc::K_TILE), 256, 0, stream_>>>(part64_, ch_kk_.nch, kk_pairs_,
-                                                                              kk_npairs_, n2, K64_);
+    {
+      Prof pf(this, "gram_kk_tf32x3");
+      tc::gram_kk_tf32x3<<<dim3(kk_npairs_, ch_kk_.nch), tc::K_THREADS, tc::K_SMEM_BYTES, stream_>>>(
+          mA2h_, mA2l_, mA2h64_, mA2l64_, d_.m, ch_kk_.rows, kk_pairs_, kk_npairs_, part64_, err_);
+      WLR_CUDA(cudaGetLastError());
+    }
+    {
+      Prof pf(this, "reduce_kk");
+      tc::reduce_kk<<<grid1d((int64_t)kk_npairs_ * tc::K_TILE), 256, 0, stream_>>>(part64_, ch_kk_.nch, kk_pairs_,
+                                                                                kk_npairs_, n2, K64_);
+    }
     count(2);
   }
   double* wpart_scratch(int n) {
