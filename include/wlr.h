@@ -178,6 +178,18 @@ wlr_status wlr_get_state(wlr_handle h, void* buf, int64_t cap, int64_t* size_out
  * Synchronises. */
 wlr_status wlr_set_state(wlr_handle h, const void* buf, int64_t size);
 
+/* FP64 refinement sweep: one loop body of Algorithm 1 (Section 3) from the handle's
+ * current X1_p, computed in FP64 whatever the handle's precision (the data widened from
+ * the handle's copy, thin QR by CholeskyQR2 in FP64, the rank-(r-k) truncation from an
+ * eigensolve run until its values stop changing).  Writes X1_{p+1} to X1_out (m x k, FP64,
+ * column-major, leading dimension ldx >= m, device or host memory per mem; NULL: not
+ * written), F_p = F~(X1_p) to F_out and F~(X1_{p+1}) to F_next_out (each may be NULL).
+ * The handle's own iterate, history and iteration count are not changed: the sweep ends
+ * an FP32 solve with FP64 accuracy of the final step.  WLR_ERR_NOT_READY before
+ * wlr_set_init; WLR_ERR_INVALID_ARG for ldx < m.  Synchronises. */
+wlr_status wlr_refine(wlr_handle h, double* X1_out, int64_t ldx, wlr_memory mem, double* F_out,
+                      double* F_next_out);
+
 /* Batched solve: `iters` further iterations of Algorithm 1 (Section 3) on each of `count`
  * independent problems, which may differ in m, n, k, r and precision.  Each handle must
  * hold its data and an initial X1 (wlr_set_data, wlr_set_init).  The first iterations

@@ -260,6 +260,15 @@ wlr_status wlr_solve_batched(wlr_handle* hs, int32_t count, int32_t iters, int32
   return WLR_OK;
 }
 
+wlr_status wlr_refine(wlr_handle h, double* X1_out, int64_t ldx, wlr_memory mem, double* F_out,
+                      double* F_next_out) {
+  return guarded(h, [&] {
+    if (mem != WLR_MEM_DEVICE && mem != WLR_MEM_HOST) throw wlr::Fail{WLR_ERR_INVALID_ARG, "bad memory kind"};
+    h->impl->refine(X1_out, ldx, mem, F_out, F_next_out);
+    return WLR_OK;
+  });
+}
+
 wlr_status wlr_objective(wlr_handle h, double* F_out) {
   return guarded(h, [&] {
     if (!F_out) throw wlr::Fail{WLR_ERR_INVALID_ARG, "F_out must be non-NULL"};

@@ -59,6 +59,7 @@ class SolverBase {
   virtual void get_state(void* buf) = 0;
   virtual void set_state(const void* buf, int64_t size) = 0;
   virtual std::vector<ProfEntry> profile(int reps) = 0;
+  virtual void refine(void* X1_out, int64_t ldx, wlr_memory mem, double* Fp, double* Fnext) = 0;
 
   // Batched solve (wlr_solve_batched).  batch_ready: the next iterations replay as a
   // graph (data and init set, warm-up done).  batch_iterate: one iteration on the handle's

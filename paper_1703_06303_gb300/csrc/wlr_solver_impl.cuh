@@ -265,6 +265,14 @@ class Solver final : public SolverBase {
       return e6[0] + e6[5];
     }
     // FP32 handle: score with an FP64 copy of the problem
+    SolverBase* sc = scorer();
+    // the scorer's stream waits on this stream, so the current X1 is complete
+    sc->set_init(WLR_INIT_USER, X1buf_[cur_], d_.m, dtype_of<T>(), WLR_MEM_DEVICE, 0);
+    return sc->objective_exact();
+  }
+  // An FP64 solver on the same data (widened from T), with the widest subspace block, used
+  // to score iterates exactly and for the refinement sweep.
+  SolverBase* scorer() {
     if (!scorer_) {
       wlr_options so = o_;
       so.precision = WLR_PREC_FP64;
@@ -275,9 +283,22 @@ class Solver final : public SolverBase {
       scorer_ = make_solver_f64(sd, so, stream_);
       scorer_->set_data(A_, lda_, W1_, ldw_, dtype_of<T>(), WLR_MEM_DEVICE);
     }
-    // the scorer's stream waits on this stream, so the current X1 is complete
-    scorer_->set_init(WLR_INIT_USER, X1buf_[cur_], d_.m, dtype_of<T>(), WLR_MEM_DEVICE, 0);
-    return scorer_->objective_exact();
+    return scorer_;
+  }
+  // FP64 refinement sweep: from the current X1_p, the FP64 solver forms C_p and D_p with
+  // the eigensolve run to convergence (F~(X1_p) = F(X1_p, C_p, D_p)), takes one loop body
+  // of Algorithm 1 to X1_{p+1} and scores it the same way.  This handle's state is kept.
+  void refine(void* X1_out, int64_t ldx, wlr_memory mem, double* Fp, double* Fnext) override {
+    need_init();
+    if (X1_out && ldx < d_.m) throw Fail{WLR_ERR_INVALID_ARG, "ldx must be >= m"};
+    SolverBase* sc = scorer();
+    sc->set_init(WLR_INIT_USER, X1buf_[cur_], d_.m, dtype_of<T>(), WLR_MEM_DEVICE, 0);
+    const double F0 = sc->objective_exact();
+    sc->step(nullptr);
+    const double F1 = sc->objective_exact();
+    if (X1_out) sc->get_result(X1_out, ldx, nullptr, 0, WLR_F64, mem);
+    if (Fp) *Fp = F0;
+    if (Fnext) *Fnext = F1;
   }
 
   void get_result(void* X1, int64_t ldx, void* X2, int64_t ldx2, wlr_dtype dt,

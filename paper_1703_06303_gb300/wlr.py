@@ -78,6 +78,7 @@ def _load():
         "wlr_get_state": (i32, [H, P, i64, ct.POINTER(i64)]),
         "wlr_set_state": (i32, [H, P, i64]),
         "wlr_solve_batched": (i32, [ct.POINTER(H), i32, i32, ct.POINTER(i32)]),
+        "wlr_refine": (i32, [H, P, i64, i32, ct.POINTER(dbl), ct.POINTER(dbl)]),
         "wlr_destroy": (i32, [H]),
         "wlr_status_string": (ct.c_char_p, [i32]),
         "wlr_last_error": (ct.c_char_p, [H]),
@@ -96,7 +97,8 @@ _lib = _load()
 EXPORTED = (
     "wlr_default_options", "wlr_create", "wlr_set_data", "wlr_set_init", "wlr_step",
     "wlr_solve", "wlr_objective", "wlr_get_result", "wlr_get_factors", "wlr_get_history",
-    "wlr_get_iteration", "wlr_get_state", "wlr_set_state", "wlr_solve_batched", "wlr_destroy",
+    "wlr_get_iteration", "wlr_get_state", "wlr_set_state", "wlr_solve_batched", "wlr_refine",
+    "wlr_destroy",
     "wlr_status_string",
     "wlr_last_error",
     "wlr_kernel_launches", "wlr_profile", "wlr_x1_update_noalloc",
@@ -293,6 +295,22 @@ def wlr_solve_batched(handles, iters):
     return st
 
 
+def wlr_refine(h, X1_out=None):
+    """FP64 refinement sweep from the current X1_p (see include/wlr.h).  X1_out: float64
+    column-major m x k torch tensor or NumPy array, or None.  Returns (F_p, F_{p+1})."""
+    F0, F1 = ct.c_double(0), ct.c_double(0)
+    if X1_out is None:
+        _check(_lib.wlr_refine(h, None, 0, WLR_MEM_DEVICE, ct.byref(F0), ct.byref(F1)), h)
+    else:
+        if isinstance(X1_out, np.ndarray) and not X1_out.flags.f_contiguous:
+            raise ValueError("X1_out must be column-major (Fortran order)")
+        ptr, ld, dt, mem, _keep = _matrix(X1_out)
+        if dt != WLR_F64:
+            raise TypeError("X1_out must be float64")
+        _check(_lib.wlr_refine(h, ptr, ld, mem, ct.byref(F0), ct.byref(F1)), h)
+    return F0.value, F1.value
+
+
 def solve_batched(solvers, iters):
     """wlr_solve_batched over Solver objects."""
     return wlr_solve_batched([s.h for s in solvers], iters)
@@ -383,6 +401,9 @@ class Solver:
 
     def result(self, X1=None, X2=None):
         return wlr_get_result(self.h, X1, X2)
+
+    def refine(self, X1_out=None):
+        return wlr_refine(self.h, X1_out)
 
     def factors(self):
         return wlr_get_factors(self.h, self.k, self.n - self.k, self.r - self.k)
