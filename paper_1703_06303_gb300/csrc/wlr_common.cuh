@@ -14,6 +14,11 @@ enum : int {
   ERRBIT_EIG = 8,            // the small eigensolver met a non-finite value
 };
 
+// Round to the nearest TF32 number (10 explicit mantissa bits, ties away from zero).
+__device__ __forceinline__ float round_tf32(float x) {
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
+
 __device__ __forceinline__ float  wsqrt(float x)  { return sqrtf(x); }
 __device__ __forceinline__ double wsqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ bool   wfinite(float x)  { return isfinite(x); }

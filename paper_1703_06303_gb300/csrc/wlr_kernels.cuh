@@ -1311,7 +1311,8 @@ struct RowPassSmem {
   template <int KP>
   static size_t bytes_k(int NP, int k, int s) {
     return sizeof(T) * (region0<KP>(NP, k) + (size_t)RP_BM * (NP + 1) + (size_t)k * k +
-                        (size_t)k * (s > 0 ? s : 1) + (kStage ? 3 * (size_t)RP_BM * (k + 1) : 0));
+                        (size_t)k * (s > 0 ? s : 1) + (kStage ? 3 * (size_t)RP_BM * (k + 1) : 0) +
+                        (size_t)k * k);
   }
   static size_t bytes(int NP, int k, int s) {
     switch (row_kp(k)) {
@@ -1323,6 +1324,17 @@ struct RowPassSmem {
       default: return bytes_k<64>(NP, k, s);
     }
   }
+};
+
+// Optional output of row_pass (float, steady state of the tensor-core path): the rows of
+// Q1 = X1new R^{-1} for the next CholeskyQR (R^{-1}: k x k upper triangular, column-major,
+// the previous iteration's factor) as a TF32 pair h + l (h = round_tf32(q),
+// l = round_tf32(q - h)), leading dimension ld.  h == nullptr: not formed.
+struct QSplitOut {
+  float* h;
+  float* l;
+  int64_t ld;
+  const float* R;
 };
 
 // Objective finalisation done by the last row_pass block (ticket != nullptr):
@@ -1470,6 +1482,41 @@ __device__ __forceinline__ void rp_phase1(const T* __restrict__ A2, int64_t lda,
     for (int v = 0; v < NPU; ++v) Ys[(4 * rg + u) * (NP + 1) + cg * NPU + v] = acc[u][v];
 }
 
+// Row i of Q1 = X1new R^{-1} (QSplitOut) from the row's solution, held by a group of LG
+// lanes (lane g: x[sl] = X1new(i, g + LG sl)): q_a = sum_{b <= a} x_b R^{-1}(b, a), summed
+// in the order b = 0, 1, ..., then split into TF32 h + l.
+template <typename T, int KP, int LG, int NS>
+__device__ __forceinline__ void q_split_row(const T (&x)[NS], const T* __restrict__ Rqs, int k, int g,
+                                            bool active, int i, const QSplitOut& qo) {
+  constexpr unsigned FULL = 0xffffffffu;
+  T qa[NS];
+#pragma unroll
+  for (int sl = 0; sl < NS; ++sl) qa[sl] = T(0);
+#pragma unroll
+  for (int bq = 0; bq < KP; ++bq) {
+    if (bq < k) {
+      const T xb = __shfl_sync(FULL, x[bq / LG], bq % LG, LG);
+#pragma unroll
+      for (int sl = 0; sl < NS; ++sl) {
+        const int a = g + LG * sl;
+        if (a < k && bq <= a) qa[sl] = fma(xb, Rqs[bq + a * k], qa[sl]);
+      }
+    }
+  }
+  if (active) {
+#pragma unroll
+    for (int sl = 0; sl < NS; ++sl) {
+      const int a = g + LG * sl;
+      if (a < k) {
+        const float v = (float)qa[sl];
+        const float h = round_tf32(v);
+        qo.h[i + (int64_t)a * qo.ld] = h;
+        qo.l[i + (int64_t)a * qo.ld] = round_tf32(v - h);
+      }
+    }
+  }
+}
+
 // Gauss-Jordan steps t0 <= t < t1 of a row system held by a whole warp (phase 3 of
 // row_pass for KP = 64): lane g holds rows q = g + 32 sl (sl < NS) shifted so that
 // R[sl][jj] = M(q, t + jj) at step t, i.e. the pivot column is always R[sl][0] and the loop
@@ -1526,7 +1573,7 @@ __global__ void __launch_bounds__(256)
 row_pass(const T* __restrict__ A, int64_t lda, const T* __restrict__ W1, int64_t ldw,
          const T* __restrict__ X1old, const T* __restrict__ Z2, const T* __restrict__ Gm,
          const T* __restrict__ CV, int m, int n2, int k, int s, int NP, T* __restrict__ X1new,
-         double* __restrict__ wpart, int* __restrict__ err, FinalizeArgs<T> fin) {
+         double* __restrict__ wpart, int* __restrict__ err, FinalizeArgs<T> fin, QSplitOut qo) {
   extern __shared__ unsigned char smem_raw[];
   constexpr bool kStage = RowPassSmem<T>::kStage;
   T* As = reinterpret_cast<T*>(smem_raw);   // phase-1 stages               (phase 1)
@@ -1538,7 +1585,10 @@ row_pass(const T* __restrict__ A, int64_t lda, const T* __restrict__ W1, int64_t
   T* Xo = CVs + k * (s > 0 ? s : 1);        // [RP_BM][k+1]  X1old rows (float)
   T* A1s = Xo + RP_BM * (k + 1);            // [RP_BM][k+1]  A1 rows    (float)
   T* W1s = A1s + RP_BM * (k + 1);           // [RP_BM][k+1]  W1 rows    (float)
+  T* Rqs = W1s + RP_BM * (k + 1);           // [k][k]        R^{-1} for Q1 (float)
   __shared__ double sh[32];
+  constexpr bool kQ = sizeof(T) == 4;
+  const bool qon = kQ && qo.h != nullptr;
 
   const int tid = threadIdx.x;
   const int i0 = blockIdx.x * RP_BM;
@@ -1563,6 +1613,8 @@ row_pass(const T* __restrict__ A, int64_t lda, const T* __restrict__ W1, int64_t
   // never use them).
   for (int e = tid; e < k * k; e += 256) cp_async_elem(Gs + e, Gm + e, true);
   for (int e = tid; e < k * s; e += 256) cp_async_elem(CVs + e, CV + e, true);
+  if (qon)
+    for (int e = tid; e < k * k; e += 256) cp_async_elem(Rqs + e, reinterpret_cast<const T*>(qo.R) + e, true);
   if (kStage) {
     for (int e = tid; e < RP_BM * k; e += 256) {
       const int r = e % RP_BM, a = e / RP_BM;
@@ -1643,13 +1695,17 @@ row_pass(const T* __restrict__ A, int64_t lda, const T* __restrict__ W1, int64_t
       }
       gj_steps<T, KP, NS, 0>(R, e, rd, 0, min(k, 32), k, g, active, bad);
       gj_steps<T, KP, NS, 1>(R, e, rd, 32, k, k, g, active, bad);
+      T x[NS];
+#pragma unroll
+      for (int sl = 0; sl < NS; ++sl) x[sl] = e[sl] * rd[sl];
       if (active) {
 #pragma unroll
         for (int sl = 0; sl < NS; ++sl) {
           const int q = g + 32 * sl;
-          if (q < k) X1new[(i0 + r) + (int64_t)q * m] = e[sl] * rd[sl];
+          if (q < k) X1new[(i0 + r) + (int64_t)q * m] = x[sl];
         }
       }
+      if (qon) q_split_row<T, KP, 32, NS>(x, Rqs, k, g, active, i0 + r, qo);
     }
   } else if constexpr (RegSolve<T, KP>::on) {
     // Symmetric Gaussian elimination (LDL^T, no square roots) on the system padded to
@@ -1731,6 +1787,7 @@ row_pass(const T* __restrict__ A, int64_t lda, const T* __restrict__ W1, int64_t
           if (q < k) X1new[(i0 + r) + (int64_t)q * m] = x[sl];
         }
       }
+      if (qon) q_split_row<T, KP, LG, NS>(x, Rqs, k, g, active, i0 + r, qo);
     }
   } else {
     // A group of LG lanes factors one row's system in shared memory (lower triangle,
@@ -1843,7 +1900,7 @@ row_pass(const T* __restrict__ A, int64_t lda, const T* __restrict__ W1, int64_t
 // Host-side: the row_pass instantiation for k (see row_kp).
 template <typename T>
 using RowPassFn = void (*)(const T*, int64_t, const T*, int64_t, const T*, const T*, const T*,
-                           const T*, int, int, int, int, int, T*, double*, int*, FinalizeArgs<T>);
+                           const T*, int, int, int, int, int, T*, double*, int*, FinalizeArgs<T>, QSplitOut);
 template <typename T>
 RowPassFn<T> row_pass_fn(int k) {
   switch (row_kp(k)) {

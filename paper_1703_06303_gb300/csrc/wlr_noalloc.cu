@@ -136,7 +136,8 @@ extern "C" wlr_status wlr_x1_update_noalloc(const float* A, int64_t lda, const f
   const size_t smem = wlr::RowPassSmem<float>::bytes(NP, ki, s);
   const wlr::FinalizeArgs<float> nofin{nullptr, 0, nullptr, nullptr, nullptr, 0, nullptr, nullptr, nullptr};
   wlr::row_pass_fn<float>(ki)<<<nblk, 256, smem, st>>>(A, lda, W1, ldw, X1, Z2, G, CV, mi, n2, ki, s, NP,
-                                                      X1_next, wpart, err, nofin);
+                                                      X1_next, wpart, err, nofin,
+                                                      wlr::QSplitOut{nullptr, nullptr, 0, nullptr});
   if (wterm) wlr::reduce_partials<double><<<1, 32, 0, st>>>(wpart, 1, nblk, 1, wterm, nullptr);
   if (status) store_err<<<1, 1, 0, st>>>(err, status);
   if (cudaGetLastError() != cudaSuccess) return fail(WLR_ERR_CUDA, "kernel launch failed");

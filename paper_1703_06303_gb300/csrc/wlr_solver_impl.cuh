@@ -804,10 +804,15 @@ class Solver final : public SolverBase {
   // part64 <- chunk partials of Q1^T [Q1 A2] with Q1 = X1 Rpre (k x (k + n2) per chunk)
   void tc_gram(const T* X1, const T* Rpre, bool fork = false) {
     const int m = d_.m, k = d_.k, n2 = d_.n2;
-    {
+    if (q_from_row_pass_ && Rpre == Rinv_) {
+      // the row pass that made X1 has already written Q1 = X1 Rinv_ (same sums, same order)
+      q_from_row_pass_ = false;
+    } else {
+      q_from_row_pass_ = false;
       Prof pf(this, "form_q_split");
       tc::form_q_split<<<grid1d((int64_t)m * k), 256, sizeof(float) * k * k, stream_>>>(
           (const float*)X1, m, (const float*)Rpre, m, k, Q1h_, Q1l_, ld4_);
+      count(1);
     }
     if (fork) fork_kv();
     {
@@ -821,7 +826,7 @@ class Solver final : public SolverBase {
         tc::gram_tf32x3_t<2 * tc::TN><<<g, tc::t_threads(2 * tc::TN), tc::t_smem_bytes(2 * tc::TN), stream_>>>(
             mQh128_, mQl128_, mA2h_, mA2l_, mQh32_, mQl32_, m, k, k, n2, ch_tc_.rows, part64_, pstride, err_);
     }
-    count(2);
+    count(1);
   }
 
   // ------------------------------------------------------------------ kernels
@@ -1213,8 +1218,13 @@ class Solver final : public SolverBase {
       Prof pf(this, "row_pass");
       FinalizeArgs<T> fin{bpart_, n2 > 0 ? (fuse_front_ ? ds_nc_ : nblk_coef_) : 0, normA2_, theta_, Fhist_, hist_cap_, iter_, Fcur_,
                           fin_ticket_};
+      // steady state on the tensor-core path: the next CholeskyQR's Q1 = X1_{p+1} R_p^{-1}
+      // (R_p^{-1} is final before this pass) is formed by the row pass itself
+      q_from_row_pass_ = steady && use_tc_ && std::is_same<T, float>::value;
+      QSplitOut qo{nullptr, nullptr, 0, nullptr};
+      if (q_from_row_pass_) qo = QSplitOut{Q1h_, Q1l_, ld4_, (const float*)Rinv_};
       row_pass_fn<T>(k)<<<g, 256, smem, stream_>>>(A_, lda_, W1_, ldw_, X1buf_[xi], Z2_, G_, CV_, m, n2, k, s, NP,
-                                                  X1buf_[xo], wpart_, err_, fin);
+                                                  X1buf_[xo], wpart_, err_, fin, qo);
     }
     count(1);
     // keep the factors of X1_p for Error_p
@@ -1375,6 +1385,7 @@ class Solver final : public SolverBase {
   // tensor-core Gram (FP32 path)
   bool use_tc_ = false;     // Q1^T [Q1 A2] on the tensor cores (k <= 32)
   bool use_tc_k_ = false;   // K = A2^T A2 on the tensor cores
+  bool q_from_row_pass_ = false;   // the last row pass wrote Q1 (consumed by tc_gram)
   int tn_ = 32;             // MMA N of the Q1^T [Q1 A2] kernel (32 or 64 columns of Q1)
   int64_t ld4_ = 0;
   size_t part_elems_ = 0;

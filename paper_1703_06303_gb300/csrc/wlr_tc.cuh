@@ -115,9 +115,6 @@ __device__ __forceinline__ void tmem_ld16(unsigned taddr, float (&v)[16]) {
 }
 
 // Nearest TF32 value (10 explicit mantissa bits; ties away from zero) as an FP32 number.
-__device__ __forceinline__ float round_tf32(float x) {
-  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
-}
 
 // x = hi + lo + r with hi = round_tf32(x), lo = round_tf32(x - hi): both parts are exact
 // TF32 numbers, so hi*hi, hi*lo and lo*hi are exact FP32 products inside the MMA and the
