@@ -3,6 +3,8 @@
 #pragma once
 
 #include <mutex>
+#include <vector>
+#include <climits>
 #include <algorithm>
 #include <type_traits>
 
@@ -564,6 +566,48 @@ class Solver final : public SolverBase {
     nch = std::max(1, cdiv(m, rows));
     return {nch, rows};
   }
+  // row chunks for a kernel with `tiles` independent output tiles whose CTAs occupy `slots`
+  // places on the GPU at a time (SMs x CTAs per SM).  The time of the busiest SM is about
+  // waves x (rows per chunk + a pipeline fill of 128 rows); the fewest chunks within 3% of
+  // the best such time are taken (fewer partial sums to add afterwards).
+  static Chunk chunking_waves(int m, int tiles, int slots) {
+    slots = std::max(slots, 1);
+    const int nmax = std::max(1, std::min(128, cdiv(m, 32)));
+    std::vector<std::pair<Chunk, int64_t>> cand;
+    int64_t best_cost = INT64_MAX;
+    for (int n = 1; n <= nmax; ++n) {
+      const int rows = std::max(32, ((cdiv(m, n) + 31) / 32) * 32);
+      const int nn = cdiv(m, rows);
+      const int64_t cost = (int64_t)cdiv(tiles * nn, slots) * (rows + 128);
+      cand.push_back({Chunk{nn, rows}, cost});
+      best_cost = std::min(best_cost, cost);
+    }
+    Chunk pick{0, 0};
+    for (const auto& c : cand)
+      if (c.second == best_cost) {
+        pick = c.first;
+        break;
+      }
+    for (const auto& c : cand)
+      if (c.second * 100 <= best_cost * 103 && c.first.nch < pick.nch) pick = c.first;
+    return pick;
+  }
+  static int sm_count() {
+    int dev = 0, n = 152;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      cudaGetLastError();
+      n = 152;
+    }
+    return n;
+  }
+  static int resident(const void* fn, int threads, size_t smem) {
+    int b = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, threads, smem) != cudaSuccess || b < 1) {
+      cudaGetLastError();
+      b = 1;
+    }
+    return b;
+  }
   static int grid1d(int64_t total) {
     return (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 152 * 16));
   }
@@ -762,14 +806,15 @@ class Solver final : public SolverBase {
       kk_npairs_ = (int)pr.size();
       kk_pairs_ = dalloc<int2>(pr.size());
       WLR_CUDA(cudaMemcpy(kk_pairs_, pr.data(), sizeof(int2) * pr.size(), cudaMemcpyHostToDevice));
-      ch_kk_ = chunking(m, (size_t)kk_npairs_, 152);
+      WLR_CUDA(cudaFuncSetAttribute((const void*)tc::gram_kk_tf32x3, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    tc::K_SMEM_BYTES));
+      ch_kk_ = chunking_waves(m, kk_npairs_,
+                              sm_count() * resident((const void*)tc::gram_kk_tf32x3, tc::K_THREADS, tc::K_SMEM_BYTES));
       const size_t needk = (size_t)ch_kk_.nch * kk_npairs_ * tc::K_TILE;
       if (needk > part_elems_) {
         part64_ = dalloc<double>(needk);
         part_elems_ = needk;
       }
-      WLR_CUDA(cudaFuncSetAttribute((const void*)tc::gram_kk_tf32x3, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    tc::K_SMEM_BYTES));
     }
     use_tc_k_ = true;
     // Q1^T [Q1 A2] each iteration: the transposed kernel takes up to 64 columns of X
@@ -780,18 +825,15 @@ class Solver final : public SolverBase {
     if (!mk(&mQh128_, Q1h_, k, 128) || !mk(&mQl128_, Q1l_, k, 128) || !mk(&mQh32_, Q1h_, k, tn_) ||
         !mk(&mQl32_, Q1l_, k, tn_))
       return;
-    ch_tc_ = chunking(m, (size_t)(1 + cdiv(n2, 128)), 152);
+    const void* gfn = tn_ == tc::TN ? (const void*)tc::gram_tf32x3_t<tc::TN> : (const void*)tc::gram_tf32x3_t<2 * tc::TN>;
+    WLR_CUDA(cudaFuncSetAttribute(gfn, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::t_smem_bytes(tn_)));
+    ch_tc_ = chunking_waves(m, 1 + cdiv(n2, 128),
+                            sm_count() * resident(gfn, tc::t_threads(tn_), tc::t_smem_bytes(tn_)));
     const size_t need = (size_t)ch_tc_.nch * ((size_t)k * k + (size_t)k * n2);
     if (need > part_elems_) {
       part64_ = dalloc<double>(need);
       part_elems_ = need;
     }
-    if (tn_ == tc::TN)
-      WLR_CUDA(cudaFuncSetAttribute((const void*)tc::gram_tf32x3_t<tc::TN>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, tc::t_smem_bytes(tc::TN)));
-    else
-      WLR_CUDA(cudaFuncSetAttribute((const void*)tc::gram_tf32x3_t<2 * tc::TN>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, tc::t_smem_bytes(2 * tc::TN)));
     use_tc_ = true;
   }
   void tc_split_a2() {
