@@ -1587,7 +1587,9 @@ row_pass(const T* __restrict__ A, int64_t lda, const T* __restrict__ W1, int64_t
   T* W1s = A1s + RP_BM * (k + 1);           // [RP_BM][k+1]  W1 rows    (float)
   T* Rqs = W1s + RP_BM * (k + 1);           // [k][k]        R^{-1} for Q1 (float)
   __shared__ double sh[32];
-  constexpr bool kQ = sizeof(T) == 4;
+  // the Q1 output exists in the float row passes with KP <= 32 (for 32 < k <= 64 the one-warp
+  // elimination needs its registers, and a separate split kernel is cheaper)
+  constexpr bool kQ = sizeof(T) == 4 && KP <= 32;
   const bool qon = kQ && qo.h != nullptr;
 
   const int tid = threadIdx.x;
@@ -1705,7 +1707,9 @@ row_pass(const T* __restrict__ A, int64_t lda, const T* __restrict__ W1, int64_t
           if (q < k) X1new[(i0 + r) + (int64_t)q * m] = x[sl];
         }
       }
-      if (qon) q_split_row<T, KP, 32, NS>(x, Rqs, k, g, active, i0 + r, qo);
+      if constexpr (kQ) {
+        if (qon) q_split_row<T, KP, 32, NS>(x, Rqs, k, g, active, i0 + r, qo);
+      }
     }
   } else if constexpr (RegSolve<T, KP>::on) {
     // Symmetric Gaussian elimination (LDL^T, no square roots) on the system padded to
@@ -1787,7 +1791,9 @@ row_pass(const T* __restrict__ A, int64_t lda, const T* __restrict__ W1, int64_t
           if (q < k) X1new[(i0 + r) + (int64_t)q * m] = x[sl];
         }
       }
-      if (qon) q_split_row<T, KP, LG, NS>(x, Rqs, k, g, active, i0 + r, qo);
+      if constexpr (kQ) {
+        if (qon) q_split_row<T, KP, LG, NS>(x, Rqs, k, g, active, i0 + r, qo);
+      }
     }
   } else {
     // A group of LG lanes factors one row's system in shared memory (lower triangle,

@@ -1262,7 +1262,7 @@ class Solver final : public SolverBase {
                           fin_ticket_};
       // steady state on the tensor-core path: the next CholeskyQR's Q1 = X1_{p+1} R_p^{-1}
       // (R_p^{-1} is final before this pass) is formed by the row pass itself
-      q_from_row_pass_ = steady && use_tc_ && std::is_same<T, float>::value;
+      q_from_row_pass_ = steady && use_tc_ && std::is_same<T, float>::value && row_kp(k) <= 32;
       QSplitOut qo{nullptr, nullptr, 0, nullptr};
       if (q_from_row_pass_) qo = QSplitOut{Q1h_, Q1l_, ld4_, (const float*)Rinv_};
       row_pass_fn<T>(k)<<<g, 256, smem, stream_>>>(A_, lda_, W1_, ldw_, X1buf_[xi], Z2_, G_, CV_, m, n2, k, s, NP,
