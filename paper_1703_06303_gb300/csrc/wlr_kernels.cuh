@@ -1517,33 +1517,34 @@ __device__ __forceinline__ void q_split_row(const T (&x)[NS], const T* __restric
   }
 }
 
-// Gauss-Jordan steps t0 <= t < t1 of a row system held by a whole warp (phase 3 of
-// row_pass for KP = 64): lane g holds rows q = g + 32 sl (sl < NS) shifted so that
-// R[sl][jj] = M(q, t + jj) at step t, i.e. the pivot column is always R[sl][0] and the loop
-// body does not depend on t.  The pivot rows of these steps sit in slot ST (lane t - 32 ST).
-// Step t: d_t = M(t,t), and every row q != t (above the pivot too) takes
-// M(q, j) -= M(q,t) M(t,j) / d_t for j > t and e_q -= M(q,t) e_t / d_t, while all rows shift
-// one place left.  After the last step M is diagonal with the pivots d_q of the steps, so
-// x_q = e_q / d_q (rd holds 1 / d_q); no factor has to be kept for a back substitution.
-template <typename T, int KP, int NS, int ST>
+// Gauss-Jordan steps t0 <= t < t1 of a row system held by a group of LG lanes (phase 3 of
+// row_pass): lane g holds rows q = g + LG sl (sl < NS) shifted so that R[sl][jj] =
+// M(q, t + jj) at step t, i.e. the pivot column is always R[sl][0] and the loop body does
+// not depend on t (a rolled loop: the code stays small enough for the instruction cache).
+// The pivot rows of these steps sit in slot ST (lane t - LG ST).  Step t: d_t = M(t,t), and
+// every row q != t (above the pivot too) takes M(q, j) -= M(q,t) M(t,j) / d_t for j > t and
+// e_q -= M(q,t) e_t / d_t, while all rows shift one place left.  After the last step M is
+// diagonal with the pivots d_q of the steps, so x_q = e_q / d_q (rd holds 1 / d_q); no factor
+// has to be kept for a back substitution.
+template <typename T, int KP, int LG, int NS, int ST>
 __device__ __forceinline__ void gj_steps(T (&R)[NS][KP], T (&e)[NS], T (&rd)[NS], int t0, int t1, int k,
                                          int g, bool active, bool& bad) {
   constexpr unsigned FULL = 0xffffffffu;
 #pragma unroll 1
   for (int t = t0; t < t1; ++t) {
-    const int ot = t - 32 * ST;
-    T d = __shfl_sync(FULL, R[ST][0], ot);
+    const int ot = t - LG * ST;
+    T d = __shfl_sync(FULL, R[ST][0], ot, LG);
     if (!(d > T(0)) || !wfinite(d)) {
       bad = bad || active;
       d = T(1);
     }
     const T rdt = wrcp(d);
     if (g == ot) rd[ST] = rdt;
-    const T et = __shfl_sync(FULL, e[ST], ot);
+    const T et = __shfl_sync(FULL, e[ST], ot, LG);
     T f[NS];
 #pragma unroll
     for (int sl = 0; sl < NS; ++sl) {
-      f[sl] = (g + 32 * sl != t) ? R[sl][0] * rdt : T(0);
+      f[sl] = (g + LG * sl != t) ? R[sl][0] * rdt : T(0);
       e[sl] = fma(-f[sl], et, e[sl]);
     }
     // columns t .. k - 1 remain (positions 0 .. rem - 1).  Groups of 8 positions: the 8
@@ -1556,7 +1557,7 @@ __device__ __forceinline__ void gj_steps(T (&R)[NS][KP], T (&e)[NS], T (&rd)[NS]
         T mj[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u)
-          if (j0 + u < KP) mj[u] = __shfl_sync(FULL, R[ST][j0 + u], ot);
+          if (j0 + u < KP) mj[u] = __shfl_sync(FULL, R[ST][j0 + u], ot, LG);
 #pragma unroll
         for (int u = 0; u < 8; ++u)
           if (j0 + u < KP) {
@@ -1565,6 +1566,15 @@ __device__ __forceinline__ void gj_steps(T (&R)[NS][KP], T (&e)[NS], T (&rd)[NS]
           }
       }
     }
+  }
+}
+// All k steps: the pivots of steps LG ST .. LG ST + LG - 1 are in slot ST.
+template <typename T, int KP, int LG, int NS, int ST = 0>
+__device__ __forceinline__ void gj_all(T (&R)[NS][KP], T (&e)[NS], T (&rd)[NS], int k, int g, bool active,
+                                       bool& bad) {
+  if constexpr (ST < NS) {
+    gj_steps<T, KP, LG, NS, ST>(R, e, rd, LG * ST, min(k, LG * (ST + 1)), k, g, active, bad);
+    gj_all<T, KP, LG, NS, ST + 1>(R, e, rd, k, g, active, bad);
   }
 }
 
@@ -1673,18 +1683,19 @@ row_pass(const T* __restrict__ A, int64_t lda, const T* __restrict__ W1, int64_t
   // ---- phase 3: row solves M x = e, M = diag(W1(i,:)^2) + C C^T (symmetric positive
   // definite), e = E(i,:)^T.
   bool bad = false;
-  if constexpr (RegSolve<T, KP>::on && RegSolve<T, KP>::LG == 32) {
-    // one warp per row system, Gauss-Jordan in registers (gj_steps), 8 systems per pass
-    constexpr int NS = RegSolve<T, KP>::NS;
-    const int g = tid & 31, grp = tid >> 5;
+  if constexpr (RegSolve<T, KP>::on) {
+    // Gauss-Jordan in registers (gj_all): LG lanes per row system, 256 / LG systems per pass
+    constexpr int LG = RegSolve<T, KP>::LG, NS = RegSolve<T, KP>::NS;
+    constexpr int GPB = 256 / LG;
+    const int g = tid % LG, grp = tid / LG;
 #pragma unroll 1
-    for (int base = 0; base < RP_BM; base += 8) {
-      const int r = base + grp;
+    for (int base = 0; base < RP_BM; base += GPB) {
+      const int r = base + grp;                    // GPB divides RP_BM: r < RP_BM
       const bool active = i0 + r < m;
       T R[NS][KP], e[NS], rd[NS];
 #pragma unroll
       for (int sl = 0; sl < NS; ++sl) {
-        const int q = g + 32 * sl;
+        const int q = g + LG * sl;
         const bool qk = q < k;
         const T w = (active && qk) ? w1_at(r, q) : T(1);
 #pragma unroll
@@ -1695,95 +1706,10 @@ row_pass(const T* __restrict__ A, int64_t lda, const T* __restrict__ W1, int64_t
         e[sl] = (active && qk) ? Ys[r * (NP + 1) + q] : T(0);
         rd[sl] = T(1);
       }
-      gj_steps<T, KP, NS, 0>(R, e, rd, 0, min(k, 32), k, g, active, bad);
-      gj_steps<T, KP, NS, 1>(R, e, rd, 32, k, k, g, active, bad);
+      gj_all<T, KP, LG, NS>(R, e, rd, k, g, active, bad);
       T x[NS];
 #pragma unroll
       for (int sl = 0; sl < NS; ++sl) x[sl] = e[sl] * rd[sl];
-      if (active) {
-#pragma unroll
-        for (int sl = 0; sl < NS; ++sl) {
-          const int q = g + 32 * sl;
-          if (q < k) X1new[(i0 + r) + (int64_t)q * m] = x[sl];
-        }
-      }
-      if constexpr (kQ) {
-        if (qon) q_split_row<T, KP, 32, NS>(x, Rqs, k, g, active, i0 + r, qo);
-      }
-    }
-  } else if constexpr (RegSolve<T, KP>::on) {
-    // Symmetric Gaussian elimination (LDL^T, no square roots) on the system padded to
-    // KP x KP with an identity block.  Step t: the pivot d_t = M(t,t) and the entries
-    // M(j,t) of column t (j > t) are broadcast from the lanes holding rows t and j; every
-    // row q > t takes M(q,j) -= M(q,t) M(j,t) / d_t for all j > t and
-    // e_q -= M(q,t) e_t / d_t.  Row t is left as it stands after step t - 1, which is row t
-    // of the upper factor U = D L^T, so the back substitution
-    // x_t = (e_t - sum_{j>t} U(t,j) x_j) / d_t reads it from the same registers.
-    constexpr int LG = RegSolve<T, KP>::LG, NS = RegSolve<T, KP>::NS;
-    constexpr int GPB = 256 / LG;                  // row systems per pass
-    constexpr unsigned FULL = 0xffffffffu;
-    const int g = tid % LG, grp = tid / LG;
-#pragma unroll 1
-    for (int base = 0; base < RP_BM; base += GPB) {
-      const int r = base + grp;                    // GPB divides RP_BM: r < RP_BM
-      const bool active = i0 + r < m;
-      T M[NS][KP], e[NS], rd[NS], acc[NS], x[NS];
-#pragma unroll
-      for (int sl = 0; sl < NS; ++sl) {
-        const int q = g + LG * sl;
-        const bool qk = q < k;
-        const T w = (active && qk) ? w1_at(r, q) : T(1);
-        const T dq = qk ? w * w : T(1);
-#pragma unroll
-        for (int j = 0; j < KP; ++j) {
-          const T gv = (qk && j < k) ? Gs[q + j * k] : T(0);
-          M[sl][j] = q == j ? gv + dq : gv;
-        }
-        e[sl] = (active && qk) ? Ys[r * (NP + 1) + q] : T(0);
-        rd[sl] = T(1);
-        acc[sl] = T(0);
-        x[sl] = T(0);
-      }
-#pragma unroll
-      for (int t = 0; t < KP; ++t) {
-        if (t < k) {
-          const int st = t / LG, ot = t % LG;
-          T d = __shfl_sync(FULL, M[st][t], ot, LG);
-          if (!(d > T(0)) || !wfinite(d)) {
-            bad = bad || active;
-            d = T(1);
-          }
-          const T rdt = wrcp(d);
-          if (g == ot) rd[st] = rdt;
-          const T et = __shfl_sync(FULL, e[st], ot, LG);
-          T f[NS];
-#pragma unroll
-          for (int sl = 0; sl < NS; ++sl) {
-            f[sl] = (g + LG * sl > t) ? M[sl][t] * rdt : T(0);
-            e[sl] = fma(-f[sl], et, e[sl]);
-          }
-#pragma unroll
-          for (int j = 1; j < KP; ++j) {
-            if (j > t) {
-              const T mj = __shfl_sync(FULL, M[j / LG][t], j % LG, LG);
-#pragma unroll
-              for (int sl = 0; sl < NS; ++sl) M[sl][j] = fma(-f[sl], mj, M[sl][j]);
-            }
-          }
-        }
-      }
-#pragma unroll
-      for (int tt = 0; tt < KP; ++tt) {
-        const int t = KP - 1 - tt;
-        if (t < k) {
-          const int st = t / LG, ot = t % LG;
-          const T xt = __shfl_sync(FULL, (e[st] - acc[st]) * rd[st], ot, LG);
-          if (g == ot) x[st] = xt;
-#pragma unroll
-          for (int sl = 0; sl < NS; ++sl)
-            acc[sl] = fma((g + LG * sl < t) ? M[sl][t] : T(0), xt, acc[sl]);
-        }
-      }
       if (active) {
 #pragma unroll
         for (int sl = 0; sl < NS; ++sl) {
