@@ -1110,16 +1110,24 @@ class Solver final : public SolverBase {
   // K V of step a3 depends only on the basis V, which nothing changes before the D-step:
   // start it on the side stream next to the Gram kernel of step a1 (one CTA per SM, which
   // leaves room beside it); dstep_run waits for it
+  void keep_prev_factors(cudaStream_t st) {
+    const int k = d_.k, n2 = d_.n2, s = d_.s, NP = d_.NP;
+    if (n2 > 0) WLR_CUDA(cudaMemcpyAsync(Z2prev_, Z2_, sizeof(T) * (size_t)n2 * NP, cudaMemcpyDeviceToDevice, st));
+    if (s > 0) WLR_CUDA(cudaMemcpyAsync(CVprev_, CV_, sizeof(T) * (size_t)k * s, cudaMemcpyDeviceToDevice, st));
+    copies_deferred_ = false;
+  }
   void fork_kv() {
     if (!use_dstep_ || eig_cold_ || prof_ || kv_pending_) return;
     WLR_CUDA(cudaEventRecord(ev_fork_, stream_));
     WLR_CUDA(cudaStreamWaitEvent(stream2_, ev_fork_, 0));
+    if (copies_deferred_) keep_prev_factors(stream2_);
     kv_launch(stream2_);
     WLR_CUDA(cudaEventRecord(ev_join_, stream2_));
     kv_pending_ = true;
   }
   void dstep_run(int q, bool cold, bool front = false) {
     const int n2 = d_.n2, b = d_.b;
+    if (copies_deferred_) keep_prev_factors(stream_);   // not forked after all: copy here
     DstepArgs<T> a = {};
     if constexpr (std::is_same<T, float>::value) {
       a.Bh = Bh_;
@@ -1269,11 +1277,12 @@ class Solver final : public SolverBase {
                                                   X1buf_[xo], wpart_, err_, fin, qo);
     }
     count(1);
-    // keep the factors of X1_p for Error_p
-    if (n2 > 0)
-      WLR_CUDA(cudaMemcpyAsync(Z2prev_, Z2_, sizeof(T) * (size_t)n2 * NP, cudaMemcpyDeviceToDevice, stream_));
-    if (s > 0)
-      WLR_CUDA(cudaMemcpyAsync(CVprev_, CV_, sizeof(T) * (size_t)k * s, cudaMemcpyDeviceToDevice, stream_));
+    // keep the factors of X1_p for Error_p.  When the K V kernel will be started on the
+    // side stream (tensor-core Gram, fused front stage, warm subspace), the copies go there
+    // too, off the critical path: the row pass above was their last reader before them and
+    // the cluster kernel, which joins the side stream, is the next writer of Z2 and CV.
+    copies_deferred_ = use_tc_ && fuse_front_ && use_dstep_ && !eig_cold_ && !prof_ && !kv_pending_;
+    if (!copies_deferred_) keep_prev_factors(stream_);
     compute_cd(xo, true, steady);
   }
 
@@ -1413,6 +1422,7 @@ class Solver final : public SolverBase {
   cudaStream_t stream2_ = nullptr;   // side stream for K V
   cudaEvent_t ev_fork_ = nullptr, ev_join_ = nullptr;
   bool kv_pending_ = false;
+  bool copies_deferred_ = false;   // Z2, CV -> previous-iterate copies left to fork_kv
   bool fuse_front_ = false;  // ... with the second factor and B, C in front (k <= 32)
   const T* front_rpre_ = nullptr;
   int ds_nc_ = 0, ds_ne_ = 1;
