@@ -120,6 +120,7 @@ class Solver final : public SolverBase {
 
   ~Solver() override {
     for (auto& g : graphs_) cudaGraphExecDestroy(g.second);
+    for (auto& g : graphs3_) cudaGraphExecDestroy(g.second);
     for (auto e : ev_pool_) cudaEventDestroy(e);
     if (scorer_) delete scorer_;
     for (void* p : allocs_) cudaFree(p);
@@ -212,6 +213,11 @@ class Solver final : public SolverBase {
     double Fprev = NAN;
     int it = 0;
     for (; it < max_iter; ++it) {
+      if (stop == WLR_STOP_NONE && max_iter - it >= 3 && three_ready()) {
+        iterate_three();
+        it += 2;
+        continue;
+      }
       iterate_once();
       if (stop == WLR_STOP_NONE) continue;
       if (stop == WLR_STOP_OBJECTIVE) {
@@ -1325,6 +1331,27 @@ class Solver final : public SolverBase {
   void graphs_clear() {
     for (auto& g : graphs_) cudaGraphExecDestroy(g.second);
     graphs_.clear();
+    for (auto& g : graphs3_) cudaGraphExecDestroy(g.second);
+    graphs3_.clear();
+  }
+  // Three steady-state iterations (one turn of the X1 buffers) as one CUDA graph, cached
+  // per starting buffer: fewer graph launches when nothing is read back between iterations.
+  bool three_ready() const { return o_.use_graph && cd_valid_ && !eig_cold_ && iters_host_ >= kFullQrIters && !prof_; }
+  void iterate_three() {
+    auto it = graphs3_.find(cur_);
+    if (it == graphs3_.end()) {
+      cudaGraph_t graph = batch_capture(3);
+      cudaGraphExec_t exec;
+      const cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      WLR_CUDA(e);
+      graph3_launch_count_ = batch_launch_count_;
+      it = graphs3_.emplace(cur_, exec).first;
+    }
+    WLR_CUDA(cudaGraphLaunch(it->second, stream_));
+    prev_ = (cur_ + 2) % 3;
+    iters_host_ += 3;
+    launches_ += graph3_launch_count_;
   }
 
   // ------------------------------------------------------------------ batched solve
@@ -1464,6 +1491,8 @@ class Solver final : public SolverBase {
   void* stage2_ = nullptr;
   size_t stage2_bytes_ = 0;
   std::map<int, cudaGraphExec_t> graphs_;
+  std::map<int, cudaGraphExec_t> graphs3_;   // three iterations from X1 buffer key
+  int64_t graph3_launch_count_ = 0;
   SolverBase* scorer_ = nullptr;
   struct ProfRec {
     const char* name;
