@@ -18,7 +18,7 @@ Notation (Section 1 and Section 3 of the paper):
   r = target rank, s = r - k = rank budget of D.
   F(X1, C, D) = ||(A1 - X1) o W1||_F^2 + ||A2 - X1 C - D||_F^2      (Eq. 8)
 
-Readings of the paper taken here (each also listed in the design doc):
+Readings of the paper taken here (the CUDA path takes the same ones):
   * The gradient in Section 3 is written F(X1, C_p, B_p): B_p is read as D_p.
   * The row update "sequentially along each row" uses E_p computed before the
     loop (Algorithm 1), so the m rows are independent (Jacobi-style update).
