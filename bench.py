@@ -213,6 +213,21 @@ def run_reference(a):
     return 0
 
 
+# --------------------------------------------------------------------- replicas (N > 1)
+def replica_seed(base_seed: int, rank: int) -> int:
+    """Seed of the clip that rank `rank` solves: independent replicas, one clip per rank."""
+    return base_seed + 1000 * rank
+
+
+def max_over_ranks(value: float, device) -> float:
+    """The largest `value` over all ranks of the process group (the slowest rank's time)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # --------------------------------------------------------------------- secondary workloads
 def run_secondary(a):
     """Throughput of the iteration on the 320x240 clip (k = 50 > 32: the one-warp row
@@ -342,7 +357,7 @@ def run_ours(a):
 
     spec, cfg = _workload()
     # each rank solves its own clip (independent replicas: no data-path collective)
-    clip = synth.make_clip(spec, seed=spec.seed + 1000 * rank)
+    clip = synth.make_clip(spec, seed=replica_seed(spec.seed, rank))
     A32 = np.asfortranarray(clip["A"].astype(np.float32))
     W32 = np.asfortranarray(clip["W1"].astype(np.float32))
     tA = torch.from_numpy(A32).to(dev)
@@ -447,9 +462,7 @@ def run_ours(a):
     clocks = sampler.stop()
     t_step = statistics.mean(times)
     if world > 1:
-        tt = torch.tensor([t_step], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_step = float(tt.item())
+        t_step = max_over_ranks(t_step, dev)
 
     # ---- e2e: host buffers through the C ABI (pinned), copies inside the timed region
     hA = torch.from_numpy(A32).pin_memory()
