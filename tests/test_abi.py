@@ -65,6 +65,22 @@ def test_status_strings_and_host_validation(lib):
     assert e.value.status == lib.WLR_ERR_UNSUPPORTED
 
 
+def test_batched_and_refine_host_validation(lib):
+    import ctypes as ct
+    # empty batch: nothing to do; negative counts and iteration numbers are refused before
+    # any device call, as are a NULL handle array and NULL handles
+    assert lib.wlr_solve_batched([], 5) == lib.WLR_OK
+    failed = ct.c_int32(7)
+    assert lib._lib.wlr_solve_batched(None, -1, 3, ct.byref(failed)) == lib.WLR_ERR_INVALID_ARG
+    assert failed.value == -1
+    assert lib._lib.wlr_solve_batched(None, 2, 3, ct.byref(failed)) == lib.WLR_ERR_INVALID_ARG
+    arr = (ct.c_void_p * 2)(None, None)
+    assert lib._lib.wlr_solve_batched(arr, 2, 3, None) == lib.WLR_ERR_INVALID_ARG
+    assert lib._lib.wlr_solve_batched(arr, 0, -4, None) == lib.WLR_ERR_INVALID_ARG
+    F0, F1 = ct.c_double(0), ct.c_double(0)
+    assert lib._lib.wlr_refine(None, None, 0, 0, ct.byref(F0), ct.byref(F1)) == lib.WLR_ERR_INVALID_ARG
+
+
 def test_no_oracle_import_in_product_code():
     # the product package never imports the oracle
     pkg = os.path.join(ROOT, "paper_1703_06303_gb300")
