@@ -584,6 +584,7 @@ def run_ours(a):
                     "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                     "step": "set_data (setup: ||A2||^2, K=A2^T A2) + set_init(A1) + p* iterations",
                     "seconds_per_iteration": t_step / max(p_star, 1),
+                    "step_seconds": times, "e2e_step_seconds": e2e_times,
                     "kernel_shares": kernels})
         line = {
             "metric": METRIC, "value": t_step, "unit": UNIT, "n_gpus": world, "steps": a.steps,
