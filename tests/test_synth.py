@@ -39,3 +39,16 @@ def test_batched_specs():
 def test_initial_x1_deterministic():
     a = synth.initial_x1(100, 4, 3)
     assert a.shape == (100, 4) and np.array_equal(a, synth.initial_x1(100, 4, 3))
+
+
+def test_batched_specs_ranges_and_determinism():
+    from paper_1703_06303_gb300 import synth
+    a = synth.batched_specs(96)
+    b = synth.batched_specs(96)
+    assert a == b                                   # same seeds, same workload
+    assert len(a) == 96 and len({sp.seed for sp in a}) == 96
+    assert {sp.m for sp in a} <= {4800, 19200, 76800}
+    for sp in a:
+        assert 100 <= sp.n <= 800 and 5 <= sp.k <= 40 and 3 <= sp.r - sp.k <= 10
+        assert sp.k <= 64 and sp.r - sp.k <= 32      # within what the library accepts
+    assert synth.batched_specs(96, base_seed=7) != a
