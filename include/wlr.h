@@ -86,7 +86,8 @@ typedef struct {
                           /* 0 = min(n-k, 32, max(r-k+8, 2(r-k)))                      */
   int32_t eig_iters;      /* subspace iterations per sWLR iteration (warm start); 0 = 1 */
   int32_t eig_iters_cold; /* subspace iterations from a cold start; 0 = 40              */
-  int32_t use_graph;      /* capture one iteration in a CUDA graph and replay it (1)    */
+  int32_t use_graph;      /* replay steady-state iterations as CUDA graphs (1): one     */
+                          /* iteration per launch, three in wlr_solve with WLR_STOP_NONE */
   uint64_t seed;          /* seed of the random subspace start (and WLR_INIT_RANDOM)     */
 } wlr_options;
 
