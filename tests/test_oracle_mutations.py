@@ -79,3 +79,86 @@ def test_planted_mistake_is_caught(name, monkeypatch):
         except (AssertionError, np.linalg.LinAlgError, ValueError):
             failed.append(pin.__name__)
     assert failed, f"no pin caught the planted mistake '{name}'"
+
+
+# ---------------------------------------------------------------- warm-start oracle
+import oracle.warmstart as ws  # noqa: E402
+from tests import test_oracle_warmstart as wpins  # noqa: E402
+
+
+def _grad_sign(Y, V):
+    return -ws._orig["projector_distance_grad"](Y, V)
+
+
+def _grad_no_gram_inverse(Y, V):
+    PY = Y @ np.linalg.solve(Y.T @ Y, Y.T)
+    return -4.0 * (np.eye(Y.shape[0]) - PY) @ (V @ V.T) @ Y
+
+
+def _upsample_no_half_pixel(U, h, w, f):
+    hw, r = U.shape
+    H, W = f * h, f * w
+    yi = np.minimum(np.arange(H) / f, h - 1.0)
+    xi = np.minimum(np.arange(W) / f, w - 1.0)
+    y0, x0 = np.floor(yi).astype(int), np.floor(xi).astype(int)
+    y1, x1 = np.minimum(y0 + 1, h - 1), np.minimum(x0 + 1, w - 1)
+    ty, tx = yi - y0, xi - x0
+    maps = U.T.reshape(r, h, w)
+    top = (1 - tx) * maps[:, y0][:, :, x0] + tx * maps[:, y0][:, :, x1]
+    bot = (1 - tx) * maps[:, y1][:, :, x0] + tx * maps[:, y1][:, :, x1]
+    return ((1 - ty)[None, :, None] * top + ty[None, :, None] * bot).reshape(r, H * W).T
+
+
+def _downsample_first_pixel(A, H, W, f):
+    m, n = A.shape
+    return A.T.reshape(n, H // f, f, W // f, f)[:, :, 0, :, 0].reshape(n, -1).T
+
+
+def _warm_start_unnormalised(A1, U):
+    return U @ (U.T @ A1)
+
+
+def _mlp_backward_no_relu_mask(params, pre, dY):
+    grads = [None] * len(params)
+    g = dY
+    for li in range(len(params) - 1, -1, -1):
+        h_in, _ = pre[li]
+        Wl, _ = params[li]
+        grads[li] = (g.T @ h_in, g.sum(axis=0))
+        g = g @ Wl
+    return grads, g
+
+
+WS_MUTATIONS = {
+    "loss gradient sign": ("projector_distance_grad", _grad_sign),
+    "loss gradient without (Y^T Y)^-1": ("projector_distance_grad", _grad_no_gram_inverse),
+    "upsampling without half-pixel centres": ("upsample_bilinear", _upsample_no_half_pixel),
+    "downsampling by the first pixel": ("downsample_frames", _downsample_first_pixel),
+    "projection without orthonormal basis": ("warm_start_x1", _warm_start_unnormalised),
+    "backward without the relu mask": ("mlp_backward", _mlp_backward_no_relu_mask),
+}
+
+WS_PINS = [
+    wpins.test_downsample_block_means,
+    wpins.test_upsample_exact_on_affine_maps_away_from_the_border,
+    wpins.test_down_then_up_keeps_constant_frames,
+    wpins.test_warm_start_projection_identities,
+    wpins.test_projector_distance_closed_forms,
+    lambda: wpins.test_projector_distance_gradient_central_differences(4),
+    wpins.test_mlp_gradients_central_differences,
+]
+
+
+@pytest.mark.parametrize("name", sorted(WS_MUTATIONS))
+def test_planted_warm_start_mistake_is_caught(name, monkeypatch):
+    attr, fn = WS_MUTATIONS[name]
+    monkeypatch.setattr(ws, "_orig", {a: getattr(ws, a) for a, _ in WS_MUTATIONS.values()}, raising=False)
+    monkeypatch.setattr(ws, attr, fn)
+    caught = 0
+    for pin in WS_PINS:
+        try:
+            with np.errstate(all="ignore"):
+                pin()
+        except AssertionError:
+            caught += 1
+    assert caught, f"no pin caught the planted mistake '{name}'"
