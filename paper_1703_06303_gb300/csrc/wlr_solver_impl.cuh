@@ -706,6 +706,16 @@ class Solver final : public SolverBase {
                                stream_));
   }
 
+  // replace a device buffer of this handle by a larger one (the old contents are dropped)
+  template <typename U>
+  U* dregrow(U* old, size_t n) {
+    if (old) {
+      WLR_CUDA(cudaStreamSynchronize(stream_));
+      allocs_.erase(std::find(allocs_.begin(), allocs_.end(), (void*)old));
+      cudaFree(old);
+    }
+    return dalloc<U>(n);
+  }
   void* staging(size_t bytes) {
     if (bytes > stage_bytes_) {
       if (stage_) {
@@ -779,7 +789,7 @@ class Solver final : public SolverBase {
                               sm_count() * resident((const void*)tc::gram_kk_tf32x3, tc::K_THREADS, tc::K_SMEM_BYTES));
       const size_t needk = (size_t)ch_kk_.nch * kk_npairs_ * tc::K_TILE;
       if (needk > part_elems_) {
-        part64_ = dalloc<double>(needk);
+        part64_ = dregrow(part64_, needk);
         part_elems_ = needk;
       }
     }
@@ -798,7 +808,7 @@ class Solver final : public SolverBase {
                             sm_count() * resident(gfn, tc::t_threads(tn_), tc::t_smem_bytes(tn_)));
     const size_t need = (size_t)ch_tc_.nch * ((size_t)k * k + (size_t)k * n2);
     if (need > part_elems_) {
-      part64_ = dalloc<double>(need);
+      part64_ = dregrow(part64_, need);
       part_elems_ = need;
     }
     use_tc_ = true;
