@@ -241,8 +241,9 @@ wlr_status wlr_profile(wlr_handle h, int32_t reps, char* names, int32_t names_ca
  * X1_{p+1}(i,:) = E(i,:) (diag(W1(i,:)^2) + C C^T)^{-1},
  * E = A1 o W1 o W1 + (A2 - D) C^T, D = (P_perp A2) V_s V_s^T, i.e. the same values as
  * the X1 step of wlr_step.  All pointers are FP32 device pointers except wterm
- * (device double: ||(A1 - X1_p) o W1||_F^2, may be NULL) and status (device int: 0, or
- * 4 = WLR_ERR_NOT_SPD if a row system broke down; may be NULL).  Work is queued on
+ * (device double: ||(A1 - X1_p) o W1||_F^2, may be NULL) and status (device int, a
+ * wlr_status code: WLR_OK, or WLR_ERR_NOT_SPD if a row system broke down, e.g. through a
+ * non-finite weight, which this call does not check; may be NULL).  Work is queued on
  * cuda_stream (a cudaStream_t, NULL = the legacy default stream); the call does not
  * synchronise.
  *
@@ -258,7 +259,9 @@ wlr_status wlr_profile(wlr_handle h, int32_t reps, char* names, int32_t names_ca
  * there, so calls whose GPU work overlaps (on different streams, or from different
  * threads) race: serialise them.
  * Returns WLR_ERR_INVALID_ARG (NULL pointer, shapes as in wlr_create, lda or ldw < m),
- * WLR_ERR_UNSUPPORTED (k > 64, r - k > 32, or the scratch rule above), WLR_ERR_CUDA. */
+ * WLR_ERR_UNSUPPORTED (k > 64, r - k > 32, or the scratch rule above), WLR_ERR_CUDA; the
+ * reason of a refusal is then in wlr_last_error(NULL).  With n = k (no unweighted frames)
+ * C and Vs may be NULL. */
 wlr_status wlr_x1_update_noalloc(const float* A, int64_t lda, const float* W1, int64_t ldw,
                                  const float* X1, int64_t m, int64_t n, int64_t k, int64_t r,
                                  const float* C, const float* Vs, float* X1_next,

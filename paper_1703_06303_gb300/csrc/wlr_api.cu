@@ -17,6 +17,14 @@ struct wlr_handle_s {
 
 namespace {
 thread_local std::string g_create_error;
+}  // namespace
+
+namespace wlr {
+// Message for wlr_last_error(NULL): failures of calls that have no handle.
+void set_global_error(const char* msg) { g_create_error = msg ? msg : ""; }
+}  // namespace wlr
+
+namespace {
 
 wlr_status fail(wlr_handle h, wlr_status st, const std::string& msg) {
   if (h) h->last_error = msg;

@@ -14,6 +14,9 @@ enum : int {
   ERRBIT_EIG = 8,            // the small eigensolver met a non-finite value
 };
 
+// Host: set the message that wlr_last_error(NULL) returns (calls without a handle).
+void set_global_error(const char* msg);
+
 // Round to the nearest TF32 number (10 explicit mantissa bits, ties away from zero).
 __device__ __forceinline__ float round_tf32(float x) {
   return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);

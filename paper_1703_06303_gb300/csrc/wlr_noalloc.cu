@@ -39,7 +39,12 @@ __global__ void pack_z2(const float* __restrict__ C, const float* __restrict__ V
   }
 }
 
-__global__ void store_err(const int* __restrict__ err, int* __restrict__ out) { *out = *err; }
+// The caller's status word gets a wlr_status code, not the kernels' error bits: the row
+// pass can only report a row system that broke down (WLR_ERR_NOT_SPD).
+__global__ void store_err(const int* __restrict__ err, int* __restrict__ out) {
+  const int e = *err;
+  *out = (e & wlr::ERRBIT_NOT_SPD) ? (int)WLR_ERR_NOT_SPD : (e != 0 ? (int)WLR_ERR_CUDA : (int)WLR_OK);
+}
 
 // First call on the current device: find the scratch array's device address and allow
 // the row-pass kernels their dynamic shared memory.  Returns nullptr on failure.
@@ -72,8 +77,11 @@ void* setup_device(int dev, const char** why) {
   return p;
 }
 
-// The status code is the whole report; the message documents the reason in the source.
-wlr_status fail(wlr_status st, const char* /*msg*/) { return st; }
+// The reason goes where wlr_last_error(NULL) reads it (this entry point has no handle).
+wlr_status fail(wlr_status st, const char* msg) {
+  wlr::set_global_error(msg);
+  return st;
+}
 
 
 // Bytes of scratch a problem needs (each piece padded to 256 bytes).
@@ -141,5 +149,6 @@ extern "C" wlr_status wlr_x1_update_noalloc(const float* A, int64_t lda, const f
   if (wterm) wlr::reduce_partials<double><<<1, 32, 0, st>>>(wpart, 1, nblk, 1, wterm, nullptr);
   if (status) store_err<<<1, 1, 0, st>>>(err, status);
   if (cudaGetLastError() != cudaSuccess) return fail(WLR_ERR_CUDA, "kernel launch failed");
+  wlr::set_global_error("");
   return WLR_OK;
 }

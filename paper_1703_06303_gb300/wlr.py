@@ -355,18 +355,36 @@ def wlr_x1_update_noalloc(A, W1, X1, k, r, C, Vs, X1_next, wterm=None, status=No
     px, ldx, dtx, memx, _ = _matrix(X1)
     pn, ldn, dtn, memn, _ = _matrix(X1_next)
     m, n = A.shape
+    k, r = int(k), int(r)
+    n2, s = n - k, r - k
     if {dta, dtw, dtx, dtn} != {WLR_F32} or {mema, memw, memx, memn} != {WLR_MEM_DEVICE}:
         raise ValueError("float32 device tensors only")
+    if tuple(X1.shape) != (m, k) or tuple(X1_next.shape) != (m, k) or tuple(W1.shape) != (m, k):
+        raise ValueError("W1, X1 and X1_next must be m x k")
     if ldx != m or ldn != m:
         raise ValueError("X1 and X1_next need leading dimension m")
-    pc = C.data_ptr() if C is not None and C.numel() else None
-    pv = Vs.data_ptr() if Vs is not None and Vs.numel() else None
-    st = _lib.wlr_x1_update_noalloc(pa, lda, pw, ldw, px, m, n, int(k), int(r), pc, pv, pn,
+
+    def factor(t, rows, cols, name):
+        # column-major float32 device matrix rows x cols with leading dimension rows
+        if rows * cols == 0:
+            return None
+        if t is None:
+            raise ValueError(f"{name} is required")
+        p, ld, dt, mem, _ = _matrix(t)
+        if dt != WLR_F32 or mem != WLR_MEM_DEVICE:
+            raise ValueError(f"{name} must be a float32 device tensor")
+        if tuple(t.shape) != (rows, cols) or ld != rows:
+            raise ValueError(f"{name} must be {rows} x {cols}, column-major with leading dimension {rows}")
+        return p
+
+    pc = factor(C, k, n2, "C")
+    pv = factor(Vs, n2, s, "Vs")
+    st = _lib.wlr_x1_update_noalloc(pa, lda, pw, ldw, px, m, n, k, r, pc, pv, pn,
                                     wterm.data_ptr() if wterm is not None else None,
                                     status.data_ptr() if status is not None else None,
                                     _stream_ptr(stream))
     if st != WLR_OK:
-        raise WlrError(st, "wlr_x1_update_noalloc")
+        raise WlrError(st, "wlr_x1_update_noalloc: " + _lib.wlr_last_error(None).decode())
     return st
 
 
