@@ -23,6 +23,26 @@ constant and affine images; the projection is idempotent, equals A1 when span(U)
 columns, and does not depend on the basis of span(U); the projector distance has the closed
 form 2 sin^2(theta) for one dimension, is invariant under Y -> Y M, vanishes exactly on
 equal spans and equals 2r - 2 ||Q^T V||_F^2; both gradients match central differences.
+The network of the warm start (per clip: n frames, k weighted, rank r <= r_max):
+  * prepare_input:       per frame two h x w channels: the frame's block means divided by
+                         the clip's RMS, and the mean of W1's k columns (block means)
+                         divided by its own mean;
+  * conv3x3s2_forward /  3 x 3 convolution (cross-correlation), stride 2, zero padding 1,
+    conv3x3s2_backward:  plus bias; output ceil(h/2) x ceil(w/2);
+  * net_forward /        relu(conv1) -> relu(conv2) -> flattened features f_j of frame j;
+    net_backward:        z_j = [f_j | mean of f over the frames of j's clip] -> relu(fc1)
+                         -> fc2 -> omega_j (r_max numbers): the row j of the frame-mixing
+                         matrix Omega (n x r_max) of the clip;
+  * omega_loss:          the clip's predicted basis is Y = A Omega[:, :r] (full resolution,
+                         m x r); loss = ||P_Y - P_V||_F^2 / (2 r) with V the converged
+                         solution's left singular subspace; gradient d/dOmega = A^T dL/dY;
+  * warm_start_x1_weighted: X1_0(:, a) = U (U^T D_a U)^{-1} U^T D_a A1(:, a), D_a =
+                         diag(W1(:, a)^2): the weighted least-squares fit of each weighted
+                         frame inside span(U) (the minimiser of the first term of Eq. 5 over
+                         X1 with columns in span(U));
+  * round_bf16, adam_step: the weight storage (round to nearest even, 8 mantissa bits) and
+                         the optimiser (Kingma & Ba, ICLR 2015, Algorithm 1).
+
 Parity unpinned: what a trained network predicts (its worth is measured by the
 iterations of Algorithm 1 it saves, not by a closed form).
 """
@@ -31,7 +51,9 @@ from __future__ import annotations
 import numpy as np
 
 __all__ = ["downsample_frames", "upsample_bilinear", "warm_start_x1", "projector_distance",
-           "projector_distance_grad", "mlp_init", "mlp_forward", "mlp_backward"]
+           "projector_distance_grad", "mlp_init", "mlp_forward", "mlp_backward",
+           "prepare_input", "conv3x3s2_forward", "conv3x3s2_backward", "net_init", "net_forward",
+           "net_backward", "omega_loss", "warm_start_x1_weighted", "round_bf16", "adam_step"]
 
 
 def downsample_frames(A: np.ndarray, H: int, W: int, f: int) -> np.ndarray:
@@ -122,3 +144,148 @@ def mlp_backward(params, pre, dY: np.ndarray):
         grads[li] = (g.T @ h_in, g.sum(axis=0))
         g = g @ Wl
     return grads, g
+
+
+# ----------------------------------------------------------------- the warm-start network
+def prepare_input(A: np.ndarray, W1: np.ndarray, H: int, W: int, f: int) -> np.ndarray:
+    """Network input of one clip, shape (n, 2, h, w): channel 0 holds each frame's f x f
+    block means divided by the RMS of all of them; channel 1 the block means of the
+    per-pixel mean of W1 over its k columns, divided by their mean (same for every frame)."""
+    n = A.shape[1]
+    h, w = H // f, W // f
+    a = downsample_frames(A, H, W, f)                         # (h w) x n
+    a = a / np.sqrt(np.mean(a * a))
+    wm = downsample_frames(np.mean(W1, axis=1, keepdims=True), H, W, f)[:, 0]
+    wm = wm / np.mean(wm)
+    X = np.empty((n, 2, h, w))
+    X[:, 0] = a.T.reshape(n, h, w)
+    X[:, 1] = wm.reshape(h, w)[None]
+    return X
+
+
+def conv3x3s2_forward(X: np.ndarray, Wc: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """Z[f, o, y, x] = b[o] + sum_{c, u, v} Wc[o, c, u, v] X[f, c, 2y + u - 1, 2x + v - 1],
+    X read as zero outside its h x w; Z is (F, O, ceil(h/2), ceil(w/2))."""
+    F, C, h, w = X.shape
+    ho, wo = (h + 1) // 2, (w + 1) // 2
+    Xp = np.zeros((F, C, h + 2, w + 2))
+    Xp[:, :, 1:h + 1, 1:w + 1] = X
+    Z = np.zeros((F, Wc.shape[0], ho, wo)) + b[None, :, None, None]
+    for u in range(3):
+        for v in range(3):
+            patch = Xp[:, :, u:u + 2 * ho:2, v:v + 2 * wo:2]   # X[2y + u - 1, 2x + v - 1]
+            Z += np.einsum("oc,fcyx->foyx", Wc[:, :, u, v], patch)
+    return Z
+
+
+def conv3x3s2_backward(X: np.ndarray, Wc: np.ndarray, dZ: np.ndarray):
+    """Gradients (dX, dWc, db) of a loss with dL/dZ = dZ for Z = conv3x3s2_forward(X, Wc, b)."""
+    F, C, h, w = X.shape
+    ho, wo = dZ.shape[2], dZ.shape[3]
+    Xp = np.zeros((F, C, h + 2, w + 2))
+    Xp[:, :, 1:h + 1, 1:w + 1] = X
+    dXp = np.zeros_like(Xp)
+    dW = np.zeros_like(Wc)
+    for u in range(3):
+        for v in range(3):
+            patch = Xp[:, :, u:u + 2 * ho:2, v:v + 2 * wo:2]
+            dW[:, :, u, v] = np.einsum("foyx,fcyx->oc", dZ, patch)
+            dXp[:, :, u:u + 2 * ho:2, v:v + 2 * wo:2] += np.einsum("oc,foyx->fcyx", Wc[:, :, u, v], dZ)
+    return dXp[:, :, 1:h + 1, 1:w + 1], dW, dZ.sum(axis=(0, 2, 3))
+
+
+def net_init(h: int, w: int, c1: int, c2: int, hidden: int, r_max: int, seed: int):
+    """Parameters [(Wc1, b1), (Wc2, b2), (W3, b3), (W4, b4)]: weights N(0, 2 / fan_in),
+    biases 0; conv weights (out, in, 3, 3), fc weights (out, in)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    h2, w2 = ((h + 1) // 2 + 1) // 2, ((w + 1) // 2 + 1) // 2
+    D = c2 * h2 * w2
+    shapes = [((c1, 2, 3, 3), 18), ((c2, c1, 3, 3), 9 * c1), ((hidden, 2 * D), 2 * D), ((r_max, hidden), hidden)]
+    return [(rng.standard_normal(sh) * np.sqrt(2.0 / fan), np.zeros(sh[0])) for sh, fan in shapes]
+
+
+def _clip_mean(feat: np.ndarray, sizes) -> np.ndarray:
+    """Each row replaced by the mean of the rows of its clip (clips = consecutive runs of
+    `sizes` rows)."""
+    out = np.empty_like(feat)
+    o = 0
+    for nc in sizes:
+        out[o:o + nc] = feat[o:o + nc].mean(axis=0, keepdims=True)
+        o += nc
+    return out
+
+
+def net_forward(params, X: np.ndarray, sizes):
+    """Omega rows (F x r_max) of the frames X (F, 2, h, w) of consecutive clips of `sizes`
+    frames, and the cache for net_backward."""
+    (Wc1, b1), (Wc2, b2), (W3, b3), (W4, b4) = params
+    z1 = conv3x3s2_forward(X, Wc1, b1)
+    a1 = np.maximum(z1, 0.0)
+    z2 = conv3x3s2_forward(a1, Wc2, b2)
+    a2 = np.maximum(z2, 0.0)
+    feat = a2.reshape(a2.shape[0], -1)
+    z = np.hstack([feat, _clip_mean(feat, sizes)])
+    z3 = z @ W3.T + b3
+    a3 = np.maximum(z3, 0.0)
+    Om = a3 @ W4.T + b4
+    return Om, (X, z1, a1, z2, a2, z, z3, a3, tuple(sizes))
+
+
+def net_backward(params, cache, dOm: np.ndarray):
+    """Gradients [(dWc1, db1), (dWc2, db2), (dW3, db3), (dW4, db4)] for dL/dOmega = dOm."""
+    (Wc1, b1), (Wc2, b2), (W3, b3), (W4, b4) = params
+    X, z1, a1, z2, a2, z, z3, a3, sizes = cache
+    dW4, db4 = dOm.T @ a3, dOm.sum(axis=0)
+    dz3 = (dOm @ W4) * (z3 > 0.0)
+    dW3, db3 = dz3.T @ z, dz3.sum(axis=0)
+    dz = dz3 @ W3
+    D = dz.shape[1] // 2
+    dfeat = dz[:, :D] + _clip_mean(dz[:, D:], sizes)
+    dz2 = dfeat.reshape(z2.shape) * (z2 > 0.0)
+    da1, dWc2, db2 = conv3x3s2_backward(a1, Wc2, dz2)
+    dz1 = da1 * (z1 > 0.0)
+    _, dWc1, db1 = conv3x3s2_backward(X, Wc1, dz1)
+    return [(dWc1, db1), (dWc2, db2), (dW3, db3), (dW4, db4)]
+
+
+def omega_loss(A: np.ndarray, Om: np.ndarray, r: int, V: np.ndarray):
+    """Loss ||P_Y - P_V||_F^2 / (2 r) of the clip basis Y = A Omega[:, :r] against the
+    orthonormal target V (m x r), and its gradient with respect to Omega (n x r_max; the
+    columns beyond r get zero)."""
+    Y = A @ Om[:, :r]
+    L = projector_distance(Y, V) / (2.0 * r)
+    dY = projector_distance_grad(Y, V) / (2.0 * r)
+    dOm = np.zeros_like(Om)
+    dOm[:, :r] = A.T @ dY
+    return L, dOm
+
+
+def warm_start_x1_weighted(A1: np.ndarray, U: np.ndarray, W1: np.ndarray) -> np.ndarray:
+    """X1_0(:, a) = U (U^T D_a U)^{-1} U^T D_a A1(:, a) with D_a = diag(W1(:, a)^2): for
+    each weighted frame the point of span(U) closest to it in the W1-weighted norm of the
+    first term of Eq. 5 (one dense solve per column; library step)."""
+    X = np.empty_like(A1, dtype=np.float64)
+    for a in range(A1.shape[1]):
+        d = W1[:, a] ** 2
+        X[:, a] = U @ np.linalg.solve(U.T @ (U * d[:, None]), U.T @ (d * A1[:, a]))
+    return X
+
+
+def round_bf16(x: np.ndarray) -> np.ndarray:
+    """float32 values rounded to bfloat16 (the upper 16 bits of an IEEE binary32), round to
+    nearest with ties to even, returned as float64."""
+    b = np.asarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    lsb = (b >> np.uint64(16)) & np.uint64(1)
+    b = (b + np.uint64(0x7FFF) + lsb) & np.uint64(0xFFFF0000)
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def adam_step(theta, g, m, v, t: int, lr: float, beta1: float = 0.9, beta2: float = 0.999,
+              eps: float = 1e-8):
+    """One Adam update (Kingma & Ba 2015, Algorithm 1) at step t >= 1: returns the new
+    (theta, m, v)."""
+    m = beta1 * m + (1.0 - beta1) * g
+    v = beta2 * v + (1.0 - beta2) * g * g
+    mh = m / (1.0 - beta1 ** t)
+    vh = v / (1.0 - beta2 ** t)
+    return theta - lr * mh / (np.sqrt(vh) + eps), m, v

@@ -129,7 +129,45 @@ def _mlp_backward_no_relu_mask(params, pre, dY):
     return grads, g
 
 
+def _conv_flipped(X, Wc, b):
+    return ws._orig["conv3x3s2_forward"](X, Wc[:, :, ::-1, ::-1], b)
+
+
+def _net_backward_no_context(params, cache, dOm):
+    (Wc1, b1), (Wc2, b2), (W3, b3), (W4, b4) = params
+    X, z1, a1, z2, a2, z, z3, a3, sizes = cache
+    dW4, db4 = dOm.T @ a3, dOm.sum(axis=0)
+    dz3 = (dOm @ W4) * (z3 > 0.0)
+    dW3, db3 = dz3.T @ z, dz3.sum(axis=0)
+    dz = dz3 @ W3
+    dfeat = dz[:, :dz.shape[1] // 2]
+    dz2 = dfeat.reshape(z2.shape) * (z2 > 0.0)
+    da1, dWc2, db2 = ws.conv3x3s2_backward(a1, Wc2, dz2)
+    _, dWc1, db1 = ws.conv3x3s2_backward(X, Wc1, da1 * (z1 > 0.0))
+    return [(dWc1, db1), (dWc2, db2), (dW3, db3), (dW4, db4)]
+
+
+def _weighted_projection_w1(A1, U, W1):
+    return ws._orig["warm_start_x1_weighted"](A1, U, np.sqrt(W1))
+
+
+def _bf16_truncated(x):
+    b = np.asarray(x, dtype=np.float32).view(np.uint32) & np.uint32(0xFFFF0000)
+    return b.view(np.float32).astype(np.float64)
+
+
+def _adam_no_bias_correction(theta, g, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    m = beta1 * m + (1.0 - beta1) * g
+    v = beta2 * v + (1.0 - beta2) * g * g
+    return theta - lr * m / (np.sqrt(v) + eps), m, v
+
+
 WS_MUTATIONS = {
+    "convolution with the kernel flipped": ("conv3x3s2_forward", _conv_flipped),
+    "network backward without the context term": ("net_backward", _net_backward_no_context),
+    "weighted projection with W1 instead of W1^2": ("warm_start_x1_weighted", _weighted_projection_w1),
+    "bf16 by truncation": ("round_bf16", _bf16_truncated),
+    "adam without bias correction": ("adam_step", _adam_no_bias_correction),
     "loss gradient sign": ("projector_distance_grad", _grad_sign),
     "loss gradient without (Y^T Y)^-1": ("projector_distance_grad", _grad_no_gram_inverse),
     "upsampling without half-pixel centres": ("upsample_bilinear", _upsample_no_half_pixel),
@@ -146,6 +184,16 @@ WS_PINS = [
     wpins.test_projector_distance_closed_forms,
     lambda: wpins.test_projector_distance_gradient_central_differences(4),
     wpins.test_mlp_gradients_central_differences,
+    wpins.test_conv_is_strided_cross_correlation,
+    wpins.test_conv_of_a_delta_and_of_a_constant,
+    wpins.test_conv_backward_central_differences,
+    wpins.test_net_backward_central_differences,
+    wpins.test_net_frames_are_exchangeable_within_a_clip,
+    wpins.test_omega_loss_gradient_invariance_and_zero,
+    wpins.test_weighted_projection,
+    wpins.test_round_bf16,
+    wpins.test_adam_first_step_and_descent,
+    wpins.test_prepare_input_scales,
 ]
 
 
