@@ -270,6 +270,99 @@ wlr_status wlr_x1_update_noalloc(const float* A, int64_t lda, const float* W1, i
 /* Number of kernels this handle has launched (graph replays count each node). */
 int64_t wlr_kernel_launches(wlr_handle h);
 
+/* ------------------------------------------------------------------------------------
+ * Learned warm start.  Algorithm 1 starts from "Initialize (X1)_0" and Section 4.1 uses a
+ * random matrix; the method itself never says where X1_0 comes from.  This build adds a
+ * small network that predicts, from a downsampled clip and its weights, the span of the
+ * solution X = (X1, X1 C + D), and starts from the weighted projection of A1 onto it:
+ *
+ *   input (per frame j, h x w):  channel 0 = block means of frame j / RMS of all of them,
+ *                                channel 1 = block means of the per-pixel mean of W1's k
+ *                                columns / their mean
+ *   relu(conv 3x3 stride 2, 2 -> c1) -> relu(conv 3x3 stride 2, c1 -> c2) -> f_j (D values)
+ *   z_j = [f_j | mean of f over the clip's frames] -> relu(fc1: 2D -> hidden) -> fc2 -> omega_j
+ *   Omega (n x r_max) = the rows omega_j;  basis U = A Omega(:, 1:r)  (m x r, full resolution)
+ *   X1_0(:, a) = U (U^T D_a U)^{-1} U^T D_a A1(:, a),  D_a = diag(W1(:, a)^2)
+ *
+ * The weighted projection minimises the first term of Eq. 5 over X1 with columns in
+ * span(U).  Weights are kept in float (master copy, updated by Adam) and used in bfloat16
+ * (round to nearest even) by every forward and backward kernel; all sums are float.
+ * Training minimises ||P_Y - P_V||_F^2 / (2r), Y = A Omega(:, 1:r), against the column space
+ * V of a converged solution (wlr_get_basis).  Network tensors are row-major:
+ * X (frames, 2, h, w), Omega (frames, r_max).  Device pointers unless stated.
+ * ------------------------------------------------------------------------------------ */
+typedef struct wlr_ws_net_s* wlr_ws_net;
+
+typedef struct {
+  int32_t h, w;      /* network input frame size (downsampled), each >= 1               */
+  int32_t c1, c2;    /* channels of the two convolutions                               */
+  int32_t hidden;    /* width of the hidden fully-connected layer                      */
+  int32_t r_max;     /* columns of Omega: ranks r <= r_max can be served                */
+} wlr_ws_shape;
+
+/* Network with weights N(0, 2/fan_in) from seed (SplitMix64 + Box-Muller as for
+ * WLR_INIT_RANDOM, one stream per parameter index), biases 0, Adam moments 0.  max_frames
+ * bounds the frames of one forward/backward call (activation buffers are allocated here).
+ * stream: cudaStream_t or NULL (the library's own).  WLR_ERR_INVALID_ARG for a bad shape. */
+wlr_status wlr_ws_create(wlr_ws_net* out, const wlr_ws_shape* shape, int32_t max_frames,
+                         uint64_t seed, void* stream);
+wlr_status wlr_ws_destroy(wlr_ws_net net);
+/* Number of parameters; the flat float layout is Wc1 (c1,2,3,3), b1, Wc2 (c2,c1,3,3), b2,
+ * W3 (hidden, 2D), b3, W4 (r_max, hidden), b4, each row-major, D = c2 ceil(ceil(h/2)/2)
+ * ceil(ceil(w/2)/2). */
+int64_t wlr_ws_param_count(wlr_ws_net net);
+/* Copy the float master weights (or the last gradients) out, or new master weights in (the
+ * bfloat16 copy is refreshed), in the flat layout above; mem says host or device. */
+wlr_status wlr_ws_get_params(wlr_ws_net net, float* out, wlr_memory mem);
+wlr_status wlr_ws_get_grads(wlr_ws_net net, float* out, wlr_memory mem);
+wlr_status wlr_ws_set_params(wlr_ws_net net, const float* in, wlr_memory mem);
+
+/* Network input of one clip: A (m x n, column-major, lda >= m, float, device) with frames of
+ * H x W pixels (m = H W, pixel index y W + x), W1 (m x k, ldw >= m); H = f h and W = f w for
+ * an integer f.  Writes X (n, 2, h, w).  WLR_ERR_INVALID_ARG otherwise. */
+wlr_status wlr_ws_prepare(wlr_ws_net net, const float* A, int64_t lda, const float* W1,
+                          int64_t ldw, int32_t H, int32_t W, int32_t n, int32_t k, float* X);
+
+/* Forward pass over `frames` frames of X that belong to consecutive clips: clip c holds
+ * frames clip_start[c] .. clip_start[c+1]-1 (host array of nclips+1 entries, clip_start[0] =
+ * 0, clip_start[nclips] = frames).  Writes Omega (frames x r_max) and keeps the activations
+ * for wlr_ws_backward.  frames <= max_frames. */
+wlr_status wlr_ws_forward(wlr_ws_net net, const float* X, int32_t frames,
+                          const int32_t* clip_start, int32_t nclips, float* Omega);
+
+/* Loss of one clip and its gradient: Y = A Omega_c(:, 1:r) with A (m x n, lda) and
+ * Omega_c (n x r_max, the clip's rows of Omega), V (m x r, column-major, ldv >= m, orthonormal
+ * columns).  Adds ||P_Y - P_V||_F^2 / (2r) to *loss (device double) and writes
+ * dOmega_c = d loss / d Omega_c (n x r_max; zero beyond column r).  1 <= r <= min(r_max, n). */
+wlr_status wlr_ws_loss(wlr_ws_net net, const float* A, int64_t lda, int32_t m, int32_t n,
+                       const float* Omega_c, int32_t r, const float* V, int64_t ldv,
+                       double* loss, float* dOmega_c);
+
+/* Backward pass of the last forward call: gradients of sum(dOmega o Omega) with respect to
+ * every parameter, stored (not accumulated) as the net's gradients. */
+wlr_status wlr_ws_backward(wlr_ws_net net, const float* dOmega);
+
+/* One Adam step (Kingma & Ba 2015) on the stored gradients times grad_scale, step count
+ * advanced by one; the bfloat16 copy is refreshed. */
+wlr_status wlr_ws_adam(wlr_ws_net net, float lr, float beta1, float beta2, float eps,
+                       float grad_scale);
+
+/* Number of kernels the network object has launched. */
+int64_t wlr_ws_launches(wlr_ws_net net);
+
+/* Orthonormal basis (m x r, column-major, leading dimension ldv >= m, float, device) of the
+ * column space of X = (X1, X1 C + D) at the handle's current iterate: the span of X1 and of
+ * the r - k left singular vectors kept in D (Theorem 1), orthonormalised in double by
+ * Cholesky QR twice.  WLR_ERR_NOT_READY before wlr_set_init.  Synchronises. */
+wlr_status wlr_get_basis(wlr_handle h, float* V, int64_t ldv);
+
+/* Initialise X1 from the network (replaces wlr_set_init): X = prepared input of the handle's
+ * data (frames H x W, H W = m), Omega = forward pass, U = A Omega(:, 1:r), then X1_0 the
+ * weighted projection above (Gram matrices and solves in double, with a ridge of 1e-12 of
+ * the trace).  Needs r <= r_max and n <= max_frames; resets the iteration like wlr_set_init.
+ * Float handles only.  Synchronises. */
+wlr_status wlr_set_init_learned(wlr_handle h, wlr_ws_net net, int32_t H, int32_t W);
+
 #ifdef __cplusplus
 }
 #endif

@@ -10,10 +10,6 @@
 
 #include "wlr_solver.cuh"
 
-struct wlr_handle_s {
-  wlr::SolverBase* impl = nullptr;
-  std::string last_error;
-};
 
 namespace {
 thread_local std::string g_create_error;

@@ -61,6 +61,24 @@ class SolverBase {
   virtual std::vector<ProfEntry> profile(int reps) = 0;
   virtual void refine(void* X1_out, int64_t ldx, wlr_memory mem, double* Fp, double* Fnext) = 0;
 
+  // Device view for the warm-start code: the data, the current X1 and (with_factors) the
+  // factors C (k x n2) and V_s (n2 x s) of its (C, D) step, column-major, element type
+  // float or double (fp64).  Work on `stream` is ordered after the handle's and the handle's
+  // later work after it.  Pointers stay valid until the next call on the handle.
+  struct View {
+    const void* A;
+    int64_t lda;
+    const void* W1;
+    int64_t ldw;
+    const void* X1;
+    const void* C;
+    const void* Vs;
+    cudaStream_t stream;
+    bool fp64;
+  };
+  virtual View view(bool with_factors) = 0;
+  virtual Dims dims() const = 0;
+
   // Batched solve (wlr_solve_batched).  batch_ready: the next iterations replay as a
   // graph (data and init set, warm-up done).  batch_iterate: one iteration on the handle's
   // own stream.  batch_capture: n iterations captured into a graph that is not run; the
@@ -80,4 +98,13 @@ class SolverBase {
 SolverBase* make_solver_f32(const Dims& d, const wlr_options& o, cudaStream_t user_stream);
 SolverBase* make_solver_f64(const Dims& d, const wlr_options& o, cudaStream_t user_stream);
 
+// Host: set the message that wlr_last_error(NULL) returns (calls without a handle).
+void set_global_error(const char* msg);
+
 }  // namespace wlr
+
+// The object behind a wlr_handle.
+struct wlr_handle_s {
+  wlr::SolverBase* impl = nullptr;
+  std::string last_error;
+};

@@ -331,6 +331,19 @@ class Solver final : public SolverBase {
     raise_err_async();
   }
 
+  View view(bool with_factors) override {
+    need_data();
+    if (with_factors) {
+      need_init();
+      begin();
+      if (!cd_valid_) compute_cd(cur_, false);
+      end();
+    }
+    return View{A_, lda_, W1_, ldw_, have_init_ ? X1buf_[cur_] : nullptr, C_, Vs_, ustream_,
+                std::is_same<T, double>::value};
+  }
+  Dims dims() const override { return d_; }
+
   void get_factors(double* C, double* Vs, double* sigma2) override {
     need_init();
     const int k = d_.k, n2 = d_.n2, s = d_.s;

@@ -49,6 +49,11 @@ class wlr_options(ct.Structure):
     ]
 
 
+class wlr_ws_shape(ct.Structure):
+    _fields_ = [("h", ct.c_int32), ("w", ct.c_int32), ("c1", ct.c_int32), ("c2", ct.c_int32),
+                ("hidden", ct.c_int32), ("r_max", ct.c_int32)]
+
+
 class WlrError(RuntimeError):
     def __init__(self, status: int, message: str, index: int = -1):
         super().__init__(f"{status_string(status)}: {message}")
@@ -85,6 +90,20 @@ def _load():
         "wlr_kernel_launches": (i64, [H]),
         "wlr_profile": (i32, [H, i32, ct.c_char_p, i32, P, P, i32, ct.POINTER(i32)]),
         "wlr_x1_update_noalloc": (i32, [P, i64, P, i64, P, i64, i64, i64, i64, P, P, P, P, P, P]),
+        "wlr_ws_create": (i32, [ct.POINTER(H), ct.POINTER(wlr_ws_shape), i32, u64, P]),
+        "wlr_ws_destroy": (i32, [H]),
+        "wlr_ws_param_count": (i64, [H]),
+        "wlr_ws_get_params": (i32, [H, P, i32]),
+        "wlr_ws_get_grads": (i32, [H, P, i32]),
+        "wlr_ws_set_params": (i32, [H, P, i32]),
+        "wlr_ws_prepare": (i32, [H, P, i64, P, i64, i32, i32, i32, i32, P]),
+        "wlr_ws_forward": (i32, [H, P, i32, P, i32, P]),
+        "wlr_ws_loss": (i32, [H, P, i64, i32, i32, P, i32, P, i64, P, P]),
+        "wlr_ws_backward": (i32, [H, P]),
+        "wlr_ws_adam": (i32, [H, ct.c_float, ct.c_float, ct.c_float, ct.c_float, ct.c_float]),
+        "wlr_ws_launches": (i64, [H]),
+        "wlr_get_basis": (i32, [H, P, i64]),
+        "wlr_set_init_learned": (i32, [H, H, i32, i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -102,6 +121,9 @@ EXPORTED = (
     "wlr_status_string",
     "wlr_last_error",
     "wlr_kernel_launches", "wlr_profile", "wlr_x1_update_noalloc",
+    "wlr_ws_create", "wlr_ws_destroy", "wlr_ws_param_count", "wlr_ws_get_params",
+    "wlr_ws_get_grads", "wlr_ws_set_params", "wlr_ws_prepare", "wlr_ws_forward", "wlr_ws_loss",
+    "wlr_ws_backward", "wlr_ws_adam", "wlr_ws_launches", "wlr_get_basis", "wlr_set_init_learned",
 )
 
 
@@ -388,6 +410,160 @@ def wlr_x1_update_noalloc(A, W1, X1, k, r, C, Vs, X1_next, wterm=None, status=No
     return st
 
 
+# ------------------------------------------------------------------ learned warm start
+def _dev_f32(t, name):
+    """data_ptr of a contiguous float32 CUDA tensor."""
+    import torch
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.float32 or not t.is_cuda:
+        raise ValueError(f"{name} must be a float32 CUDA tensor")
+    if not t.is_contiguous() and not (t.dim() == 2 and t.stride(0) == 1):
+        raise ValueError(f"{name} must be contiguous (row-major) or column-major")
+    return t.data_ptr()
+
+
+def _net_check(st, net):
+    if st != WLR_OK:
+        raise WlrError(st, _lib.wlr_last_error(None).decode())
+    return st
+
+
+def wlr_ws_create(h, w, c1, c2, hidden, r_max, max_frames, seed=0, stream=None):
+    sh = wlr_ws_shape(h, w, c1, c2, hidden, r_max)
+    net = ct.c_void_p()
+    _net_check(_lib.wlr_ws_create(ct.byref(net), ct.byref(sh), int(max_frames), int(seed),
+                                  _stream_ptr(stream)), None)
+    return net
+
+
+def wlr_ws_destroy(net):
+    if net:
+        _lib.wlr_ws_destroy(net)
+
+
+def wlr_ws_param_count(net):
+    return int(_lib.wlr_ws_param_count(net))
+
+
+def wlr_ws_get_params(net):
+    out = np.empty(wlr_ws_param_count(net), dtype=np.float32)
+    _net_check(_lib.wlr_ws_get_params(net, out.ctypes.data, WLR_MEM_HOST), net)
+    return out
+
+
+def wlr_ws_get_grads(net):
+    out = np.empty(wlr_ws_param_count(net), dtype=np.float32)
+    _net_check(_lib.wlr_ws_get_grads(net, out.ctypes.data, WLR_MEM_HOST), net)
+    return out
+
+
+def wlr_ws_set_params(net, params):
+    a = np.ascontiguousarray(params, dtype=np.float32)
+    if a.size != wlr_ws_param_count(net):
+        raise ValueError("wrong parameter count")
+    _net_check(_lib.wlr_ws_set_params(net, a.ctypes.data, WLR_MEM_HOST), net)
+
+
+def wlr_ws_prepare(net, A, W1, H, W, k, X):
+    """Network input X (n, 2, h, w) of the clip A (m x n, column-major float32 CUDA tensor)."""
+    pa, lda, dta, mema, _ = _matrix(A)
+    pw, ldw, dtw, memw, _ = _matrix(W1)
+    if {dta, dtw} != {WLR_F32} or {mema, memw} != {WLR_MEM_DEVICE}:
+        raise ValueError("A and W1 must be float32 CUDA tensors")
+    _net_check(_lib.wlr_ws_prepare(net, pa, lda, pw, ldw, int(H), int(W), int(A.shape[1]), int(k),
+                                   _dev_f32(X, "X")), net)
+
+
+def wlr_ws_forward(net, X, clip_start, Omega):
+    cs = np.ascontiguousarray(clip_start, dtype=np.int32)
+    frames = int(cs[-1])
+    _net_check(_lib.wlr_ws_forward(net, _dev_f32(X, "X"), frames, cs.ctypes.data, len(cs) - 1,
+                                   _dev_f32(Omega, "Omega")), net)
+
+
+def wlr_ws_loss(net, A, Omega_c, r, V, loss, dOmega_c):
+    """Adds the clip's loss to loss (1-element float64 CUDA tensor); writes dOmega_c."""
+    pa, lda, dta, mema, _ = _matrix(A)
+    pv, ldv, dtv, memv, _ = _matrix(V)
+    if {dta, dtv} != {WLR_F32} or {mema, memv} != {WLR_MEM_DEVICE}:
+        raise ValueError("A and V must be float32 CUDA tensors")
+    m, n = A.shape
+    _net_check(_lib.wlr_ws_loss(net, pa, lda, int(m), int(n), _dev_f32(Omega_c, "Omega_c"), int(r),
+                                pv, ldv, loss.data_ptr(), _dev_f32(dOmega_c, "dOmega_c")), net)
+
+
+def wlr_ws_backward(net, dOmega):
+    _net_check(_lib.wlr_ws_backward(net, _dev_f32(dOmega, "dOmega")), net)
+
+
+def wlr_ws_adam(net, lr, beta1=0.9, beta2=0.999, eps=1e-8, grad_scale=1.0):
+    _net_check(_lib.wlr_ws_adam(net, float(lr), float(beta1), float(beta2), float(eps),
+                                float(grad_scale)), net)
+
+
+def wlr_ws_launches(net):
+    return int(_lib.wlr_ws_launches(net))
+
+
+def wlr_get_basis(h, V):
+    """Orthonormal basis (m x r float32 CUDA tensor, column-major) of span(X1, X1 C + D)."""
+    p, ld, dt, mem, _ = _matrix(V)
+    if dt != WLR_F32 or mem != WLR_MEM_DEVICE:
+        raise ValueError("V must be a float32 CUDA tensor")
+    _check(_lib.wlr_get_basis(h, p, ld), h)
+
+
+def wlr_set_init_learned(h, net, H, W):
+    _check(_lib.wlr_set_init_learned(h, net, int(H), int(W)), h)
+
+
+class WarmStartNet:
+    """Owner of one warm-start network (destroyed with the object)."""
+
+    def __init__(self, h=30, w=40, c1=16, c2=32, hidden=384, r_max=64, max_frames=4096, seed=0,
+                 stream=None):
+        self.shape = (h, w, c1, c2, hidden, r_max)
+        self.h, self.w, self.r_max = h, w, r_max
+        self.net = wlr_ws_create(h, w, c1, c2, hidden, r_max, max_frames, seed, stream)
+
+    def params(self):
+        return wlr_ws_get_params(self.net)
+
+    def grads(self):
+        return wlr_ws_get_grads(self.net)
+
+    def set_params(self, p):
+        wlr_ws_set_params(self.net, p)
+
+    def prepare(self, A, W1, H, W, k, X):
+        wlr_ws_prepare(self.net, A, W1, H, W, k, X)
+
+    def forward(self, X, clip_start, Omega):
+        wlr_ws_forward(self.net, X, clip_start, Omega)
+
+    def loss(self, A, Omega_c, r, V, loss, dOmega_c):
+        wlr_ws_loss(self.net, A, Omega_c, r, V, loss, dOmega_c)
+
+    def backward(self, dOmega):
+        wlr_ws_backward(self.net, dOmega)
+
+    def adam(self, lr, beta1=0.9, beta2=0.999, eps=1e-8, grad_scale=1.0):
+        wlr_ws_adam(self.net, lr, beta1, beta2, eps, grad_scale)
+
+    def launches(self):
+        return wlr_ws_launches(self.net)
+
+    def close(self):
+        if getattr(self, "net", None):
+            wlr_ws_destroy(self.net)
+            self.net = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Solver:
     """Convenience owner of one handle (destroyed with the object)."""
 
@@ -422,6 +598,12 @@ class Solver:
 
     def refine(self, X1_out=None):
         return wlr_refine(self.h, X1_out)
+
+    def basis(self, V):
+        return wlr_get_basis(self.h, V)
+
+    def set_init_learned(self, net, H, W):
+        return wlr_set_init_learned(self.h, net.net if isinstance(net, WarmStartNet) else net, H, W)
 
     def factors(self):
         return wlr_get_factors(self.h, self.k, self.n - self.k, self.r - self.k)
