@@ -33,9 +33,12 @@ The network of the warm start (per clip: n frames, k weighted, rank r <= r_max):
     net_backward:        z_j = [f_j | mean of f over the frames of j's clip] -> relu(fc1)
                          -> fc2 -> omega_j (r_max numbers): the row j of the frame-mixing
                          matrix Omega (n x r_max) of the clip;
-  * omega_loss:          the clip's predicted basis is Y = A Omega[:, :r] (full resolution,
-                         m x r); loss = ||P_Y - P_V||_F^2 / (2 r) with V the converged
-                         solution's left singular subspace; gradient d/dOmega = A^T dL/dY;
+  * omega_basis /        the clip's predicted basis is Y = [A1 | 0] + A Omega[:, :r] / n (full
+    omega_loss:          resolution, m x r): the weighted frames plus frame mixtures (the W1
+                         term of Eq. 5 keeps X1 close to A1, so the solution's span holds
+                         A1's columns up to small corrections); loss = ||P_Y - P_V||_F^2 / (2 r)
+                         with V the converged solution's column space; gradient
+                         d/dOmega = A^T dL/dY / n;
   * warm_start_x1_weighted: X1_0(:, a) = U (U^T D_a U)^{-1} U^T D_a A1(:, a), D_a =
                          diag(W1(:, a)^2): the weighted least-squares fit of each weighted
                          frame inside span(U) (the minimiser of the first term of Eq. 5 over
@@ -53,7 +56,7 @@ import numpy as np
 __all__ = ["downsample_frames", "upsample_bilinear", "warm_start_x1", "projector_distance",
            "projector_distance_grad", "mlp_init", "mlp_forward", "mlp_backward",
            "prepare_input", "conv3x3s2_forward", "conv3x3s2_backward", "net_init", "net_forward",
-           "net_backward", "omega_loss", "warm_start_x1_weighted", "round_bf16", "adam_step"]
+           "net_backward", "omega_basis", "omega_loss", "warm_start_x1_weighted", "round_bf16", "adam_step"]
 
 
 def downsample_frames(A: np.ndarray, H: int, W: int, f: int) -> np.ndarray:
@@ -248,15 +251,25 @@ def net_backward(params, cache, dOm: np.ndarray):
     return [(dWc1, db1), (dWc2, db2), (dW3, db3), (dW4, db4)]
 
 
-def omega_loss(A: np.ndarray, Om: np.ndarray, r: int, V: np.ndarray):
-    """Loss ||P_Y - P_V||_F^2 / (2 r) of the clip basis Y = A Omega[:, :r] against the
-    orthonormal target V (m x r), and its gradient with respect to Omega (n x r_max; the
-    columns beyond r get zero)."""
-    Y = A @ Om[:, :r]
+def omega_basis(A: np.ndarray, Om: np.ndarray, r: int, k: int) -> np.ndarray:
+    """The clip's predicted basis Y = [A1 | 0] + A Omega[:, :r] / n (m x r): the k weighted
+    frames plus frame mixtures, so that an output near zero starts from span(A1)."""
+    n = A.shape[1]
+    Y = A @ Om[:, :r] / n
+    Y[:, :k] += A[:, :k]
+    return Y
+
+
+def omega_loss(A: np.ndarray, Om: np.ndarray, r: int, V: np.ndarray, k: int):
+    """Loss ||P_Y - P_V||_F^2 / (2 r) of the clip basis Y = omega_basis(A, Omega, r, k)
+    against the orthonormal target V (m x r), and its gradient with respect to Omega
+    (n x r_max; the columns beyond r get zero): d/dOmega = A^T dL/dY / n."""
+    n = A.shape[1]
+    Y = omega_basis(A, Om, r, k)
     L = projector_distance(Y, V) / (2.0 * r)
     dY = projector_distance_grad(Y, V) / (2.0 * r)
     dOm = np.zeros_like(Om)
-    dOm[:, :r] = A.T @ dY
+    dOm[:, :r] = A.T @ dY / n
     return L, dOm
 
 

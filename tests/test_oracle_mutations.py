@@ -189,7 +189,7 @@ WS_PINS = [
     wpins.test_conv_backward_central_differences,
     wpins.test_net_backward_central_differences,
     wpins.test_net_frames_are_exchangeable_within_a_clip,
-    wpins.test_omega_loss_gradient_invariance_and_zero,
+    wpins.test_omega_loss_gradient_prior_and_zero,
     wpins.test_weighted_projection,
     wpins.test_round_bf16,
     wpins.test_adam_first_step_and_descent,

@@ -260,27 +260,28 @@ def test_net_frames_are_exchangeable_within_a_clip():
     assert np.allclose(Om3[:3], Om[:3], atol=1e-12)
 
 
-def test_omega_loss_gradient_invariance_and_zero():
+def test_omega_loss_gradient_prior_and_zero():
     rng = np.random.default_rng(16)
-    m, n, r, rmax = 30, 8, 3, 5
+    m, n, r, k, rmax = 30, 8, 4, 2, 5
     A = rng.standard_normal((m, n))
     V, _ = np.linalg.qr(rng.standard_normal((m, r)))
     Om = rng.standard_normal((n, rmax))
-    L, dOm = ws.omega_loss(A, Om, r, V)
+    L, dOm = ws.omega_loss(A, Om, r, V, k)
     assert 0.0 <= L <= 1.0
     assert np.all(dOm[:, r:] == 0.0)
-    for idx in [(0, 0), (7, 2), (3, 1)]:
-        assert abs(_num_grad(lambda t: ws.omega_loss(A, t, r, V)[0], Om, idx) - dOm[idx]) < 1e-7
-    # only span(A Omega[:, :r]) matters
-    M = rng.standard_normal((r, r)) + 3 * np.eye(r)
-    Om2 = Om.copy()
-    Om2[:, :r] = Om[:, :r] @ M
-    assert abs(ws.omega_loss(A, Om2, r, V)[0] - L) < 1e-12
-    # zero when A Omega spans V
-    Om3 = Om.copy()
-    Om3[:, :r] = np.linalg.lstsq(A, A @ rng.standard_normal((n, r)), rcond=None)[0]
-    V3, _ = np.linalg.qr(A @ Om3[:, :r])
-    assert ws.omega_loss(A, Om3, r, V3)[0] < 1e-24
+    for idx in [(0, 0), (7, 2), (3, 1), (5, 3)]:
+        assert abs(_num_grad(lambda t: ws.omega_loss(A, t, r, V, k)[0], Om, idx) - dOm[idx]) < 1e-7
+    # the basis is the weighted frames plus mixtures scaled by 1 / n
+    Y = ws.omega_basis(A, Om, r, k)
+    assert np.allclose(Y[:, :k], A[:, :k] + A @ Om[:, :k] / n, atol=1e-13)
+    assert np.allclose(Y[:, k:], A @ Om[:, k:r] / n, atol=1e-13)
+    # with r = k and Omega = 0 the basis is A1 itself: the loss is A1's distance to V
+    Vk, _ = np.linalg.qr(rng.standard_normal((m, k)))
+    Lk, _ = ws.omega_loss(A, np.zeros((n, rmax)), k, Vk, k)
+    assert abs(Lk - ws.projector_distance(A[:, :k], Vk) / (2 * k)) < 1e-12
+    # zero when the target is the predicted span itself
+    V3, _ = np.linalg.qr(Y)
+    assert ws.omega_loss(A, Om, r, V3, k)[0] < 1e-24
 
 
 def test_weighted_projection():
