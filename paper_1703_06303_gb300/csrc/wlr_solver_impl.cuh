@@ -343,6 +343,7 @@ class Solver final : public SolverBase {
                 std::is_same<T, double>::value};
   }
   Dims dims() const override { return d_; }
+  cudaStream_t user_stream() const override { return ustream_; }
 
   void get_factors(double* C, double* Vs, double* sigma2) override {
     need_init();
@@ -772,6 +773,7 @@ class Solver final : public SolverBase {
       return;
     }
     auto enc = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    enc_ = (void*)fn;
     ld4_ = ((m + 3) / 4) * 4;
     A2h_ = dalloc<float>((size_t)ld4_ * n2);
     A2l_ = dalloc<float>((size_t)ld4_ * n2);
@@ -826,7 +828,26 @@ class Solver final : public SolverBase {
     }
     use_tc_ = true;
   }
+  // TMA map of the FP32 A2 itself (32 rows x 128 columns, 128-byte swizzle) for the
+  // per-iteration Gram, when its leading dimension and base allow TMA (lda a multiple of 4,
+  // 16-byte aligned); otherwise the Gram reads the TF32 split copies.
+  void tc_map_a2() {
+    a2f_ok_ = false;
+    if (!use_tc_ || !enc_ || !std::is_same<T, float>::value) return;
+    const int m = d_.m, k = d_.k, n2 = d_.n2;
+    const float* A2 = (const float*)(A_ + (int64_t)k * lda_);
+    if (lda_ % 4 != 0 || ((uintptr_t)A2 & 15) != 0) return;
+    auto enc = (PFN_cuTensorMapEncodeTiled_v12000)enc_;
+    cuuint64_t dims[2] = {(cuuint64_t)m, (cuuint64_t)n2};
+    cuuint64_t strides[1] = {(cuuint64_t)lda_ * 4};
+    cuuint32_t box[2] = {32, 128};
+    cuuint32_t es[2] = {1, 1};
+    a2f_ok_ = enc(&mA2f_, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)A2, dims, strides, box, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  }
   void tc_split_a2() {
+    tc_map_a2();
     if (!use_tc_k_) return;
     const int m = d_.m, k = d_.k, n2 = d_.n2;
     tc::split_tf32<<<grid1d((int64_t)m * n2), 256, 0, stream_>>>((const float*)(A_ + (int64_t)k * lda_), lda_, m, n2,
@@ -851,12 +872,16 @@ class Solver final : public SolverBase {
       Prof pf(this, "gram_tf32x3_t");
       dim3 g(1 + cdiv(n2, 128), ch_tc_.nch);
       const int64_t pstride = (int64_t)k * k + (int64_t)k * n2;
+      const CUtensorMap& mf = a2f_ok_ ? mA2f_ : mA2h_;
+      const int split = a2f_ok_ ? 1 : 0;
       if (tn_ == tc::TN)
         tc::gram_tf32x3_t<tc::TN><<<g, tc::t_threads(tc::TN), tc::t_smem_bytes(tc::TN), stream_>>>(
-            mQh128_, mQl128_, mA2h_, mA2l_, mQh32_, mQl32_, m, k, k, n2, ch_tc_.rows, part64_, pstride, err_);
+            mQh128_, mQl128_, mA2h_, mA2l_, mQh32_, mQl32_, mf, split, m, k, k, n2, ch_tc_.rows, part64_, pstride,
+            err_);
       else
         tc::gram_tf32x3_t<2 * tc::TN><<<g, tc::t_threads(2 * tc::TN), tc::t_smem_bytes(2 * tc::TN), stream_>>>(
-            mQh128_, mQl128_, mA2h_, mA2l_, mQh32_, mQl32_, m, k, k, n2, ch_tc_.rows, part64_, pstride, err_);
+            mQh128_, mQl128_, mA2h_, mA2l_, mQh32_, mQl32_, mf, split, m, k, k, n2, ch_tc_.rows, part64_, pstride,
+            err_);
     }
     count(1);
   }
@@ -1454,6 +1479,9 @@ class Solver final : public SolverBase {
   size_t part_elems_ = 0;
   float *A2h_ = nullptr, *A2l_ = nullptr, *Q1h_ = nullptr, *Q1l_ = nullptr;
   CUtensorMap mA2h_, mA2l_, mQh128_, mQl128_, mQh32_, mQl32_, mA2h64_, mA2l64_;
+  CUtensorMap mA2f_;          // FP32 A2 itself (per-iteration Gram, split in shared memory)
+  bool a2f_ok_ = false;
+  void* enc_ = nullptr;       // cuTensorMapEncodeTiled
   int2* kk_pairs_ = nullptr;   // column-block pairs of the tensor-core K
   int kk_npairs_ = 0;
   Chunk ch_kk_{1, 32};

@@ -46,8 +46,9 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                : "memory");
 }
-// Wait for the phase with the given parity to complete; false after kWaitNs.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+// Wait for the phase with the given parity to complete; false after limit_ns.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity,
+                                          unsigned long long limit_ns = kWaitNs) {
   const unsigned long long t0 = now_ns();
   while (true) {
     unsigned done;
@@ -58,7 +59,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
         : "r"(smem_u32(bar)), "r"(parity)
         : "memory");
     if (done) return true;
-    if (now_ns() - t0 > kWaitNs) return false;
+    if (now_ns() - t0 > limit_ns) return false;
   }
 }
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x,
@@ -197,22 +198,31 @@ __device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) 
   e = (a - ap) + (b - bp);
 }
 
+//
+// With split != 0 the column tiles of Y2 (= A2) come from the FP32 matrix itself (mY2f):
+// TMA brings the FP32 tile into the hi slot of the stage, and the epilogue warps, between
+// two slab read-backs, replace it in place by its TF32 high part and write the low part to
+// the lo slot at the same (swizzled) offsets, then release the stage to the MMA warp.  The
+// values are those of the split copies, so the result is the same bit for bit, while one
+// pass over A2 reads half the bytes (and the row pass reads the same FP32 A2).
 template <int TNV>
 static __global__ void __launch_bounds__(t_threads(TNV))
 gram_tf32x3_t(const __grid_constant__ CUtensorMap mY1h, const __grid_constant__ CUtensorMap mY1l,
               const __grid_constant__ CUtensorMap mY2h, const __grid_constant__ CUtensorMap mY2l,
               const __grid_constant__ CUtensorMap mXh, const __grid_constant__ CUtensorMap mXl,
+              const __grid_constant__ CUtensorMap mY2f, int split,
               int m, int P, int q1, int q2, int chunk_rows, double* __restrict__ part, int64_t pstride,
               int* __restrict__ err) {
   constexpr int NEPI = 4 * (TNV / 32);                  // epilogue warps
   constexpr int T_B_BYTES = t_b_bytes(TNV), T_STAGE_BYTES = t_stage_bytes(TNV);
   constexpr unsigned T_TMEM_COLS = 2 * TNV;             // two TNV-column accumulators
   extern __shared__ unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t full[T_STAGES], empty[T_STAGES], accf[2], acce[2];
+  __shared__ __align__(8) uint64_t full[T_STAGES], empty[T_STAGES], splt[T_STAGES], accf[2], acce[2];
   __shared__ unsigned tmem_base;
   __shared__ int fail;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int tile = blockIdx.x, c = blockIdx.y;
+  const bool do_split = split != 0 && tile != 0;
   const int i_begin = c * chunk_rows;
   const int i_end = min(m, i_begin + chunk_rows);
   const int nkb = (i_end - i_begin + BK - 1) / BK;
@@ -232,6 +242,7 @@ gram_tf32x3_t(const __grid_constant__ CUtensorMap mY1h, const __grid_constant__ 
     for (int s = 0; s < T_STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
+      mbar_init(&splt[s], NEPI);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&accf[b], 1);
@@ -260,10 +271,15 @@ gram_tf32x3_t(const __grid_constant__ CUtensorMap mY1h, const __grid_constant__ 
           break;
         }
         if (*(volatile int*)&fail) break;
-        mbar_expect_tx(&full[s], T_STAGE_BYTES);
         const int x = i_begin + kb * BK;
-        tma_load_2d(base_ptr + (a_addr(s, 0) - base), yh, &full[s], x, y0);
-        tma_load_2d(base_ptr + (a_addr(s, 1) - base), yl, &full[s], x, y0);
+        if (do_split) {
+          mbar_expect_tx(&full[s], T_A_BYTES + 2 * T_B_BYTES);
+          tma_load_2d(base_ptr + (a_addr(s, 0) - base), &mY2f, &full[s], x, y0);
+        } else {
+          mbar_expect_tx(&full[s], T_STAGE_BYTES);
+          tma_load_2d(base_ptr + (a_addr(s, 0) - base), yh, &full[s], x, y0);
+          tma_load_2d(base_ptr + (a_addr(s, 1) - base), yl, &full[s], x, y0);
+        }
         tma_load_2d(base_ptr + (b_addr(s, 0) - base), &mXh, &full[s], x, 0);
         tma_load_2d(base_ptr + (b_addr(s, 1) - base), &mXl, &full[s], x, 0);
       }
@@ -273,7 +289,8 @@ gram_tf32x3_t(const __grid_constant__ CUtensorMap mY1h, const __grid_constant__ 
       constexpr uint32_t idesc = idesc_tf32(128, TNV);
       for (int kb = 0; kb < nkb; ++kb) {
         const int s = kb % T_STAGES, b = kb & 1;
-        if (!mbar_wait(&full[s], (unsigned)((kb / T_STAGES) & 1)) ||
+        const unsigned ph = (unsigned)((kb / T_STAGES) & 1);
+        if (!mbar_wait(&full[s], ph) || (do_split && !mbar_wait(&splt[s], ph)) ||
             (kb >= 2 && !mbar_wait(&acce[b], (unsigned)((kb / 2 - 1) & 1)))) {
           atomicOr(&fail, 1);
           break;
@@ -304,8 +321,35 @@ gram_tf32x3_t(const __grid_constant__ CUtensorMap mY1h, const __grid_constant__ 
       lo[a] = 0.f;
     }
     bool ok = true;
-    for (int kb = 0; kb < nkb; ++kb) {
+    // split of stage kb: the FP32 tile (hi slot) -> TF32 hi in place and lo in the lo slot,
+    // 16 bytes per step over the epilogue warps' threads
+    auto split_stage = [&](int kb) -> bool {
+      const int s = kb % T_STAGES;
+      if (!mbar_wait(&full[s], (unsigned)((kb / T_STAGES) & 1))) return false;
+      float4* yh = reinterpret_cast<float4*>(base_ptr + (a_addr(s, 0) - base));
+      float4* yl = reinterpret_cast<float4*>(base_ptr + (a_addr(s, 1) - base));
+      for (int e = threadIdx.x; e < T_A_BYTES / 16; e += 32 * NEPI) {
+        const float4 x = yh[e];
+        float4 h, l;
+        h.x = round_tf32(x.x); l.x = round_tf32(x.x - h.x);
+        h.y = round_tf32(x.y); l.y = round_tf32(x.y - h.y);
+        h.z = round_tf32(x.z); l.z = round_tf32(x.z - h.z);
+        h.w = round_tf32(x.w); l.w = round_tf32(x.w - h.w);
+        yh[e] = h;
+        yl[e] = l;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&splt[s]);
+      return true;
+    };
+    if (do_split && nkb > 0) ok = split_stage(0);
+    for (int kb = 0; ok && kb < nkb; ++kb) {
       const int b = kb & 1;
+      if (do_split && kb + 1 < nkb && !split_stage(kb + 1)) {
+        ok = false;
+        break;
+      }
       if (!mbar_wait(&accf[b], (unsigned)((kb / 2) & 1))) {
         ok = false;
         break;

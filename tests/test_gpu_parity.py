@@ -377,3 +377,31 @@ def test_fp32_default_trajectory_matches_oracle_fixture(wlr):
     rel = np.abs(Fh - ref[:2500]) / ref[:2500]
     assert rel.max() <= 1e-4, (int(rel.argmax()), float(rel.max()))
     s.close()
+
+
+def test_gram_split_in_shared_memory_is_bit_identical(wlr):
+    """Q1^T [Q1 A2] from the FP32 A2 split into TF32 hi/lo in shared memory (lda a
+    multiple of 4) equals the one from the split copies (lda = m + 1 rules out the TMA
+    map of A2 itself) bit for bit, iteration after iteration."""
+    spec = synth.ClipSpec(H=60, W=80, n=300, k=12, r=17, rho=4, coverage=0.05, sigma=0.02,
+                          w_const=None, w_range=(5.0, 50.0), discs=True, seed=19)
+    clip = synth.make_clip(spec)
+    m, n, k, r = spec.m, spec.n, spec.k, spec.r
+    A32 = clip["A"].astype(np.float32)
+    W32 = clip["W1"].astype(np.float32)
+    tA = _dev(A32)
+    pad = torch.zeros((n, m + 1), dtype=torch.float32, device=DEV).T
+    pad[:m] = tA
+    tA_pad = pad[:m]
+    assert tA_pad.stride() == (1, m + 1)
+    outs = []
+    for A_ in (tA, tA_pad):
+        s = _solver(wlr, (m, n, k, r), wlr.WLR_PREC_FP32, stop=wlr.WLR_STOP_NONE)
+        s.set_data(A_, _dev(W32))
+        s.set_init(wlr.WLR_INIT_A1)
+        s.solve(0.0, 25)
+        Fh, _ = s.history()
+        outs.append((Fh, _x1(s, m, k, np.float32)))
+        s.close()
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert np.array_equal(outs[0][1], outs[1][1])
