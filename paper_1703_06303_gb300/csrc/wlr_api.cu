@@ -114,6 +114,7 @@ wlr_status wlr_set_data(wlr_handle h, const void* A, int64_t lda, const void* W1
   return guarded(h, [&] {
     if (dt != WLR_F32 && dt != WLR_F64) throw wlr::Fail{WLR_ERR_INVALID_ARG, "unknown dtype"};
     h->impl->set_data(A, lda, W1, ldw, dt, mem);
+    h->perm.clear();
     return WLR_OK;
   });
 }

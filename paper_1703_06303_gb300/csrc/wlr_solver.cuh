@@ -78,6 +78,7 @@ class SolverBase {
   };
   virtual View view(bool with_factors) = 0;
   virtual Dims dims() const = 0;
+  virtual cudaStream_t user_stream() const = 0;
 
   // Batched solve (wlr_solve_batched).  batch_ready: the next iterations replay as a
   // graph (data and init set, warm-up done).  batch_iterate: one iteration on the handle's
@@ -103,8 +104,18 @@ void set_global_error(const char* msg);
 
 }  // namespace wlr
 
-// The object behind a wlr_handle.
+// The object behind a wlr_handle.  perm: the caller's column order of A when the weighted
+// frames were given as an index set (wlr_set_data_cols): column q of the problem the solver
+// sees is the caller's column perm[q]; empty means the identity.
 struct wlr_handle_s {
   wlr::SolverBase* impl = nullptr;
   std::string last_error;
+  std::vector<int> perm;
+  void* perm_buf = nullptr;     // the permuted copy of A (device data)
+  size_t perm_bytes = 0;
+  int* perm_dev = nullptr;
+  ~wlr_handle_s() {
+    if (perm_buf) cudaFree(perm_buf);
+    if (perm_dev) cudaFree(perm_dev);
+  }
 };
