@@ -138,3 +138,26 @@ def test_state_buffers_are_checked(wlr):
     s.set_state(state)   # its own checkpoint is accepted
     for h in (s, other, f64):
         h.close()
+
+
+def test_bounded_wait_gives_up_and_the_context_stays_usable(wlr):
+    """A bounded mbarrier wait that nothing completes (10 ms limit) returns
+    WLR_ERR_DEVICE_TIMEOUT, twice in a row, and a solve on a fresh handle then runs."""
+    import time
+    for _ in range(2):
+        t0 = time.perf_counter()
+        st = wlr.wlr_selftest_bounded_wait(10_000_000)
+        assert st == wlr.WLR_ERR_DEVICE_TIMEOUT
+        assert time.perf_counter() - t0 < 5.0
+        assert "gave up" in wlr.wlr_last_error(None)
+    assert wlr.wlr_selftest_bounded_wait(0) == wlr.WLR_ERR_INVALID_ARG
+    rng = np.random.default_rng(3)
+    m, n, k, r = 500, 40, 4, 7
+    A = np.asfortranarray(rng.standard_normal((m, n)).astype(np.float32))
+    W1 = np.asfortranarray(rng.uniform(5, 50, (m, k)).astype(np.float32))
+    s = wlr.Solver(m, n, k, r, precision=wlr.WLR_PREC_FP32, stop=wlr.WLR_STOP_NONE)
+    s.set_data(torch.from_numpy(A).cuda(), torch.from_numpy(W1).cuda())
+    s.set_init(wlr.WLR_INIT_A1)
+    it, F, _ = s.solve(0.0, 10)
+    assert it == 10 and np.isfinite(F)
+    s.close()
