@@ -60,10 +60,17 @@ def _args():
     ap.add_argument("--p-star", type=int, default=0,
                     help="use this iteration count instead of calibrating it (profiling runs)")
     ap.add_argument("--workload", default="clip160x120",
-                    choices=["clip160x120", "clip320x240", "batched96"],
+                    choices=["clip160x120", "clip320x240", "batched96", "warmstart", "fig3c"],
                     help="clip160x120: the headline time-to-rel-obj run (default); "
                          "clip320x240: iterations/s on the 320x240, n=1000, k=50, r=60 clip; "
-                         "batched96: clip-iterations/s of wlr_solve_batched on 96 uneven clips")
+                         "batched96: clip-iterations/s of wlr_solve_batched on 96 uneven clips; "
+                         "warmstart: train the learned warm start on the GPU and measure what it "
+                         "saves on held-out clips; fig3c: runtime against the number of frames "
+                         "(Section 4.2, Fig. 3c: k = 15, r = k + 1), GPU next to the oracle")
+    ap.add_argument("--ws-train", type=int, default=1024, help="training clips (warmstart)")
+    ap.add_argument("--ws-steps", type=int, default=2000, help="Adam steps (warmstart)")
+    ap.add_argument("--ws-lr", type=float, default=1e-4, help="learning rate (warmstart)")
+    ap.add_argument("--ws-eval", type=int, default=32, help="held-out clips (warmstart)")
     ap.add_argument("--iters", type=int, default=0,
                     help="iterations per timed step of the clip320x240 / batched96 workloads")
     return ap.parse_args()
@@ -676,6 +683,273 @@ def run_ours(a):
     return 0
 
 
+def _oracle_seconds_per_iteration(spec_args: dict, n_iter: int, threads: int) -> float:
+    """Seconds per FP64 oracle iteration of Algorithm 1 on the clip ClipSpec(**spec_args)
+    from X1_0 = A1, in a fresh process using `threads` BLAS threads."""
+    code = f"""
+import sys, time, json
+sys.path.insert(0, {ROOT!r})
+import oracle
+from paper_1703_06303_gb300 import synth
+spec = synth.ClipSpec(**{spec_args!r})
+c = synth.make_clip(spec)
+A, W1 = c["A"], c["W1"]
+X = A[:, :spec.k].copy()
+X = oracle.swlr_step(A, W1, X, spec.r).X1_next
+t = time.perf_counter()
+for _ in range({n_iter}):
+    X = oracle.swlr_step(A, W1, X, spec.r).X1_next
+print(json.dumps({{"s": (time.perf_counter() - t) / {n_iter}}}))
+"""
+    env = dict(os.environ)
+    for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[v] = str(threads)
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])["s"]
+
+
+def run_fig3c(a):
+    """Analogue of Section 4.2's Fig. 3(c): runtime of sWLR against the number of frames n
+    (k = 15 weighted frames, r = k + 1), on clips of the first workload's generator (60x80
+    pixels, rank-3 background, 4% foreground, noise 0.01, W1 = 20).  Per n: the FP32 GPU
+    solve with the paper's relative stopping rule (Section 4.1) at eps = 1e-5 (at most 20000
+    iterations; the paper's eps = 1e-7 is not met within 20000 iterations on these clips),
+    its iterations and seconds (CUDA events), the FP32 and FP64 paths' milliseconds per
+    iteration, and the FP64 oracle's seconds per iteration on the host cores (a few
+    iterations), projected to the GPU's iteration count."""
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    import __graft_entry__ as g
+    g.build()
+    from paper_1703_06303_gb300 import synth, wlr
+    stream = torch.cuda.current_stream(dev)
+    threads = os.cpu_count() or 1
+    eps = 1e-5
+    sampler = ClockSampler(0)
+    sampler.start()
+    rows = []
+
+    def per_iteration_ms(sv, reps):
+        sv.set_init(wlr.WLR_INIT_A1)
+        sv.solve(0.0, 20)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sv.solve(0.0, reps)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    for n in (100, 200, 300, 400, 500, 600):
+        args = dict(H=60, W=80, n=n, k=15, r=16, rho=3, coverage=0.04, sigma=0.01, w_const=20.0, seed=7)
+        spec = synth.ClipSpec(**args)
+        c = synth.make_clip(spec)
+        tA = torch.from_numpy(np.asfortranarray(c["A"].astype(np.float32))).to(dev)
+        tW = torch.from_numpy(np.asfortranarray(c["W1"].astype(np.float32))).to(dev)
+        s = wlr.Solver(spec.m, n, 15, 16, precision=wlr.WLR_PREC_FP32, stop=wlr.WLR_STOP_PAPER, stream=stream)
+        s.set_data(tA, tW)
+
+        def run():
+            s.set_init(wlr.WLR_INIT_A1)
+            return s.solve(eps, 20000)
+
+        run()                          # warm-up: one whole solve
+        ts = []
+        for _ in range(max(1, a.steps)):
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            it, F, conv = run()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1) / 1e3)
+        s.close()
+        f32 = wlr.Solver(spec.m, n, 15, 16, precision=wlr.WLR_PREC_FP32, stop=wlr.WLR_STOP_NONE, stream=stream)
+        f32.set_data(tA, tW)
+        f32_ms = per_iteration_ms(f32, 1000)
+        f32.close()
+        f64 = wlr.Solver(spec.m, n, 15, 16, precision=wlr.WLR_PREC_FP64, stop=wlr.WLR_STOP_NONE, stream=stream)
+        tA64, tW64 = tA.double(), tW.double()
+        f64.set_data(tA64, tW64)
+        f64_ms = per_iteration_ms(f64, 200)
+        f64.close()
+        ora = _oracle_seconds_per_iteration(args, 3, threads) if not a.no_cpu_baseline else None
+        rows.append({"n": n, "iterations": it, "converged": conv, "gpu_fp32_s": statistics.mean(ts),
+                     "gpu_fp32_ms_per_iteration_with_stop_test": statistics.mean(ts) / max(it, 1) * 1e3,
+                     "gpu_fp32_ms_per_iteration": f32_ms, "gpu_fp64_ms_per_iteration": f64_ms,
+                     "oracle_s_per_iteration": ora,
+                     "oracle_projected_s": ora * it if ora is not None else None})
+        print(json.dumps(rows[-1]), file=sys.stderr)
+    clocks = sampler.stop()
+    line = {"metric": "sWLR runtime against the number of frames (Fig. 3c analogue), FP32 GPU path, paper stop rule",
+            "value": rows[-1]["gpu_fp32_s"], "unit": "s (n = 600)", "n_gpus": 1, "steps": a.steps,
+            "warmup": 1, "ms_per_step": rows[-1]["gpu_fp32_s"] * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "60x80-pixel clips of the first workload's generator, k = 15, r = 16, "
+                                   "n = 100..600, X1_0 = A1, stop: Error_p < eps or Error_p/||X_p|| < eps, "
+                                   f"eps = {eps:g}",
+                       "rows": rows, "oracle_cores": threads},
+            "clocks": clocks}
+    print(json.dumps(line))
+    return 0
+
+
+def run_warmstart(a):
+    """Row a9 and the combined form: train the warm-start network on the GPU (targets: the
+    method's own solutions of 30x40-pixel training clips), then on held-out clips
+    (1) FP64 iterations to rel-obj 1e-6 from X1_0 = A1 and from the learned start (alone and
+        with the objective-judged fallback to A1);
+    (2) time until every held-out clip reaches rel-obj 1e-6: the plain FP32 path (X1_0 = A1,
+        one clip after another) against learned/fallback start + FP32 iterations of all clips
+        in wlr_solve_batched launches + one final FP64 refinement sweep per clip (iterations
+        per clip calibrated beforehand on FP64-scored checkpoints every 250 iterations)."""
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    import __graft_entry__ as g
+    g.build()
+    from paper_1703_06303_gb300 import warmstart as W
+    from paper_1703_06303_gb300 import wlr
+    stream = torch.cuda.current_stream(dev)
+    sampler = ClockSampler(0)
+    sampler.start()
+    t_all = time.perf_counter()
+    net = wlr.WarmStartNet(max_frames=4096, seed=1)
+    W.damp_output(net, 0.1)
+    tr = W.load_clips([W.family_spec(100000 + i) for i in range(a.ws_train)], net, dev)
+    va = W.load_clips([W.family_spec(150000 + i) for i in range(32)], net, dev)
+    t0 = time.perf_counter()
+    W.solve_targets(tr + va, 4000)
+    torch.cuda.synchronize(dev)
+    t_targets = time.perf_counter() - t0
+    l0 = net.launches()
+    t0 = time.perf_counter()
+    hist = W.train(net, tr, a.ws_steps, batch=32, lr=a.ws_lr, val=va, log_every=250,
+                   log=lambda m_: print(m_, file=sys.stderr))
+    torch.cuda.synchronize(dev)
+    t_train = time.perf_counter() - t0
+    train_launches = net.launches() - l0
+    ev = W.load_clips([W.family_spec(200000 + i) for i in range(a.ws_eval)], net, dev)
+    iters = 20000
+    rows = W.evaluate(net, ev, iters)
+    rows_fb = W.evaluate(net, ev, iters, fallback=True)
+    summ, summ_fb = W.summarize(rows, iters), W.summarize(rows_fb, iters)
+    # (2) time to rel-obj 1e-6 of the whole held-out set.  Calibration (not timed): each
+    #     arm's iterations p* per clip, the first checkpoint whose iterate has an FP64
+    #     objective F~ within 1e-6 of F* (F* per clip from the FP64 runs of (1)).  Timed:
+    #     the plain path replays p* iterations per clip, one clip after another; the form
+    #     starts every clip from the network (with the fallback), advances all clips
+    #     together in wlr_solve_batched launches, each clip leaving the batch at its p*,
+    #     and ends each clip with one FP64 refinement sweep (wlr_refine).
+    fstar = {r["seed"]: min(r["F_star"], r2["F_star"]) for r, r2 in zip(rows, rows_fb)}
+    chunk, cap = 250, iters
+    TARGET_ = 1e-6
+
+    def calibrate(c, learned):
+        sp = c.spec
+        sv = wlr.Solver(sp.m, sp.n, sp.k, sp.r, precision=wlr.WLR_PREC_FP32, stop=wlr.WLR_STOP_NONE, stream=stream)
+        sv.set_data(c.A, c.W1)
+        if learned:
+            sv.set_init_learned(net, sp.H, sp.W, fallback=True)
+        else:
+            sv.set_init(wlr.WLR_INIT_A1)
+        p_, ok_ = 0, False
+        while p_ < cap:
+            sv.solve(0.0, chunk)
+            p_ += chunk
+            if (sv.objective() - fstar[sp.seed]) / fstar[sp.seed] <= TARGET_:
+                ok_ = True
+                break
+        sv.close()
+        return p_, ok_
+
+    cal_plain = [calibrate(c, False) for c in ev]
+    cal_form = [calibrate(c, True) for c in ev]
+    # plain FP32, one clip after another
+    t_plain = 0.0
+    for c, (p_, _) in zip(ev, cal_plain):
+        sp = c.spec
+        sv = wlr.Solver(sp.m, sp.n, sp.k, sp.r, precision=wlr.WLR_PREC_FP32, stop=wlr.WLR_STOP_NONE, stream=stream)
+        sv.set_data(c.A, c.W1)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sv.set_init(wlr.WLR_INIT_A1)
+        sv.solve(0.0, p_)
+        e1.record(stream)
+        e1.synchronize()
+        t_plain += e0.elapsed_time(e1) / 1e3
+        sv.close()
+    # the form: learned start with fallback, batched FP32 iterations, final FP64 sweep
+    hs = []
+    for c, (p_, _) in zip(ev, cal_form):
+        sp = c.spec
+        sv = wlr.Solver(sp.m, sp.n, sp.k, sp.r, precision=wlr.WLR_PREC_FP32, stop=wlr.WLR_STOP_NONE, stream=stream)
+        sv.set_data(c.A, c.W1)
+        hs.append([c, sv, p_, None])
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for item in hs:
+        item[1].set_init_learned(net, item[0].spec.H, item[0].spec.W, fallback=True)
+    t_init = time.perf_counter() - t0
+    p, t_ref = 0, 0.0
+    active = list(hs)
+    while active:
+        wlr.solve_batched([it_[1] for it_ in active], chunk)
+        p += chunk
+        keep = []
+        for it_ in active:
+            if p >= it_[2]:
+                t1 = time.perf_counter()
+                _, F1 = it_[1].refine()
+                t_ref += time.perf_counter() - t1
+                it_[3] = (F1 - fstar[it_[0].spec.seed]) / fstar[it_[0].spec.seed]
+            else:
+                keep.append(it_)
+        active = keep
+    torch.cuda.synchronize(dev)
+    t_form = time.perf_counter() - t0
+    refined_ok = sum(1 for it_ in hs if it_[3] is not None and it_[3] <= TARGET_)
+    for it_ in hs:
+        it_[1].close()
+    t_iter = t_form - t_init - t_ref
+    plain_reached = sum(ok for _, ok in cal_plain)
+    done_at = {c.spec.seed: p_ for c, (p_, ok) in zip(ev, cal_form) if ok}
+    p_plain = [p_ for p_, _ in cal_plain]
+    clocks = sampler.stop()
+    line = {"metric": "time to rel-obj 1e-6 of every held-out clip: learned+mixed+batched vs plain FP32",
+            "value": t_form, "unit": "s", "n_gpus": 1, "steps": 1, "warmup": 0,
+            "ms_per_step": t_form * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64 refine", "data": "synthetic",
+            "config": {"workload": f"{a.ws_eval} held-out 30x40-pixel clips, n~U[40,100], k~U[3,12], r=k+U[2,8]",
+                       "training": {"clips": a.ws_train, "target_iters": 4000, "steps": a.ws_steps,
+                                    "lr": a.ws_lr, "targets_s": t_targets, "train_s": t_train,
+                                    "network_launches": train_launches, "history": hist},
+                       "held_out_fp64_iterations": {"learned": summ, "learned_with_fallback": summ_fb},
+                       "time_to_target": {
+                           "plain_fp32_one_by_one_s": t_plain, "plain_reached": plain_reached,
+                           "plain_iterations_mean": float(np.mean(p_plain)),
+                           "form_s": t_form, "form_init_s": t_init, "form_batched_iterations_s": t_iter,
+                           "form_refine_s": t_ref, "form_reached": len(done_at),
+                           "form_reached_after_refine": refined_ok,
+                           "form_iterations_mean": float(np.mean(list(done_at.values()))) if done_at else None,
+                           "ratio_plain_over_form": t_plain / t_form if t_form > 0 else None,
+                           "checkpoint_every": chunk, "cap_iterations": cap},
+                       "wall_s": time.perf_counter() - t_all},
+            "clocks": clocks}
+    net.close()
+    print(json.dumps(line))
+    return 0
+
+
 def _gemm_report(kk, gt, m, n2, k, peaks, hbm_peak, hbm_src):
     """TFLOP/s of the two tensor-core contractions against the TF32 peak (the measured
     bf16 peak x the nominal TF32/BF16 ratio 1.1/2.25).
@@ -703,12 +977,13 @@ def _gemm_report(kk, gt, m, n2, k, peaks, hbm_peak, hbm_src):
     if gt:
         ms = gt[0] / gt[1]
         f_alg = 2 * m * k * (k + n2)
-        b_ = 8 * m * (n2 + k)
+        # A2 read once as FP32 (split into TF32 hi/lo in shared memory) + Q1 as a TF32 pair
+        b_ = 4 * m * n2 + 8 * m * k
         out["a2_Q1tQ1A2"] = {"kernel": "gram_tf32x3_t", "ms": ms, "algorithmic_flops": f_alg,
                              "tflops": f_alg / ms / 1e9, "frac": f_alg / ms / 1e9 / tf32,
                              "bytes": b_, "gbs": b_ / ms / 1e6, "hbm_frac": b_ / ms / 1e6 / hbm_peak,
                              "hbm_peak_source": f"{hbm_src} hbm_gbs",
-                             "note": "HBM-bound: 2 k (k + n2) flops per 8 (n2 + k) bytes of a row"}
+                             "note": "HBM-bound: 2 k (k + n2) flops per 4 n2 + 8 k bytes of a row"}
     return out
 
 
@@ -746,6 +1021,10 @@ def main():
                               "unavailable": "the oracle is timed on the clip160x120 workload only"}))
             return 0
         return run_reference(a)
+    if a.workload == "warmstart":
+        return run_warmstart(a)
+    if a.workload == "fig3c":
+        return run_fig3c(a)
     if a.workload != "clip160x120":
         return run_secondary(a)
     return run_ours(a)

@@ -112,6 +112,21 @@ wlr_status wlr_create(wlr_handle* out, int64_t m, int64_t n, int64_t k, int64_t 
 wlr_status wlr_set_data(wlr_handle h, const void* A, int64_t lda, const void* W1,
                         int64_t ldw, wlr_dtype dt, wlr_memory mem);
 
+/* wlr_set_data with the weighted frames at arbitrary columns: cols (host, k distinct
+ * indices in [0, n)) lists the columns of A that are weighted, in the order of W1's
+ * columns.  Eq. 5 and Algorithm 1 take them as the first k columns; the library permutes A
+ * to (A(:, cols), the other columns in increasing order) (a copy it owns for device data),
+ * so X1 follows the order of cols and X2 that of the other columns; wlr_get_x returns
+ * X = (X1, X2) in the caller's column order.  A later wlr_set_data resets the order to the
+ * identity.  Errors as wlr_set_data, and WLR_ERR_INVALID_ARG for a bad index set. */
+wlr_status wlr_set_data_cols(wlr_handle h, const void* A, int64_t lda, const void* W1,
+                             int64_t ldw, wlr_dtype dt, wlr_memory mem, const int32_t* cols);
+
+/* The whole approximation X (m x n, leading dimension ldx >= m, dtype dt, memory mem) in the
+ * caller's column order: the weighted columns hold X1, the others X2 = X1 C + D with C, D
+ * recomputed for the current X1 (Algorithm 1's output).  Synchronises. */
+wlr_status wlr_get_x(wlr_handle h, void* X, int64_t ldx, wlr_dtype dt, wlr_memory mem);
+
 /* Set X1_0 (Algorithm 1, initialisation).  X1_0 (m x k, leading dimension ldx, dtype
  * dt, memory mem) is read only for WLR_INIT_USER and may be NULL otherwise.  Resets
  * the iteration counter and the subspace warm start. */
@@ -267,6 +282,16 @@ wlr_status wlr_x1_update_noalloc(const float* A, int64_t lda, const float* W1, i
                                  const float* C, const float* Vs, float* X1_next,
                                  double* wterm, int* status, void* cuda_stream);
 
+/* Self-test of the bounded device waits.  The paper has no counterpart: the tensor-core
+ * kernels of this library wait on shared-memory barriers with a time limit (2 s), after
+ * which they record an error bit and return, and the handle reports
+ * WLR_ERR_DEVICE_TIMEOUT.  This call runs that same wait, limited to limit_ns (1 .. 2e9)
+ * nanoseconds, on a barrier that nothing completes, on cuda_stream (NULL = the legacy
+ * default stream), with no copy, MMA or tensor memory involved.  It returns
+ * WLR_ERR_DEVICE_TIMEOUT when the wait gave up as designed (the expected result) and the
+ * GPU context stays usable; WLR_OK would mean the limit did not work.  Synchronises. */
+wlr_status wlr_selftest_bounded_wait(int64_t limit_ns, void* cuda_stream);
+
 /* Number of kernels this handle has launched (graph replays count each node). */
 int64_t wlr_kernel_launches(wlr_handle h);
 
@@ -281,13 +306,16 @@ int64_t wlr_kernel_launches(wlr_handle h);
  *                                columns / their mean
  *   relu(conv 3x3 stride 2, 2 -> c1) -> relu(conv 3x3 stride 2, c1 -> c2) -> f_j (D values)
  *   z_j = [f_j | mean of f over the clip's frames] -> relu(fc1: 2D -> hidden) -> fc2 -> omega_j
- *   Omega (n x r_max) = the rows omega_j;  basis U = A Omega(:, 1:r)  (m x r, full resolution)
+ *   Omega (n x r_max) = the rows omega_j;  basis U = [A1 | 0] + A Omega(:, 1:r) / n
+ *                                (m x r, full resolution: the weighted frames plus mixtures)
  *   X1_0(:, a) = U (U^T D_a U)^{-1} U^T D_a A1(:, a),  D_a = diag(W1(:, a)^2)
  *
  * The weighted projection minimises the first term of Eq. 5 over X1 with columns in
- * span(U).  Weights are kept in float (master copy, updated by Adam) and used in bfloat16
+ * span(U).  That term keeps X1 close to A1, so the solution's span holds A1's columns up to
+ * small corrections: the network predicts those corrections and the r - k other
+ * directions.  Weights are kept in float (master copy, updated by Adam) and used in bfloat16
  * (round to nearest even) by every forward and backward kernel; all sums are float.
- * Training minimises ||P_Y - P_V||_F^2 / (2r), Y = A Omega(:, 1:r), against the column space
+ * Training minimises ||P_Y - P_V||_F^2 / (2r), Y = U of the clip, against the column space
  * V of a converged solution (wlr_get_basis).  Network tensors are row-major:
  * X (frames, 2, h, w), Omega (frames, r_max).  Device pointers unless stated.
  * ------------------------------------------------------------------------------------ */
@@ -303,7 +331,9 @@ typedef struct {
 /* Network with weights N(0, 2/fan_in) from seed (SplitMix64 + Box-Muller as for
  * WLR_INIT_RANDOM, one stream per parameter index), biases 0, Adam moments 0.  max_frames
  * bounds the frames of one forward/backward call (activation buffers are allocated here).
- * stream: cudaStream_t or NULL (the library's own).  WLR_ERR_INVALID_ARG for a bad shape. */
+ * stream: the cudaStream_t all of the network's work is queued on (NULL = the legacy
+ * default stream); the calls that return host data or whose host arguments are copied
+ * synchronise it.  WLR_ERR_INVALID_ARG for a bad shape. */
 wlr_status wlr_ws_create(wlr_ws_net* out, const wlr_ws_shape* shape, int32_t max_frames,
                          uint64_t seed, void* stream);
 wlr_status wlr_ws_destroy(wlr_ws_net net);
@@ -330,12 +360,13 @@ wlr_status wlr_ws_prepare(wlr_ws_net net, const float* A, int64_t lda, const flo
 wlr_status wlr_ws_forward(wlr_ws_net net, const float* X, int32_t frames,
                           const int32_t* clip_start, int32_t nclips, float* Omega);
 
-/* Loss of one clip and its gradient: Y = A Omega_c(:, 1:r) with A (m x n, lda) and
- * Omega_c (n x r_max, the clip's rows of Omega), V (m x r, column-major, ldv >= m, orthonormal
- * columns).  Adds ||P_Y - P_V||_F^2 / (2r) to *loss (device double) and writes
- * dOmega_c = d loss / d Omega_c (n x r_max; zero beyond column r).  1 <= r <= min(r_max, n). */
+/* Loss of one clip and its gradient: Y = [A1 | 0] + A Omega_c(:, 1:r) / n with A (m x n, lda),
+ * A1 its first k columns, Omega_c (n x r_max, the clip's rows of Omega), V (m x r,
+ * column-major, ldv >= m, orthonormal columns).  Adds ||P_Y - P_V||_F^2 / (2r) to *loss
+ * (device double) and writes dOmega_c = d loss / d Omega_c (n x r_max; zero beyond column
+ * r).  0 <= k <= r <= min(r_max, n). */
 wlr_status wlr_ws_loss(wlr_ws_net net, const float* A, int64_t lda, int32_t m, int32_t n,
-                       const float* Omega_c, int32_t r, const float* V, int64_t ldv,
+                       int32_t k, const float* Omega_c, int32_t r, const float* V, int64_t ldv,
                        double* loss, float* dOmega_c);
 
 /* Backward pass of the last forward call: gradients of sum(dOmega o Omega) with respect to
@@ -357,11 +388,14 @@ int64_t wlr_ws_launches(wlr_ws_net net);
 wlr_status wlr_get_basis(wlr_handle h, float* V, int64_t ldv);
 
 /* Initialise X1 from the network (replaces wlr_set_init): X = prepared input of the handle's
- * data (frames H x W, H W = m), Omega = forward pass, U = A Omega(:, 1:r), then X1_0 the
- * weighted projection above (Gram matrices and solves in double, with a ridge of 1e-12 of
- * the trace).  Needs r <= r_max and n <= max_frames; resets the iteration like wlr_set_init.
- * Float handles only.  Synchronises. */
-wlr_status wlr_set_init_learned(wlr_handle h, wlr_ws_net net, int32_t H, int32_t W);
+ * data (frames H x W, H W = m), Omega = forward pass, U = [A1 | 0] + A Omega(:, 1:r) / n,
+ * then X1_0 the weighted projection above (Gram matrices and solves in double, with a ridge
+ * of 1e-12 of the trace).  With fallback != 0 the objective F_0 = F(X1_0, C_0, D_0) of one
+ * iteration from this start and from X1_0 = A1 (the value wlr_step returns) are compared and
+ * the lower start is kept (A1 on a tie); *used_learned (may be NULL) says which.  Needs r <= r_max and n <= max_frames; resets the
+ * iteration like wlr_set_init.  Float handles only.  Synchronises. */
+wlr_status wlr_set_init_learned(wlr_handle h, wlr_ws_net net, int32_t H, int32_t W,
+                                int32_t fallback, int32_t* used_learned);
 
 #ifdef __cplusplus
 }

@@ -19,7 +19,7 @@ BUILD = os.path.join(ROOT, "_build")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libwlr.so")
 
-SOURCES = ["wlr_api.cu", "wlr_solver_f32.cu", "wlr_solver_f64.cu", "wlr_noalloc.cu", "wlr_warmstart.cu"]
+SOURCES = ["wlr_api.cu", "wlr_solver_f32.cu", "wlr_solver_f64.cu", "wlr_noalloc.cu", "wlr_warmstart.cu", "wlr_cols.cu", "wlr_selftest.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

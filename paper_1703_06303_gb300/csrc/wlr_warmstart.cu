@@ -1,7 +1,7 @@
 // Learned warm start of the sWLR iteration (declared in include/wlr.h): a small conv + MLP
 // network that maps a downsampled clip and its weights to frame-mixing weights Omega, whose
-// basis U = A Omega(:, 1:r) starts Algorithm 1 ("Initialize (X1)_0") from the weighted
-// projection of A1 onto span(U).  Everything here runs in this file's kernels: input
+// basis U = [A1 | 0] + A Omega(:, 1:r) / n starts Algorithm 1 ("Initialize (X1)_0") from the
+// weighted projection of A1 onto span(U).  Everything here runs in this file's kernels: input
 // preparation, the two stride-2 convolutions, the clip-context pooling, the two
 // fully-connected layers (a tiled float GEMM reading bfloat16 weights), their backward
 // passes, Adam, the projector-distance loss with its gradient, the basis of a solution
@@ -391,18 +391,22 @@ void gemm(cudaStream_t st, const float* A, int64_t lda, const TB* B, int64_t ldb
 }
 
 // ------------------------------------------------------------------ tall-skinny algebra
-// Y (m x r, column-major, ldy) = A (m x n, lda) Om(:, 0:r), Om row-major n x ldo
+// Y (m x r, column-major, ldy) = [A1 | 0] + A (m x n, lda) Om(:, 0:r) / n, Om row-major
+// n x ldo: the k weighted frames plus frame mixtures
 template <typename TO>
-__global__ void basis_from_omega(const float* __restrict__ A, int64_t lda, int m, int n,
+__global__ void basis_from_omega(const float* __restrict__ A, int64_t lda, int m, int n, int k,
                                  const float* __restrict__ Om, int ldo, int r, TO* __restrict__ Y,
                                  int64_t ldy) {
   const int64_t total = (int64_t)m * r;
+  const double inv_n = 1.0 / n;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int c = (int)(t / m);
     const int i = (int)(t - (int64_t)c * m);
     double s = 0.0;
     for (int j = 0; j < n; ++j) s += (double)A[i + (int64_t)j * lda] * Om[(int64_t)j * ldo + c];
+    s *= inv_n;
+    if (c < k) s += (double)A[i + (int64_t)c * lda];
     Y[i + (int64_t)c * ldy] = (TO)s;
   }
 }
@@ -568,10 +572,10 @@ __global__ void form_dy(const float* __restrict__ V, int64_t ldv, const float* _
   }
 }
 
-// dOm (n x rmax row-major): dOm[j][c] = sum_i A[i][j] dY[i][c] for c < r, else 0.
+// dOm (n x rmax row-major): dOm[j][c] = scale sum_i A[i][j] dY[i][c] for c < r, else 0.
 // Block per frame j; each thread sums rows for 8 columns at a time.
 __global__ void omega_grad(const float* __restrict__ A, int64_t lda, int m, const float* __restrict__ dY,
-                           int r, int rmax, float* __restrict__ dOm) {
+                           int r, int rmax, double scale, float* __restrict__ dOm) {
   __shared__ double sh[32];
   const int j = blockIdx.x;
   const float* Aj = A + (int64_t)j * lda;
@@ -590,7 +594,7 @@ __global__ void omega_grad(const float* __restrict__ A, int64_t lda, int m, cons
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       const double v = block_sum_double(acc[u], sh);
-      if (threadIdx.x == 0 && c0 + u < rmax) dOm[(int64_t)j * rmax + c0 + u] = c0 + u < r ? (float)v : 0.f;
+      if (threadIdx.x == 0 && c0 + u < rmax) dOm[(int64_t)j * rmax + c0 + u] = c0 + u < r ? (float)(scale * v) : 0.f;
       __syncthreads();
     }
   }
@@ -918,12 +922,9 @@ wlr_status wlr_ws_create(wlr_ws_net* out, const wlr_ws_shape* shape, int32_t max
     net->lay = layout_of(S);
     net->np = net->lay.off[8];
     net->max_frames = max_frames;
-    if (stream) {
-      net->stream = (cudaStream_t)stream;
-    } else {
-      WLR_CUDA(cudaStreamCreateWithFlags(&net->stream, cudaStreamNonBlocking));
-      net->own_stream = true;
-    }
+    // NULL: the legacy default stream, so that the network's work is ordered with the
+    // caller's default-stream work (as the solver handles order theirs)
+    net->stream = (cudaStream_t)stream;
     setup_smem_limits();
     const int64_t np = net->np;
     net->P = net->alloc<float>(np);
@@ -1102,14 +1103,14 @@ wlr_status wlr_ws_adam(wlr_ws_net net, float lr, float beta1, float beta2, float
   });
 }
 
-wlr_status wlr_ws_loss(wlr_ws_net net, const float* A, int64_t lda, int32_t m, int32_t n,
+wlr_status wlr_ws_loss(wlr_ws_net net, const float* A, int64_t lda, int32_t m, int32_t n, int32_t k,
                        const float* Omega_c, int32_t r, const float* V, int64_t ldv, double* loss,
                        float* dOmega_c) {
   return net_guard(net, [&]() -> wlr_status {
     const Shape& S = net->sh;
     if (!A || !Omega_c || !V || !loss || !dOmega_c) throw Fail{WLR_ERR_INVALID_ARG, "NULL pointer"};
-    if (m < 1 || n < 1 || r < 1 || r > S.rmax || r > n || lda < m || ldv < m)
-      throw Fail{WLR_ERR_INVALID_ARG, "need 1 <= r <= min(r_max, n), lda, ldv >= m"};
+    if (m < 1 || n < 1 || r < 1 || r > S.rmax || r > n || k < 0 || k > r || lda < m || ldv < m)
+      throw Fail{WLR_ERR_INVALID_ARG, "need 0 <= k <= r <= min(r_max, n), lda, ldv >= m"};
     cudaStream_t st = net->stream;
     const int nblk = (m + GR - 1) / GR;
     size_t off = 0;
@@ -1123,13 +1124,13 @@ wlr_status wlr_ws_loss(wlr_ws_net net, const float* A, int64_t lda, int32_t m, i
     double* part = (double*)(base + off); off += bP;
     double* GT = (double*)(base + off); off += bG;
     float* P12 = (float*)(base + off);
-    basis_from_omega<float><<<grid_for((int64_t)m * r), 256, 0, st>>>(A, lda, m, n, Omega_c, S.rmax, r, Y, m);
+    basis_from_omega<float><<<grid_for((int64_t)m * r), 256, 0, st>>>(A, lda, m, n, k, Omega_c, S.rmax, r, Y, m);
     check_launch(net, 1);
     gram(net, st, Y, false, m, 0, r, Y, false, m, 0, r, nullptr, 0, m, 1, part, GT);           // G = Y^T Y
     gram(net, st, V, false, ldv, 0, r, Y, false, m, 0, r, nullptr, 0, m, 1, part, GT + r * r); // T = V^T Y
     loss_small<<<1, 256, sizeof(double) * (4 * r * r + r), st>>>(GT, r, loss, P12, P12 + r * r);
     form_dy<<<grid_for((int64_t)m * r), 256, 0, st>>>(V, ldv, Y, m, r, P12, P12 + r * r, dY);
-    omega_grad<<<n, 256, 0, st>>>(A, lda, m, dY, r, S.rmax, dOmega_c);
+    omega_grad<<<n, 256, 0, st>>>(A, lda, m, dY, r, S.rmax, 1.0 / n, dOmega_c);
     check_launch(net, 3);
     return WLR_OK;
   });
@@ -1189,7 +1190,9 @@ wlr_status wlr_get_basis(wlr_handle h, float* V, int64_t ldv) {
   });
 }
 
-wlr_status wlr_set_init_learned(wlr_handle h, wlr_ws_net net, int32_t H, int32_t W) {
+wlr_status wlr_set_init_learned(wlr_handle h, wlr_ws_net net, int32_t H, int32_t W, int32_t fallback,
+                                int32_t* used_learned) {
+  if (used_learned) *used_learned = 0;
   if (!net) {
     if (h) h->last_error = "NULL network";
     return WLR_ERR_INVALID_ARG;
@@ -1234,7 +1237,7 @@ wlr_status wlr_set_init_learned(wlr_handle h, wlr_ws_net net, int32_t H, int32_t
     st = wlr_ws_forward(net, X, n, cs, 1, Om);
     if (st != WLR_OK) throw Fail{st, net->last_error};
     cudaStream_t s = net->stream;
-    basis_from_omega<double><<<grid_for((int64_t)m * r), 256, 0, s>>>(A, v.lda, m, n, Om, S.rmax, r, U, m);
+    basis_from_omega<double><<<grid_for((int64_t)m * r), 256, 0, s>>>(A, v.lda, m, n, k, Om, S.rmax, r, U, m);
     check_launch(net, 1);
     // per weighted frame a: [U^T D_a U | U^T D_a A1(:, a)] (r x r, then r), D_a = W1(:, a)^2
     {
@@ -1251,6 +1254,21 @@ wlr_status wlr_set_init_learned(wlr_handle h, wlr_ws_net net, int32_t H, int32_t
     }
     WLR_CUDA(cudaStreamSynchronize(s));
     h->impl->set_init(WLR_INIT_USER, X1, m, WLR_F32, WLR_MEM_DEVICE, 0);
+    bool learned = true;
+    if (fallback) {
+      // the objective judges the two starts: F_0 = F(X1_0, C_0, D_0) of one iteration from
+      // each (the value wlr_step returns); the plain start wins ties
+      double FL = 0.0, FA = 0.0;
+      h->impl->step(&FL);
+      h->impl->set_init(WLR_INIT_A1, nullptr, 0, WLR_F32, WLR_MEM_DEVICE, 0);
+      h->impl->step(&FA);
+      if (FL < FA) h->impl->set_init(WLR_INIT_USER, X1, m, WLR_F32, WLR_MEM_DEVICE, 0);
+      else {
+        h->impl->set_init(WLR_INIT_A1, nullptr, 0, WLR_F32, WLR_MEM_DEVICE, 0);
+        learned = false;
+      }
+    }
+    if (used_learned) *used_learned = learned ? 1 : 0;
     return WLR_OK;
   });
 }

@@ -98,12 +98,15 @@ def _load():
         "wlr_ws_set_params": (i32, [H, P, i32]),
         "wlr_ws_prepare": (i32, [H, P, i64, P, i64, i32, i32, i32, i32, P]),
         "wlr_ws_forward": (i32, [H, P, i32, P, i32, P]),
-        "wlr_ws_loss": (i32, [H, P, i64, i32, i32, P, i32, P, i64, P, P]),
+        "wlr_ws_loss": (i32, [H, P, i64, i32, i32, i32, P, i32, P, i64, P, P]),
         "wlr_ws_backward": (i32, [H, P]),
         "wlr_ws_adam": (i32, [H, ct.c_float, ct.c_float, ct.c_float, ct.c_float, ct.c_float]),
         "wlr_ws_launches": (i64, [H]),
         "wlr_get_basis": (i32, [H, P, i64]),
-        "wlr_set_init_learned": (i32, [H, H, i32, i32]),
+        "wlr_set_data_cols": (i32, [H, P, i64, P, i64, i32, i32, P]),
+        "wlr_selftest_bounded_wait": (i32, [i64, P]),
+        "wlr_get_x": (i32, [H, P, i64, i32, i32]),
+        "wlr_set_init_learned": (i32, [H, H, i32, i32, i32, ct.POINTER(i32)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -124,6 +127,7 @@ EXPORTED = (
     "wlr_ws_create", "wlr_ws_destroy", "wlr_ws_param_count", "wlr_ws_get_params",
     "wlr_ws_get_grads", "wlr_ws_set_params", "wlr_ws_prepare", "wlr_ws_forward", "wlr_ws_loss",
     "wlr_ws_backward", "wlr_ws_adam", "wlr_ws_launches", "wlr_get_basis", "wlr_set_init_learned",
+    "wlr_set_data_cols", "wlr_get_x", "wlr_selftest_bounded_wait",
 )
 
 
@@ -206,6 +210,31 @@ def wlr_set_data(h, A, W1):
     if dta != dtw or mema != memw:
         raise ValueError("A and W1 must share dtype and memory kind")
     return _check(_lib.wlr_set_data(h, pa, lda, pw, ldw, dta, mema), h)
+
+
+def wlr_set_data_cols(h, A, W1, cols):
+    """wlr_set_data with the weighted frames at the columns `cols` of A (W1's column order)."""
+    pa, lda, dta, mema, ka = _matrix(A)
+    pw, ldw, dtw, memw, kw = _matrix(W1)
+    if dta != dtw or mema != memw:
+        raise ValueError("A and W1 must share dtype and memory kind")
+    c = np.ascontiguousarray(cols, dtype=np.int32)
+    if c.ndim != 1 or c.size != W1.shape[1]:
+        raise ValueError("cols must list one column of A per column of W1")
+    return _check(_lib.wlr_set_data_cols(h, pa, lda, pw, ldw, dta, mema, c.ctypes.data), h)
+
+
+def wlr_get_x(h, X):
+    """X = (X1, X2) in the caller's column order (m x n, column-major)."""
+    if isinstance(X, np.ndarray) and not X.flags.f_contiguous:
+        raise ValueError("NumPy outputs must be Fortran-ordered")
+    p, ld, dt, mem, _keep = _matrix(X)
+    _check(_lib.wlr_get_x(h, p, ld, dt, mem), h)
+
+
+def wlr_selftest_bounded_wait(limit_ns=10_000_000, stream=None):
+    """Status of the bounded-wait self-test (WLR_ERR_DEVICE_TIMEOUT is the expected one)."""
+    return int(_lib.wlr_selftest_bounded_wait(int(limit_ns), _stream_ptr(stream)))
 
 
 def wlr_set_init(h, kind=WLR_INIT_A1, X1_0=None, seed=0):
@@ -480,14 +509,14 @@ def wlr_ws_forward(net, X, clip_start, Omega):
                                    _dev_f32(Omega, "Omega")), net)
 
 
-def wlr_ws_loss(net, A, Omega_c, r, V, loss, dOmega_c):
+def wlr_ws_loss(net, A, k, Omega_c, r, V, loss, dOmega_c):
     """Adds the clip's loss to loss (1-element float64 CUDA tensor); writes dOmega_c."""
     pa, lda, dta, mema, _ = _matrix(A)
     pv, ldv, dtv, memv, _ = _matrix(V)
     if {dta, dtv} != {WLR_F32} or {mema, memv} != {WLR_MEM_DEVICE}:
         raise ValueError("A and V must be float32 CUDA tensors")
     m, n = A.shape
-    _net_check(_lib.wlr_ws_loss(net, pa, lda, int(m), int(n), _dev_f32(Omega_c, "Omega_c"), int(r),
+    _net_check(_lib.wlr_ws_loss(net, pa, lda, int(m), int(n), int(k), _dev_f32(Omega_c, "Omega_c"), int(r),
                                 pv, ldv, loss.data_ptr(), _dev_f32(dOmega_c, "dOmega_c")), net)
 
 
@@ -512,8 +541,12 @@ def wlr_get_basis(h, V):
     _check(_lib.wlr_get_basis(h, p, ld), h)
 
 
-def wlr_set_init_learned(h, net, H, W):
-    _check(_lib.wlr_set_init_learned(h, net, int(H), int(W)), h)
+def wlr_set_init_learned(h, net, H, W, fallback=False):
+    """X1_0 from the network; with fallback, the start with the lower FP64 objective among
+    it and A1.  Returns True when the network's start is used."""
+    used = ct.c_int32(0)
+    _check(_lib.wlr_set_init_learned(h, net, int(H), int(W), 1 if fallback else 0, ct.byref(used)), h)
+    return bool(used.value)
 
 
 class WarmStartNet:
@@ -521,6 +554,11 @@ class WarmStartNet:
 
     def __init__(self, h=30, w=40, c1=16, c2=32, hidden=384, r_max=64, max_frames=4096, seed=0,
                  stream=None):
+        # by default the network works on torch's current stream, so its kernels are
+        # ordered with the torch operations that make its inputs and read its outputs
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream()
         self.shape = (h, w, c1, c2, hidden, r_max)
         self.h, self.w, self.r_max = h, w, r_max
         self.net = wlr_ws_create(h, w, c1, c2, hidden, r_max, max_frames, seed, stream)
@@ -540,8 +578,8 @@ class WarmStartNet:
     def forward(self, X, clip_start, Omega):
         wlr_ws_forward(self.net, X, clip_start, Omega)
 
-    def loss(self, A, Omega_c, r, V, loss, dOmega_c):
-        wlr_ws_loss(self.net, A, Omega_c, r, V, loss, dOmega_c)
+    def loss(self, A, k, Omega_c, r, V, loss, dOmega_c):
+        wlr_ws_loss(self.net, A, k, Omega_c, r, V, loss, dOmega_c)
 
     def backward(self, dOmega):
         wlr_ws_backward(self.net, dOmega)
@@ -584,6 +622,13 @@ class Solver:
     def set_init(self, kind=WLR_INIT_A1, X1_0=None, seed=0):
         return wlr_set_init(self.h, kind, X1_0, seed)
 
+    def set_data_cols(self, A, W1, cols):
+        self._data = (A, W1)
+        return wlr_set_data_cols(self.h, A, W1, cols)
+
+    def x(self, X):
+        return wlr_get_x(self.h, X)
+
     def step(self, want_objective=True):
         return wlr_step(self.h, want_objective)
 
@@ -602,8 +647,8 @@ class Solver:
     def basis(self, V):
         return wlr_get_basis(self.h, V)
 
-    def set_init_learned(self, net, H, W):
-        return wlr_set_init_learned(self.h, net.net if isinstance(net, WarmStartNet) else net, H, W)
+    def set_init_learned(self, net, H, W, fallback=False):
+        return wlr_set_init_learned(self.h, net.net if isinstance(net, WarmStartNet) else net, H, W, fallback)
 
     def factors(self):
         return wlr_get_factors(self.h, self.k, self.n - self.k, self.r - self.k)

@@ -125,8 +125,8 @@ def test_frames_of_other_clips_do_not_interact(wlr):
     net.close()
 
 
-@pytest.mark.parametrize("r", [1, 6, 20])
-def test_loss_and_gradient_match_oracle(wlr, r):
+@pytest.mark.parametrize("r,k", [(1, 1), (6, 2), (20, 0), (20, 7)])
+def test_loss_and_gradient_match_oracle(wlr, r, k):
     rng = np.random.default_rng(7 + r)
     m, n = 1200, 40
     A = rng.standard_normal((m, n)).astype(np.float32)
@@ -135,8 +135,8 @@ def test_loss_and_gradient_match_oracle(wlr, r):
     net = wlr.WarmStartNet(**SHAPE, max_frames=64)
     loss = torch.zeros(1, dtype=torch.float64, device=DEV)
     dOm = torch.full((n, 64), np.nan, dtype=torch.float32, device=DEV)
-    net.loss(_col(A), _rows(Om), r, _col(V.astype(np.float32)), loss, dOm)
-    Lw, dw = ows.omega_loss(A.astype(np.float64), Om.astype(np.float64), r, V.astype(np.float32).astype(np.float64))
+    net.loss(_col(A), k, _rows(Om), r, _col(V.astype(np.float32)), loss, dOm)
+    Lw, dw = ows.omega_loss(A.astype(np.float64), Om.astype(np.float64), r, V.astype(np.float32).astype(np.float64), k)
     assert abs(loss.item() - Lw) <= 1e-5 * max(Lw, 1e-3)
     got = dOm.cpu().numpy()
     assert np.all(got[:, r:] == 0.0)
@@ -206,7 +206,7 @@ def test_learned_init_is_the_weighted_projection(wlr):
     net.prepare(tA, tW, H, W, k, X)
     Om = torch.empty((n, 64), dtype=torch.float32, device=DEV)
     net.forward(X, [0, n], Om)
-    U = A.astype(np.float64) @ Om.cpu().numpy().astype(np.float64)[:, :r]
+    U = ows.omega_basis(A.astype(np.float64), Om.cpu().numpy().astype(np.float64), r, k)
     want = ows.warm_start_x1_weighted(A[:, :k].astype(np.float64), U, W1.astype(np.float64))
     assert _rel_max(X1.astype(np.float64), want) < 1e-5
     assert s.iteration() == 0
@@ -233,6 +233,7 @@ def test_training_lowers_the_loss(wlr):
         net.prepare(tA, tW, H, W, k, X)
         clips.append((tA, X, V, n, r))
         s.close()
+    k_of = [3 + q for q in range(4)]
     Xall = torch.cat([c[1] for c in clips])
     starts = np.cumsum([0] + [c[3] for c in clips])
     F = int(starts[-1])
@@ -245,10 +246,36 @@ def test_training_lowers_the_loss(wlr):
         loss.zero_()
         for c, (tA, _, V, n, r) in enumerate(clips):
             a, b = int(starts[c]), int(starts[c + 1])
-            net.loss(tA, Om[a:b], r, V, loss, dOm[a:b])
+            net.loss(tA, k_of[c], Om[a:b], r, V, loss, dOm[a:b])
         hist.append(loss.item() / len(clips))
         net.backward(dOm)
         net.adam(1e-3, grad_scale=1.0 / len(clips))
     assert all(np.isfinite(hist))
     assert hist[-1] < 0.7 * hist[0], hist
+    net.close()
+
+
+def test_fallback_keeps_the_start_with_the_lower_objective(wlr):
+    # an untrained network's start lies far above X1_0 = A1 in F~: the fallback keeps A1
+    H, W, n, k, r = 30, 40, 30, 4, 8
+    A, W1 = _clip(H, W, n, k, r, 14)
+    _, flat = _oracle_params(11)
+    net = wlr.WarmStartNet(**SHAPE, max_frames=64)
+    net.set_params(flat)
+    tA, tW = _col(A), _col(W1)
+    s = wlr.Solver(H * W, n, k, r, precision=wlr.WLR_PREC_FP32, stop=wlr.WLR_STOP_NONE)
+    s.set_data(tA, tW)
+    assert s.set_init_learned(net, H, W, fallback=False) is True
+    XL = np.zeros((H * W, k), dtype=np.float32, order="F")
+    s.result(XL)
+    F_learned = s.step()
+    s.set_init(wlr.WLR_INIT_A1)
+    F_a1 = s.step()
+    used = s.set_init_learned(net, H, W, fallback=True)
+    assert used == (F_learned < F_a1)
+    assert s.iteration() == 0
+    X1 = np.zeros((H * W, k), dtype=np.float32, order="F")
+    s.result(X1)
+    assert np.array_equal(X1, XL if used else A[:, :k])
+    s.close()
     net.close()
