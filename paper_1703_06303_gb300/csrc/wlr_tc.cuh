@@ -166,12 +166,15 @@ static __global__ void form_q_split(const float* __restrict__ X1, int64_t ldx, c
 // the MMAs.  Column tile 0 uses Y1 (= Q1, q1 columns) as Y, tiles t >= 1 use columns
 // (t-1)*128 .. of Y2 (= A2).
 constexpr int TN = 32;                                   // MMA N for up to 32 columns of X
-constexpr int T_STAGES = 3;
+constexpr int T_STAGES = 4;
+// warps that split FP32 A2 tiles: 4, or 2 for N = 64 (whose 8 epilogue warps keep 96 live
+// accumulator registers each; more threads would cap the registers below that)
+__host__ __device__ constexpr int t_split_warps(int tnv) { return tnv == TN ? 4 : 2; }
 constexpr int T_A_BYTES = 128 * BK * 4;                  // Y tile: 128 columns x 32 rows
 __host__ __device__ constexpr int t_b_bytes(int tnv) { return tnv * BK * 4; }   // X tile
 __host__ __device__ constexpr int t_stage_bytes(int tnv) { return 2 * T_A_BYTES + 2 * t_b_bytes(tnv); }
 __host__ __device__ constexpr int t_smem_bytes(int tnv) { return T_STAGES * t_stage_bytes(tnv) + 1024; }
-__host__ __device__ constexpr int t_threads(int tnv) { return 32 * (4 * (tnv / 32) + 2); }
+__host__ __device__ constexpr int t_threads(int tnv) { return 32 * (4 * (tnv / 32) + 2 + t_split_warps(tnv)); }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
@@ -200,11 +203,13 @@ __device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) 
 
 //
 // With split != 0 the column tiles of Y2 (= A2) come from the FP32 matrix itself (mY2f):
-// TMA brings the FP32 tile into the hi slot of the stage, and the epilogue warps, between
-// two slab read-backs, replace it in place by its TF32 high part and write the low part to
-// the lo slot at the same (swizzled) offsets, then release the stage to the MMA warp.  The
-// values are those of the split copies, so the result is the same bit for bit, while one
-// pass over A2 reads half the bytes (and the row pass reads the same FP32 A2).
+// TMA brings the FP32 tile into the hi slot of the stage, and the split warps
+// (t_split_warps, running ahead of the MMA as far as the stages allow) replace it in place by its TF32
+// high part and write the low part to the lo slot at the same (swizzled) offsets, then
+// release the stage to the MMA warp.  The values are those of the split copies, so the
+// result is the same bit for bit, while one pass over A2 reads half the bytes (and the row
+// pass reads the same FP32 A2).  Warps: epilogue 0 .. NEPI-1, TMA NEPI, MMA NEPI+1, split
+// the rest.
 template <int TNV>
 static __global__ void __launch_bounds__(t_threads(TNV))
 gram_tf32x3_t(const __grid_constant__ CUtensorMap mY1h, const __grid_constant__ CUtensorMap mY1l,
@@ -214,6 +219,7 @@ gram_tf32x3_t(const __grid_constant__ CUtensorMap mY1h, const __grid_constant__ 
               int m, int P, int q1, int q2, int chunk_rows, double* __restrict__ part, int64_t pstride,
               int* __restrict__ err) {
   constexpr int NEPI = 4 * (TNV / 32);                  // epilogue warps
+  constexpr int NSPL = t_split_warps(TNV);              // split warps
   constexpr int T_B_BYTES = t_b_bytes(TNV), T_STAGE_BYTES = t_stage_bytes(TNV);
   constexpr unsigned T_TMEM_COLS = 2 * TNV;             // two TNV-column accumulators
   extern __shared__ unsigned char smem_raw[];
@@ -242,7 +248,7 @@ gram_tf32x3_t(const __grid_constant__ CUtensorMap mY1h, const __grid_constant__ 
     for (int s = 0; s < T_STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
-      mbar_init(&splt[s], NEPI);
+      mbar_init(&splt[s], NSPL);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&accf[b], 1);
@@ -264,6 +270,7 @@ gram_tf32x3_t(const __grid_constant__ CUtensorMap mY1h, const __grid_constant__ 
 
   if (warp == NEPI) {
     if (lane == 0) {
+      int issued = 0;
       for (int kb = 0; kb < nkb; ++kb) {
         const int s = kb % T_STAGES;
         if (kb >= T_STAGES && !mbar_wait(&empty[s], (unsigned)((kb / T_STAGES - 1) & 1))) {
@@ -271,6 +278,7 @@ gram_tf32x3_t(const __grid_constant__ CUtensorMap mY1h, const __grid_constant__ 
           break;
         }
         if (*(volatile int*)&fail) break;
+        issued = kb + 1;
         const int x = i_begin + kb * BK;
         if (do_split) {
           mbar_expect_tx(&full[s], T_A_BYTES + 2 * T_B_BYTES);
@@ -283,10 +291,15 @@ gram_tf32x3_t(const __grid_constant__ CUtensorMap mY1h, const __grid_constant__ 
         tma_load_2d(base_ptr + (b_addr(s, 0) - base), &mXh, &full[s], x, 0);
         tma_load_2d(base_ptr + (b_addr(s, 1) - base), &mXl, &full[s], x, 0);
       }
+      // drain: the last fill issued into each stage has landed before the CTA exits (in
+      // the normal path these phases completed long ago)
+      for (int kb = issued - 1; kb >= 0 && kb >= issued - T_STAGES; --kb)
+        if (!mbar_wait(&full[kb % T_STAGES], (unsigned)((kb / T_STAGES) & 1))) atomicOr(&fail, 1);
     }
   } else if (warp == NEPI + 1) {
     if (lane == 0) {
       constexpr uint32_t idesc = idesc_tf32(128, TNV);
+      int committed = 0;
       for (int kb = 0; kb < nkb; ++kb) {
         const int s = kb % T_STAGES, b = kb & 1;
         const unsigned ph = (unsigned)((kb / T_STAGES) & 1);
@@ -308,6 +321,41 @@ gram_tf32x3_t(const __grid_constant__ CUtensorMap mY1h, const __grid_constant__ 
         }
         mma_commit(&empty[s]);
         mma_commit(&accf[b]);
+        committed = kb + 1;
+      }
+      // drain: the last commit tracks every MMA this thread issued; wait for it before the
+      // tensor memory is freed
+      if (committed > 0) {
+        const int kl = committed - 1;
+        if (!mbar_wait(&accf[kl & 1], (unsigned)((kl / 2) & 1))) atomicOr(&fail, 1);
+      }
+    }
+  } else if (warp >= NEPI + 2) {
+    // split warps: stage kb's FP32 tile (hi slot) -> TF32 hi in place and lo in the lo slot,
+    // 16 bytes per step over the split warps' threads
+    if (do_split) {
+      const int t = threadIdx.x - 32 * (NEPI + 2);
+      for (int kb = 0; kb < nkb; ++kb) {
+        const int s = kb % T_STAGES;
+        if (!mbar_wait(&full[s], (unsigned)((kb / T_STAGES) & 1))) {
+          atomicOr(&fail, 1);
+          break;
+        }
+        float4* yh = reinterpret_cast<float4*>(base_ptr + (a_addr(s, 0) - base));
+        float4* yl = reinterpret_cast<float4*>(base_ptr + (a_addr(s, 1) - base));
+        for (int e = t; e < T_A_BYTES / 16; e += 32 * NSPL) {
+          const float4 x = yh[e];
+          float4 h, l;
+          h.x = round_tf32(x.x); l.x = round_tf32(x.x - h.x);
+          h.y = round_tf32(x.y); l.y = round_tf32(x.y - h.y);
+          h.z = round_tf32(x.z); l.z = round_tf32(x.z - h.z);
+          h.w = round_tf32(x.w); l.w = round_tf32(x.w - h.w);
+          yh[e] = h;
+          yl[e] = l;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&splt[s]);
       }
     }
   } else {
@@ -321,35 +369,8 @@ gram_tf32x3_t(const __grid_constant__ CUtensorMap mY1h, const __grid_constant__ 
       lo[a] = 0.f;
     }
     bool ok = true;
-    // split of stage kb: the FP32 tile (hi slot) -> TF32 hi in place and lo in the lo slot,
-    // 16 bytes per step over the epilogue warps' threads
-    auto split_stage = [&](int kb) -> bool {
-      const int s = kb % T_STAGES;
-      if (!mbar_wait(&full[s], (unsigned)((kb / T_STAGES) & 1))) return false;
-      float4* yh = reinterpret_cast<float4*>(base_ptr + (a_addr(s, 0) - base));
-      float4* yl = reinterpret_cast<float4*>(base_ptr + (a_addr(s, 1) - base));
-      for (int e = threadIdx.x; e < T_A_BYTES / 16; e += 32 * NEPI) {
-        const float4 x = yh[e];
-        float4 h, l;
-        h.x = round_tf32(x.x); l.x = round_tf32(x.x - h.x);
-        h.y = round_tf32(x.y); l.y = round_tf32(x.y - h.y);
-        h.z = round_tf32(x.z); l.z = round_tf32(x.z - h.z);
-        h.w = round_tf32(x.w); l.w = round_tf32(x.w - h.w);
-        yh[e] = h;
-        yl[e] = l;
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&splt[s]);
-      return true;
-    };
-    if (do_split && nkb > 0) ok = split_stage(0);
     for (int kb = 0; ok && kb < nkb; ++kb) {
       const int b = kb & 1;
-      if (do_split && kb + 1 < nkb && !split_stage(kb + 1)) {
-        ok = false;
-        break;
-      }
       if (!mbar_wait(&accf[b], (unsigned)((kb / 2) & 1))) {
         ok = false;
         break;
@@ -412,7 +433,7 @@ gram_kk_tf32x3(const __grid_constant__ CUtensorMap mh, const __grid_constant__ C
                int chunk_rows, const int2* __restrict__ pairs, int npairs, double* __restrict__ part,
                int* __restrict__ err) {
   extern __shared__ unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t full[K_STAGES], empty[K_STAGES], accf[2], acce[2];
+  __shared__ __align__(8) uint64_t full[K_STAGES], empty[K_STAGES], accf[2], acce[2], drain_bar;
   __shared__ unsigned tmem_base;
   __shared__ int fail;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -438,6 +459,7 @@ gram_kk_tf32x3(const __grid_constant__ CUtensorMap mh, const __grid_constant__ C
       mbar_init(&accf[b], 1);
       mbar_init(&acce[b], 8);
     }
+    mbar_init(&drain_bar, 1);
     fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -454,6 +476,7 @@ gram_kk_tf32x3(const __grid_constant__ CUtensorMap mh, const __grid_constant__ C
 
   if (warp == 8) {
     if (lane == 0) {
+      int issued = 0;
       for (int kb = 0; kb < nkb; ++kb) {
         const int s = kb % K_STAGES;
         if (kb >= K_STAGES && !mbar_wait(&empty[s], (unsigned)((kb / K_STAGES - 1) & 1))) {
@@ -461,6 +484,7 @@ gram_kk_tf32x3(const __grid_constant__ CUtensorMap mh, const __grid_constant__ C
           break;
         }
         if (*(volatile int*)&fail) break;
+        issued = kb + 1;
         mbar_expect_tx(&full[s], K_STAGE_BYTES);
         const int x = i_begin + kb * BK;
         tma_load_2d(base_ptr + (a_addr(s, 0) - base), &mh, &full[s], x, pb.x * 128);
@@ -468,10 +492,14 @@ gram_kk_tf32x3(const __grid_constant__ CUtensorMap mh, const __grid_constant__ C
         tma_load_2d(base_ptr + (b_addr(s, 0) - base), &mh64, &full[s], x, pb.y * KN);
         tma_load_2d(base_ptr + (b_addr(s, 1) - base), &ml64, &full[s], x, pb.y * KN);
       }
+      // drain the last fill of each stage (see gram_tf32x3_t)
+      for (int kb = issued - 1; kb >= 0 && kb >= issued - K_STAGES; --kb)
+        if (!mbar_wait(&full[kb % K_STAGES], (unsigned)((kb / K_STAGES) & 1))) atomicOr(&fail, 1);
     }
   } else if (warp == 9) {
     if (lane == 0) {
       constexpr uint32_t idesc = idesc_tf32(128, KN);
+      int last_slab = -1;
       for (int kb = 0; kb < nkb; ++kb) {
         const int s = kb % K_STAGES, slab = kb / K_SLAB, b = slab & 1;
         const bool first = kb % K_SLAB == 0;
@@ -492,7 +520,25 @@ gram_kk_tf32x3(const __grid_constant__ CUtensorMap mh, const __grid_constant__ C
           mma_tf32(d, al + adv, bh + adv, idesc, 1u);
         }
         mma_commit(&empty[s]);
-        if (kb % K_SLAB == K_SLAB - 1 || kb == nkb - 1) mma_commit(&accf[b]);
+        if (kb % K_SLAB == K_SLAB - 1 || kb == nkb - 1) {
+          mma_commit(&accf[b]);
+          last_slab = slab;
+        } else {
+          last_slab = -1;   // MMAs issued after the last slab commit: committed below
+        }
+      }
+      // drain: a commit after the last MMA tracks all of them; wait for it before the
+      // tensor memory is freed
+      if (nkb > 0) {
+        if (last_slab < 0) {
+          // (only after a failure: the loop stopped inside a slab)
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           smem_u32(&drain_bar))
+                       : "memory");
+          if (!mbar_wait(&drain_bar, 0u)) atomicOr(&fail, 1);
+        } else if (!mbar_wait(&accf[last_slab & 1], (unsigned)((last_slab / 2) & 1))) {
+          atomicOr(&fail, 1);
+        }
       }
     }
   } else {

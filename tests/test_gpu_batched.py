@@ -45,12 +45,12 @@ def _clip(i, H, W, n, k, r):
     return synth.make_clip(spec)
 
 
-def _make(wlr, i, shape, use_graph=1):
+def _make(wlr, i, shape, use_graph=1, eig_iters=0):
     H, W, n, k, r, prec = shape
     clip = _clip(i, H, W, n, k, r)
     dt = np.float32 if prec == "fp32" else np.float64
     p = wlr.WLR_PREC_FP32 if prec == "fp32" else wlr.WLR_PREC_FP64
-    kw = dict(eig_block=32, eig_iters_cold=400, eig_iters=60) if prec == "fp64" else {}
+    kw = dict(eig_block=32, eig_iters_cold=400, eig_iters=60) if prec == "fp64" else dict(eig_iters=eig_iters)
     s = wlr.Solver(H * W, n, k, r, precision=p, stop=wlr.WLR_STOP_NONE, use_graph=use_graph, **kw)
     A = torch.from_numpy(np.asfortranarray(clip["A"].astype(dt))).to(DEV)
     Wt = torch.from_numpy(np.asfortranarray(clip["W1"].astype(dt))).to(DEV)
@@ -129,4 +129,27 @@ def test_batched_errors(wlr):
         wlr.solve_batched([s0, fresh], 6)
     assert e.value.status == wlr.WLR_ERR_NOT_READY and e.value.index == 1
     for s in (s0, s1, fresh):
+        s.close()
+
+
+@pytest.mark.parametrize("eig_iters,tol", [(3, 1e-4), (0, 3e-4)])
+def test_batched_fp32_members_follow_the_oracle(wlr, eig_iters, tol):
+    """FP32 members after 30 iterations of the joined graph launches, against the FP64
+    oracle's own 30 iterations of Algorithm 1 on the same clip from X1_0 = A1: the FP64
+    objective of each GPU iterate within tol of the oracle's F_30, for a k > 32 member and
+    an s = 0 member too.  With 3 warm subspace steps per iteration the rank-(r-k) step
+    tracks the oracle's exact SVD and the reduced-precision tolerance 1e-4 holds; the
+    default single warm step trails it in the early transient (1.2e-4 measured at p = 30 on
+    the 15 x 20 member; within 1.5e-5 over 2500 iterations on the 160 x 120 clip)."""
+    shapes = [SHAPES[0], SHAPES[1], SHAPES[2], SHAPES[3], SHAPES[4]]
+    made = [_make(wlr, 20 + i, sh, eig_iters=eig_iters) for i, sh in enumerate(shapes)]
+    wlr.solve_batched([s for s, _ in made], 30)
+    for (s, clip), sh in zip(made, shapes):
+        H, W, n, k, r, _ = sh
+        A = clip["A"].astype(np.float32).astype(np.float64)
+        W1 = clip["W1"].astype(np.float32).astype(np.float64)
+        ref = oracle.swlr(A, W1, r, A[:, :k].copy(), max_iter=30, stop="none")
+        F = s.objective()
+        assert s.iteration() == 30
+        assert abs(F - ref.F[30]) <= tol * ref.F[30], (sh, F, ref.F[30])
         s.close()

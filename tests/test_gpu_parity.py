@@ -3,8 +3,12 @@
 Tolerances:
   * FP64 path: 1e-10 relative (per result, max-abs error over max-abs value).
   * FP32 path: objective within 1e-4 relative of the oracle's value for the same X1;
-    per-step X1 within 2e-3 relative (FP32 arithmetic with a cond(X1) ~ 1e2..1e3
-    least-squares step: u * cond ~ 6e-8 * 1e3 * a few).
+    per-step X1 within 2e-3 relative as the bound u cond(row system) allows (FP32
+    arithmetic, cond ~ 1e2..1e3), and row by row: ||X1(i,:) - X1_ref(i,:)|| within `row`
+    of ||X1_ref(i,:)|| + 1e-2 median_i ||X1_ref(i,:)||, with `row` set about ten times above
+    the measured worst row (the arithmetic is deterministic): 2.4e-6 at 160 x 120,
+    1.9e-6 at 320 x 240, 4e-7 at k = 33 and 1.1e-3 at k = 64 (r = 70, the worst
+    conditioned of these cases).
 """
 import numpy as np
 import pytest
@@ -36,6 +40,12 @@ def _dev(a):
 
 def _rel(a, b):
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def _row_rel(a, b):
+    """Largest row error relative to the row's norm plus 1% of the median row norm."""
+    rn = np.linalg.norm(b, axis=1)
+    return float((np.linalg.norm(a - b, axis=1) / (rn + 1e-2 * np.median(rn))).max())
 
 
 def _solver(wlr, spec_or_dims, precision, **kw):
@@ -180,6 +190,7 @@ def test_fp32_step_full_size(wlr, config):
     X1 = _x1(s, spec.m, spec.k)
     assert abs(F - st.F) <= 1e-4 * st.F
     assert _rel(X1, st.X1_next) < 2e-3
+    assert _row_rel(X1, st.X1_next) < 3e-5
     s.close()
 
 
@@ -201,6 +212,7 @@ def test_fp32_step_wide_k(wlr, k):
     X1 = _x1(s, m, k)
     assert abs(F - st.F) <= 1e-4 * st.F
     assert _rel(X1, st.X1_next) < 2e-3
+    assert _row_rel(X1, st.X1_next) < {33: 5e-6, 64: 1e-2}[k]
     s.close()
 
 
