@@ -76,6 +76,11 @@ class SolverBase {
     cudaStream_t stream;
     bool fp64;
   };
+  // Start the rank-(r-k) subspace iteration from the given basis (n2 x b columns, float or
+  // double, column-major, device) instead of a random one: the first min(b, this b) columns
+  // are taken, the rest stay random.  Used by the FP64 scorer of a float handle, which then
+  // starts from the float iteration's own, nearly converged, subspace.
+  virtual void seed_subspace(const void* V, int b, bool fp64) = 0;
   virtual View view(bool with_factors) = 0;
   virtual Dims dims() const = 0;
   virtual cudaStream_t user_stream() const = 0;

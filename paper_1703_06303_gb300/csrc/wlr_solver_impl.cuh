@@ -272,10 +272,13 @@ class Solver final : public SolverBase {
       raise_err();
       return e6[0] + e6[5];
     }
-    // FP32 handle: score with an FP64 copy of the problem
+    // FP32 handle: score with an FP64 copy of the problem, its subspace iteration started
+    // from this handle's current basis (nearly converged; the random start needed hundreds
+    // of rounds to reach the same values)
     SolverBase* sc = scorer();
     // the scorer's stream waits on this stream, so the current X1 is complete
     sc->set_init(WLR_INIT_USER, X1buf_[cur_], d_.m, dtype_of<T>(), WLR_MEM_DEVICE, 0);
+    if (!eig_cold_) sc->seed_subspace(V_, d_.b, std::is_same<T, double>::value);
     return sc->objective_exact();
   }
   // An FP64 solver on the same data (widened from T), with the widest subspace block, used
@@ -301,6 +304,7 @@ class Solver final : public SolverBase {
     if (X1_out && ldx < d_.m) throw Fail{WLR_ERR_INVALID_ARG, "ldx must be >= m"};
     SolverBase* sc = scorer();
     sc->set_init(WLR_INIT_USER, X1buf_[cur_], d_.m, dtype_of<T>(), WLR_MEM_DEVICE, 0);
+    if (!eig_cold_) sc->seed_subspace(V_, d_.b, std::is_same<T, double>::value);
     const double F0 = sc->objective_exact();
     sc->step(nullptr);
     const double F1 = sc->objective_exact();
@@ -331,6 +335,20 @@ class Solver final : public SolverBase {
     raise_err_async();
   }
 
+  void seed_subspace(const void* V, int b, bool fp64) override {
+    need_init();
+    const int n2 = d_.n2, nb = std::min(b, d_.b);
+    if (d_.s == 0 || n2 == 0 || !V || nb < 1) return;
+    begin();
+    if (eig_cold_) eig_start();
+    if (fp64)
+      convert_copy<T, double><<<grid1d((int64_t)n2 * nb), 256, 0, stream_>>>(V_, n2, (const double*)V, n2, n2, nb);
+    else
+      convert_copy<T, float><<<grid1d((int64_t)n2 * nb), 256, 0, stream_>>>(V_, n2, (const float*)V, n2, n2, nb);
+    count(1);
+    eig_cold_ = false;
+    end();
+  }
   View view(bool with_factors) override {
     need_data();
     if (with_factors) {
