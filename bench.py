@@ -267,12 +267,12 @@ def run_secondary(a):
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
 
-    def load(spec):
+    def load(spec, autotune=0):
         c = synth.make_clip(spec)
         tA = torch.from_numpy(np.asfortranarray(c["A"].astype(np.float32))).to(dev)
         tW = torch.from_numpy(np.asfortranarray(c["W1"].astype(np.float32))).to(dev)
         sv = wlr.Solver(spec.m, spec.n, spec.k, spec.r, precision=wlr.WLR_PREC_FP32,
-                        stop=wlr.WLR_STOP_NONE, stream=stream)
+                        stop=wlr.WLR_STOP_NONE, stream=stream, autotune=autotune)
         sv.set_data(tA, tW)
         sv.set_init(wlr.WLR_INIT_A1)
         sv._keep = (tA, tW)
@@ -321,7 +321,9 @@ def run_secondary(a):
     else:
         specs = synth.batched_specs(96)
         iters = a.iters or 30
-        hs = [load(sp) for sp in specs]
+        t_at = time.perf_counter()
+        hs = [load(sp, autotune=1) for sp in specs]   # Gram row chunks by the autotuner
+        t_at = time.perf_counter() - t_at
         wlr.solve_batched(hs, 3)           # warm-up iterations, each clip alone
         for _ in range(a.warmup):
             wlr.solve_batched(hs, iters)
@@ -340,6 +342,9 @@ def run_secondary(a):
                 "config": {"workload": f"96 uneven clips, m in {ms}, n~U[100,800], k~U[5,40], r=k+U[3,10]",
                            "iterations_per_step": iters,
                            "one_clip_at_a_time": {"value": 96 * iters / ta, "ms_per_step": ta * 1e3},
+                           "launch_shapes": "per-iteration Gram row chunks from the autotuner "
+                                            "(options.autotune; set-up of the 96 handles "
+                                            f"including the timing: {t_at:.2f} s)",
                            "l2": "inputs larger than L2 (6.4 GB of clips)"},
                 "gpu_launches": launches, "clocks": clocks}
         for h in hs:

@@ -89,6 +89,12 @@ typedef struct {
   int32_t use_graph;      /* replay steady-state iterations as CUDA graphs (1): one     */
                           /* iteration per launch, three in wlr_solve with WLR_STOP_NONE */
   uint64_t seed;          /* seed of the random subspace start (and WLR_INIT_RANDOM)     */
+  int32_t autotune;       /* 1: the row chunks of the per-iteration tensor-core Gram are  */
+                          /* chosen by timing candidates at the first wlr_set_data of an  */
+                          /* (m, n-k, k) shape in the process (cached; handles of one     */
+                          /* shape share the choice, so they compute the same values);    */
+                          /* 0 (default): a fixed rule (whole waves of CTAs on the SMs).  */
+                          /* The paper has no counterpart.                                */
 } wlr_options;
 
 typedef struct wlr_handle_s* wlr_handle;

@@ -56,6 +56,7 @@ void wlr_default_options(wlr_options* opt) {
   opt->eig_iters_cold = 0;
   opt->use_graph = 1;
   opt->seed = 0x1703063032ull;
+  opt->autotune = 0;
 }
 
 wlr_status wlr_create(wlr_handle* out, int64_t m, int64_t n, int64_t k, int64_t r,

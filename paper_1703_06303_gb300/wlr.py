@@ -46,6 +46,7 @@ class wlr_options(ct.Structure):
         ("eig_iters_cold", ct.c_int32),
         ("use_graph", ct.c_int32),
         ("seed", ct.c_uint64),
+        ("autotune", ct.c_int32),
     ]
 
 
@@ -606,9 +607,11 @@ class Solver:
     """Convenience owner of one handle (destroyed with the object)."""
 
     def __init__(self, m, n, k, r, precision=WLR_PREC_FP32, stop=WLR_STOP_RELATIVE,
-                 eig_block=0, eig_iters=0, eig_iters_cold=0, use_graph=1, seed=None, stream=None):
+                 eig_block=0, eig_iters=0, eig_iters_cold=0, use_graph=1, seed=None, stream=None,
+                 autotune=0):
         o = wlr_default_options()
         o.precision, o.stop = precision, stop
+        o.autotune = autotune
         o.eig_block, o.eig_iters, o.eig_iters_cold, o.use_graph = eig_block, eig_iters, eig_iters_cold, use_graph
         if seed is not None:
             o.seed = seed

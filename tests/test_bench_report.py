@@ -22,7 +22,7 @@ def test_gemm_report_counts():
     assert abs(kk["tflops"] - kk["algorithmic_flops"] / 0.05e-3 / 1e12) < 1e-6
     g = rep["a2_Q1tQ1A2"]
     assert g["algorithmic_flops"] == 2 * m * k * (k + n2)
-    assert g["bytes"] == 8 * m * (n2 + k)
+    assert g["bytes"] == 4 * m * n2 + 8 * m * k        # FP32 A2 once + the Q1 pair
     assert abs(g["gbs"] - g["bytes"] / 0.02e-3 / 1e9) < 1e-6
     assert abs(g["hbm_frac"] - g["gbs"] / 7000.0) < 1e-12
 

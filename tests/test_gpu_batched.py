@@ -153,3 +153,30 @@ def test_batched_fp32_members_follow_the_oracle(wlr, eig_iters, tol):
         assert s.iteration() == 30
         assert abs(F - ref.F[30]) <= tol * ref.F[30], (sh, F, ref.F[30])
         s.close()
+
+
+def test_autotuned_handles_agree_and_follow_the_oracle(wlr):
+    """options.autotune: the first wlr_set_data of a shape times candidate row chunkings of
+    the per-iteration Gram and caches the fastest; a second handle of the same shape takes
+    the cached choice, so the two compute the same iterates bit for bit, and the objective
+    stays within the reduced-precision tolerance of the oracle's trajectory."""
+    H, W, n, k, r = 60, 80, 160, 10, 14
+    spec = synth.ClipSpec(H=H, W=W, n=n, k=k, r=r, rho=3, coverage=0.04, sigma=0.01, w_const=20.0, seed=777)
+    clip = synth.make_clip(spec)
+    A32 = np.asfortranarray(clip["A"].astype(np.float32))
+    W32 = np.asfortranarray(clip["W1"].astype(np.float32))
+    tA, tW = torch.from_numpy(A32).to(DEV), torch.from_numpy(W32).to(DEV)
+    hist = []
+    for _ in range(2):
+        s = wlr.Solver(spec.m, n, k, r, precision=wlr.WLR_PREC_FP32, stop=wlr.WLR_STOP_NONE, autotune=1,
+                       eig_iters=3)
+        s.set_data(tA, tW)
+        s.set_init(wlr.WLR_INIT_A1)
+        s.solve(0.0, 30)
+        Fh, _ = s.history()
+        hist.append((Fh, s.objective()))
+        s.close()
+    assert np.array_equal(hist[0][0], hist[1][0])
+    ref = oracle.swlr(A32.astype(np.float64), W32.astype(np.float64), r, A32[:, :k].astype(np.float64),
+                      max_iter=30, stop="none")
+    assert abs(hist[0][1] - ref.F[30]) <= 1e-4 * ref.F[30]
