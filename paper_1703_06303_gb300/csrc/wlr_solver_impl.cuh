@@ -2,7 +2,9 @@
 // Included by wlr_solver_f32.cu and wlr_solver_f64.cu, one instantiation each.
 #pragma once
 
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <vector>
 #include <climits>
 #include <algorithm>
@@ -892,16 +894,84 @@ class Solver final : public SolverBase {
       const int64_t pstride = (int64_t)k * k + (int64_t)k * n2;
       const CUtensorMap& mf = a2f_ok_ ? mA2f_ : mA2h_;
       const int split = a2f_ok_ ? 1 : 0;
-      if (tn_ == tc::TN)
-        tc::gram_tf32x3_t<tc::TN><<<g, tc::t_threads(tc::TN), tc::t_smem_bytes(tc::TN), stream_>>>(
-            mQh128_, mQl128_, mA2h_, mA2l_, mQh32_, mQl32_, mf, split, m, k, k, n2, ch_tc_.rows, part64_, pstride,
-            err_);
-      else
-        tc::gram_tf32x3_t<2 * tc::TN><<<g, tc::t_threads(2 * tc::TN), tc::t_smem_bytes(2 * tc::TN), stream_>>>(
-            mQh128_, mQl128_, mA2h_, mA2l_, mQh32_, mQl32_, mf, split, m, k, k, n2, ch_tc_.rows, part64_, pstride,
-            err_);
+      launch_gram_tc(ch_tc_);
     }
     count(1);
+  }
+  void launch_gram_tc(const Chunk& ch) {
+    const int m = d_.m, k = d_.k, n2 = d_.n2;
+    dim3 g(1 + cdiv(n2, 128), ch.nch);
+    const int64_t pstride = (int64_t)k * k + (int64_t)k * n2;
+    const CUtensorMap& mf = a2f_ok_ ? mA2f_ : mA2h_;
+    const int split = a2f_ok_ ? 1 : 0;
+    if (tn_ == tc::TN)
+      tc::gram_tf32x3_t<tc::TN><<<g, tc::t_threads(tc::TN), tc::t_smem_bytes(tc::TN), stream_>>>(
+          mQh128_, mQl128_, mA2h_, mA2l_, mQh32_, mQl32_, mf, split, m, k, k, n2, ch.rows, part64_, pstride, err_);
+    else
+      tc::gram_tf32x3_t<2 * tc::TN><<<g, tc::t_threads(2 * tc::TN), tc::t_smem_bytes(2 * tc::TN), stream_>>>(
+          mQh128_, mQl128_, mA2h_, mA2l_, mQh32_, mQl32_, mf, split, m, k, k, n2, ch.rows, part64_, pstride, err_);
+  }
+  // Autotuner of the per-iteration Gram's row chunks (options.autotune): the whole-wave
+  // rule's chunk count and its neighbours (half, two thirds, 3/2 and twice as many chunks)
+  // are each launched on this problem's own A2 (one warm-up, then three launches timed by
+  // CUDA events) and the fastest is kept, for every handle of this (m, n2, k) in the
+  // process.  The partials it writes are scratch (the next iteration rewrites them).
+  void autotune_gram() {
+    const int m = d_.m, k = d_.k, n2 = d_.n2;
+    static std::mutex mu;
+    static std::map<std::tuple<int, int, int, int>, Chunk> cache;
+    const auto key = std::make_tuple(m, n2, k, a2f_ok_ ? 1 : 0);
+    {
+      std::lock_guard<std::mutex> lock(mu);
+      auto it = cache.find(key);
+      if (it != cache.end()) {
+        ch_tc_ = it->second;
+        return;
+      }
+    }
+    auto chunk_of = [&](int n) {
+      n = std::max(1, std::min(128, n));
+      const int rows = std::max(32, ((cdiv(m, n) + 31) / 32) * 32);
+      return Chunk{cdiv(m, rows), rows};
+    };
+    const Chunk rule = ch_tc_;
+    std::vector<Chunk> cand = {rule};
+    for (int n : {rule.nch / 2, (2 * rule.nch) / 3, (3 * rule.nch) / 2, 2 * rule.nch}) {
+      const Chunk c = chunk_of(n);
+      bool dup = false;
+      for (const Chunk& e : cand) dup = dup || e.nch == c.nch;
+      if (!dup) cand.push_back(c);
+    }
+    size_t need = 0;
+    for (const Chunk& c : cand) need = std::max(need, (size_t)c.nch * ((size_t)k * k + (size_t)k * n2));
+    if (need > part_elems_) {
+      part64_ = dregrow(part64_, need);
+      part_elems_ = need;
+    }
+    cudaEvent_t e0, e1;
+    WLR_CUDA(cudaEventCreate(&e0));
+    WLR_CUDA(cudaEventCreate(&e1));
+    Chunk best = rule;
+    float best_ms = 1e30f;
+    for (const Chunk& c : cand) {
+      launch_gram_tc(c);
+      WLR_CUDA(cudaEventRecord(e0, stream_));
+      for (int rep = 0; rep < 3; ++rep) launch_gram_tc(c);
+      WLR_CUDA(cudaEventRecord(e1, stream_));
+      WLR_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      WLR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      count(4);
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = c;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ch_tc_ = best;
+    std::lock_guard<std::mutex> lock(mu);
+    cache.emplace(key, best);
   }
 
   // ------------------------------------------------------------------ kernels
@@ -950,6 +1020,7 @@ class Solver final : public SolverBase {
     reduce_partials<double><<<1, 32, 0, stream_>>>(wpart_scratch(nb), 1, nb, 1, normA2_, nullptr);
     count(2);
     tc_split_a2();
+    if (o_.autotune && use_tc_) autotune_gram();
     if (use_tc_k_) {
       tc_gram_k();
     } else {
@@ -1275,8 +1346,14 @@ class Solver final : public SolverBase {
       eig_start();
       eig_cold_ = false;
     }
+    // rounds of ten subspace steps until the Ritz values stop changing: every value to
+    // 1e-15 of the largest, or their sum (what F~ depends on: sum_{j <= s} sigma_j^2 and a
+    // D that is unique up to ties sigma_s = sigma_{s+1}) to 1e-14 of itself; with nearly
+    // equal sigma_s and sigma_{s+1} the single values can take hundreds of rounds while
+    // the sum has long settled
     const int s = d_.s;
     std::vector<T> prev(s, (T)0), now(s);
+    double sum_prev = 0.0;
     for (int round = 0; round < 400; ++round) {
       if (use_dstep_) dstep_run(10, true);
       else
@@ -1284,10 +1361,16 @@ class Solver final : public SolverBase {
       WLR_CUDA(cudaMemcpyAsync(hbuf_ + 128, theta_, sizeof(T) * s, cudaMemcpyDeviceToHost, stream_));
       WLR_CUDA(cudaStreamSynchronize(stream_));
       std::memcpy(now.data(), hbuf_ + 128, sizeof(T) * s);
-      double diff = 0, top = std::fabs((double)now[0]);
-      for (int c = 0; c < s; ++c) diff = std::max(diff, std::fabs((double)now[c] - (double)prev[c]));
+      double diff = 0, top = std::fabs((double)now[0]), sum = 0.0;
+      for (int c = 0; c < s; ++c) {
+        diff = std::max(diff, std::fabs((double)now[c] - (double)prev[c]));
+        sum += (double)now[c];
+      }
       prev = now;
-      if (round > 0 && diff <= 1e-15 * std::max(top, 1e-300)) break;
+      const bool settled = round > 0 && (diff <= 1e-15 * std::max(top, 1e-300) ||
+                                         std::fabs(sum - sum_prev) <= 1e-14 * std::max(std::fabs(sum), 1e-300));
+      sum_prev = sum;
+      if (settled) break;
     }
   }
 
