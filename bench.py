@@ -926,6 +926,38 @@ def run_warmstart(a):
     for it_ in hs:
         it_[1].close()
     t_iter = t_form - t_init - t_ref
+
+    # the same batched iterations and final sweep from X1_0 = A1 (the plain path's
+    # calibrated iterations): what batching and the FP64 sweep give without the network
+    def batched_from_a1():
+        hs_ = []
+        for c, (p_, _) in zip(ev, cal_plain):
+            sp = c.spec
+            sv = wlr.Solver(sp.m, sp.n, sp.k, sp.r, precision=wlr.WLR_PREC_FP32, stop=wlr.WLR_STOP_NONE, stream=stream)
+            sv.set_data(c.A, c.W1)
+            hs_.append([c, sv, p_])
+        torch.cuda.synchronize(dev)
+        t0_ = time.perf_counter()
+        for it_ in hs_:
+            it_[1].set_init(wlr.WLR_INIT_A1)
+        p_, act = 0, list(hs_)
+        while act:
+            wlr.solve_batched([it_[1] for it_ in act], chunk)
+            p_ += chunk
+            keep_ = []
+            for it_ in act:
+                if p_ >= it_[2]:
+                    it_[1].refine()
+                else:
+                    keep_.append(it_)
+            act = keep_
+        torch.cuda.synchronize(dev)
+        dt_ = time.perf_counter() - t0_
+        for it_ in hs_:
+            it_[1].close()
+        return dt_
+
+    t_a1_batched = batched_from_a1()
     plain_reached = sum(ok for _, ok in cal_plain)
     done_at = {c.spec.seed: p_ for c, (p_, ok) in zip(ev, cal_form) if ok}
     p_plain = [p_ for p_, _ in cal_plain]
@@ -947,6 +979,8 @@ def run_warmstart(a):
                            "form_reached_after_refine": refined_ok,
                            "form_iterations_mean": float(np.mean(list(done_at.values()))) if done_at else None,
                            "ratio_plain_over_form": t_plain / t_form if t_form > 0 else None,
+                           "a1_start_batched_with_sweep_s": t_a1_batched,
+                           "a1_start_batched_reached": plain_reached,
                            "checkpoint_every": chunk, "cap_iterations": cap},
                        "wall_s": time.perf_counter() - t_all},
             "clocks": clocks}
