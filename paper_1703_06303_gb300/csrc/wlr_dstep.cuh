@@ -530,6 +530,19 @@ __device__ __forceinline__ T cluster_sum(cgrp::cluster_group& cl, T* base, int e
   return (T)acc.value();
 }
 
+// The same sum over ranks 1 .. nc - 1 only (the front-stage kernel, whose CTA 0 owns no rows).
+template <typename T>
+__device__ __forceinline__ T cluster_sum_w(cgrp::cluster_group& cl, T* base, int e, int nc) {
+  T v[15];
+#pragma unroll
+  for (int u = 0; u < 15; ++u) v[u] = u + 1 < nc ? cl.map_shared_rank(base, u + 1)[e] : T(0);
+  WideAcc<T> acc;
+#pragma unroll
+  for (int u = 0; u < 15; ++u)
+    if (u + 1 < nc) acc.add(v[u]);
+  return (T)acc.value();
+}
+
 // (K V)(l, c) for all rows in double-float: one warp per (row l, group of KV_CG columns),
 // the lanes splitting the sum over j (K is symmetric, so row l of K is the contiguous
 // column l).  Each lane loads the K and V entries of KV_JM values of j before using them
@@ -804,6 +817,304 @@ dstep_cluster(DstepArgs<T> a) {
     if (e < k * k) a.G[e] = cluster_sum(cluster, Gp, e, nc);
     else a.CV[e - k * k] = cluster_sum(cluster, CVp, e - k * k, nc);
   }
+  // every CTA keeps its shared memory until the others have read it
+  cluster.sync();
+}
+
+// ------------------------------------------------------------------------------------
+// The steady-state step with the front stage (k <= 32), arranged so that the second
+// CholeskyQR factor does not hold up the products over the basis rows.  With
+// t = Q1^T A2 (the Gram's sums), B = (I + N) t and C = R^{-1} B:
+//   B V = (I + N) (t V)   and   B^T (B V) = t^T X,  X = (I + N)^T (B V),
+// so the partials of t V need only t.  CTA 0 owns no basis rows: it factors
+// Q1^T Q1 = (I + Lambda)(I + Lambda)^T (chol2_block) while CTAs 1 .. nc-1 form t V over
+// their rows; after one cluster barrier they form (I + N) and X from the summed t V and
+// their rows of Z = K V - t^T X, H and P.  CTA 0 then runs the Rayleigh-Ritz step while
+// the others form their columns of B, C (and ||B||^2, C C^T) in its shadow.  Same
+// quantities as dstep_cluster's front stage; only the order of the float sums differs.
+struct DfLayout {
+  size_t Tq, Th, Tl, Vr, Zh, Zl, Zr, Bs, Cs, Vsr, TVp, TV, BVx, Xs, HPp, Gp, CVp, Ml, NR, Wk, total;
+  template <typename T>
+  __host__ __device__ static DfLayout make(int k, int b, int s, int RL) {
+    return DfLayout(k, b, s, RL, (int)(sizeof(double) / sizeof(T)));
+  }
+  __host__ __device__ DfLayout(int k, int b, int s, int RL, int dw) {
+    const size_t ss = s > 0 ? s : 1;
+    size_t o = 0;
+    Tq = o;  o += (size_t)dw * k * RL;     // t(:, rows) in double, t(x, j) at Tq[(j - l0) k + x]
+    Th = o;  o += (size_t)k * RL;          // t(:, rows) as a T pair: high
+    Tl = o;  o += (size_t)k * RL;          // low
+    Vr = o;  o += (size_t)b * RL;          // V(rows), V(j, c) at Vr[c RL + j - l0]
+    Zh = o;  o += (size_t)b * RL;          // (K V)(rows), high
+    Zl = o;  o += (size_t)b * RL;          // low
+    Zr = o;  o += (size_t)RL * b;          // Z(rows), Zr[(j - l0) b + c]
+    Bs = o;  o += 2 * (size_t)k * RL;      // B(:, rows): high, low
+    Cs = o;  o += (size_t)RL * k;          // C(:, rows)
+    Vsr = o; o += (size_t)RL * ss;         // V_s(rows)
+    TVp = o; o += 2 * (size_t)k * b;       // partial t V (high, low)
+    TV = o;  o += 2 * (size_t)k * b;       // t V
+    BVx = o; o += 2 * (size_t)k * b;       // B V = (I + N) t V
+    Xs = o;  o += 2 * (size_t)k * b;       // X = (I + N)^T B V
+    HPp = o; o += 2 * (size_t)b * b;       // partial H, P
+    Gp = o;  o += (size_t)k * k;           // partial C C^T
+    CVp = o; o += (size_t)k * ss;          // partial C V_s
+    Ml = o;  o += 3 * (size_t)b * b;       // local copies of Y, Mv, Mz
+    NR = o;  o += 2 * (size_t)k * k;       // local copies of N and R^{-1}
+    Wk = o;  o += 10 * (size_t)DS_BM * DS_P;   // second factor, then Rayleigh-Ritz (CTA 0)
+    total = o;
+  }
+};
+__host__ __device__ inline int df_rows(int n2, int nc) { return (n2 + nc - 2) / (nc - 1); }
+
+template <typename T, int NE>
+__global__ void __launch_bounds__(DS_THREADS, 1)
+dstep_front(DstepArgs<T> a) {
+  extern __shared__ unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  cgrp::cluster_group cluster = cgrp::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int nc = (int)cluster.num_blocks();
+  const int tid = threadIdx.x;
+  const int n2 = a.n2, k = a.k, b = a.b, s = a.s, NP = a.NP;
+  const int RL = df_rows(n2, nc);
+  const int l0 = rank == 0 ? 0 : min(n2, (rank - 1) * RL);
+  const int l1 = rank == 0 ? 0 : min(n2, l0 + RL);
+  const int nr = l1 - l0;
+  const DfLayout L = DfLayout::make<T>(k, b, s, RL);
+  double* Tq = reinterpret_cast<double*>(sm + L.Tq);
+  T* Th = sm + L.Th;
+  T* Tl = sm + L.Tl;
+  T* Vr = sm + L.Vr;
+  T* Zh = sm + L.Zh;
+  T* Zl = sm + L.Zl;
+  T* Zr = sm + L.Zr;
+  T* Bs = sm + L.Bs;
+  T* Cs = sm + L.Cs;
+  T* Vsr = sm + L.Vsr;
+  T* TVp = sm + L.TVp;
+  T* TV = sm + L.TV;
+  T* BVx = sm + L.BVx;
+  T* Xs = sm + L.Xs;
+  T* HPp = sm + L.HPp;
+  T* Gp = sm + L.Gp;
+  T* CVp = sm + L.CVp;
+  T* Ml = sm + L.Ml;
+  T* Nl = sm + L.NR;
+  T* Rl = Nl + k * k;
+  T* Wk = sm + L.Wk;
+  const int kb = k * b;
+  constexpr bool kF = sizeof(T) == 4;
+  __shared__ double bsh[32];
+
+  // ---- inputs of the CTA's rows (one asynchronous group): t in double, V, K V
+  for (int e = tid; e < k * nr; e += DS_THREADS) cp_async_elem(Tq + e, a.S2T + (int64_t)(k + l0) * k + e, true);
+  for (int e = tid; e < b * nr; e += DS_THREADS) {
+    const int c = e / nr, rr = e % nr;
+    const int64_t g = l0 + rr + (int64_t)c * n2;
+    cp_async_elem(Vr + c * RL + rr, a.V + g, true);
+    cp_async_elem(Zh + c * RL + rr, a.ZKh + g, true);
+    if (a.ZKl) cp_async_elem(Zl + c * RL + rr, a.ZKl + g, true);
+  }
+  cp_async_commit();
+  if (rank == 0) {
+    // ---- (1) the second factor: N and R^{-1} into Wk (and global memory)
+    chol2_block<T, NE>(Wk, k, [&](int e) { return a.F2[e]; }, a.R1inv, a.Nout, a.Rinv, a.err);
+    if (tid == 0) a.bpart[0] = 0.0;
+    cp_async_wait<0>();
+  } else {
+    cp_async_wait<0>();
+    __syncthreads();
+    for (int v = tid; v < k * nr; v += DS_THREADS) {
+      const double t = Tq[v];
+      const T h = (T)t;
+      Th[v] = h;
+      Tl[v] = kF ? (T)(t - (double)h) : T(0);
+    }
+    __syncthreads();
+    // ---- (2) partial t V over the CTA's rows (double-float)
+    for (int e = tid; e < kb; e += DS_THREADS) {
+      const int x = e % k, c = e / k;
+      DfAcc<T> acc;
+      for (int rr = 0; rr < nr; ++rr) acc.add(Th[rr * k + x], Tl[rr * k + x], Vr[c * RL + rr]);
+      TVp[e] = acc.hi;
+      TVp[kb + e] = acc.lo;
+    }
+  }
+  cluster.sync();
+  if (rank > 0) {
+    // ---- (3) N and R^{-1} from CTA 0; t V summed in rank order; B V = t V + N t V and
+    // X = B V + N^T B V (the N products in T, added to the double-float sums)
+    {
+      const T* w0 = cluster.map_shared_rank(Wk, 0);
+      for (int e = tid; e < k * k; e += DS_THREADS) {
+        Nl[e] = w0[2 * DS_BM * DS_BM + e];
+        Rl[e] = w0[3 * DS_BM * DS_BM + e];
+      }
+    }
+    for (int e = tid; e < kb; e += DS_THREADS) {
+      T ph[15], pl[15];
+#pragma unroll
+      for (int u = 0; u < 15; ++u) {
+        if (u + 1 < nc) {
+          const T* rp = cluster.map_shared_rank(TVp, u + 1);
+          ph[u] = rp[e];
+          pl[u] = rp[kb + e];
+        }
+      }
+      DfAcc<T> acc;
+#pragma unroll
+      for (int u = 0; u < 15; ++u)
+        if (u + 1 < nc) acc.add_pair(ph[u], pl[u]);
+      TV[e] = acc.hi;
+      TV[kb + e] = acc.lo;
+    }
+    __syncthreads();
+    for (int e = tid; e < kb; e += DS_THREADS) {
+      const int x = e % k, c = e / k;
+      T corr = T(0);
+      for (int l = 0; l <= x; ++l) corr = fma(Nl[x * k + l], TV[l + c * k], corr);
+      DfAcc<T> acc;
+      acc.hi = TV[e];
+      acc.lo = TV[kb + e];
+      acc.add_pair(corr, T(0));
+      BVx[e] = acc.hi;
+      BVx[kb + e] = acc.lo;
+    }
+    __syncthreads();
+    for (int e = tid; e < kb; e += DS_THREADS) {
+      const int x = e % k, c = e / k;
+      T corr = T(0);
+      for (int l = x; l < k; ++l) corr = fma(Nl[l * k + x], BVx[l + c * k], corr);
+      DfAcc<T> acc;
+      acc.hi = BVx[e];
+      acc.lo = BVx[kb + e];
+      acc.add_pair(corr, T(0));
+      Xs[e] = acc.hi;
+      Xs[kb + e] = acc.lo;
+    }
+    __syncthreads();
+    // ---- Z(rows) = K V - t^T X, rounded to T after the subtraction
+    for (int e = tid; e < nr * b; e += DS_THREADS) {
+      const int rr = e % nr, c = e / nr;
+      DfAcc<T> acc;
+      acc.hi = Zh[c * RL + rr];
+      acc.lo = a.ZKl ? Zl[c * RL + rr] : T(0);
+      for (int x = 0; x < k; ++x) acc.sub2(Th[rr * k + x], Tl[rr * k + x], Xs[x + c * k], Xs[kb + x + c * k]);
+      Zr[rr * b + c] = acc.hi + acc.lo;
+    }
+    __syncthreads();
+    // ---- partial H = V^T Z and P = Z^T Z over the CTA's rows
+    for (int e = tid; e < b * b; e += DS_THREADS) {
+      const int c1 = e % b, c2 = e / b;
+      T h = T(0), p = T(0);
+      for (int rr = 0; rr < nr; ++rr) {
+        const T z2 = Zr[rr * b + c2];
+        h = fma(Vr[c1 * RL + rr], z2, h);
+        p = fma(Zr[rr * b + c1], z2, p);
+      }
+      HPp[e] = h;
+      HPp[b * b + e] = p;
+    }
+  }
+  cluster.sync();
+  if (rank == 0) {
+    // ---- (4) Rayleigh-Ritz on CTA 0 (H into work array 0, P into work array 4)
+    for (int e = tid; e < 2 * b * b; e += DS_THREADS) {
+      const T v = cluster_sum_w(cluster, HPp, e, nc);
+      const int f = e % (b * b), r_ = f % b, c_ = f / b;
+      Wk[(e < b * b ? 0 : 4 * DS_BM * DS_P) + r_ * DS_P + c_] = v;
+    }
+    __syncthreads();
+    ritz_step<T, NE>(Wk, b, a.sweeps, a.theta, a.resid, a.err);
+  } else {
+    // ---- meanwhile B = t + N t and C = R^{-1} B for the CTA's columns, ||B||^2 and the
+    // partial C C^T
+    double bn = 0.0;
+    for (int v = tid; v < k * nr; v += DS_THREADS) {
+      const int x = v % k, jj = v / k;
+      T corr = T(0);
+      for (int l = 0; l <= x; ++l) corr = fma(Nl[x * k + l], Th[jj * k + l], corr);
+      const double bv = Tq[v] + (double)corr;
+      const int64_t o = (int64_t)(l0 + jj) * k + x;
+      if (a.B64) a.B64[o] = bv;
+      if constexpr (kF) {
+        const float hi = (float)bv, lo = (float)(bv - (double)hi);
+        a.Bho[o] = hi;
+        a.Blo[o] = lo;
+        Bs[v] = hi;
+        Bs[k * RL + v] = lo;
+      } else {
+        Bs[v] = (T)bv;
+      }
+      bn += bv * bv;
+    }
+    __syncthreads();
+    for (int v = tid; v < k * nr; v += DS_THREADS) {
+      const int x = v % k, jj = v / k;
+      T cv = T(0);
+      for (int l = x; l < k; ++l) {
+        const T bl = kF ? Bs[jj * k + l] + Bs[k * RL + jj * k + l] : Bs[jj * k + l];
+        cv = fma(Rl[x * k + l], bl, cv);
+      }
+      Cs[v] = cv;
+      const int64_t o = (int64_t)(l0 + jj) * k + x;
+      a.Cout[o] = cv;
+      a.Z2[(int64_t)(l0 + jj) * NP + x] = cv;
+    }
+    bn = block_sum_double(bn, bsh);
+    if (tid == 0) a.bpart[rank] = bn;
+    __syncthreads();
+    for (int e = tid; e < k * k; e += DS_THREADS) {
+      const int x = e % k, y = e / k;
+      T v = T(0);
+      for (int rr = 0; rr < nr; ++rr) v = fma(Cs[rr * k + x], Cs[rr * k + y], v);
+      Gp[e] = v;
+    }
+  }
+  cluster.sync();
+  if (rank == 0) {
+    // ---- (5) G = C C^T over the workers' partials
+    for (int e = tid; e < k * k; e += DS_THREADS) a.G[e] = cluster_sum_w(cluster, Gp, e, nc);
+  } else {
+    // ---- next basis rows and Ritz vectors (Y, Mv, Mz from CTA 0), then partial C V_s
+    const T* w0 = cluster.map_shared_rank(Wk, 0);
+    T* Yl = Ml;
+    T* Mvl = Ml + b * b;
+    T* Mzl = Ml + 2 * b * b;
+    for (int e = tid; e < b * b; e += DS_THREADS) {
+      Yl[e] = w0[7 * DS_BM * DS_P + e];
+      Mvl[e] = w0[8 * DS_BM * DS_P + e];
+      Mzl[e] = w0[9 * DS_BM * DS_P + e];
+    }
+    __syncthreads();
+    for (int e = tid; e < nr * b; e += DS_THREADS) {
+      const int rr = e % nr, c = e / nr;
+      const int l = l0 + rr;
+      T vr = T(0), vn = T(0);
+      for (int x = 0; x < b; ++x) {
+        const T v = Vr[x * RL + rr], z = Zr[rr * b + x];
+        vr = fma(v, Yl[x + c * b], vr);
+        vn = fma(v, Mvl[x + c * b], vn);
+        vn = fma(z, Mzl[x + c * b], vn);
+      }
+      a.V[l + (int64_t)c * n2] = vn;
+      if (c < s) {
+        a.Vs[l + (int64_t)c * n2] = vr;
+        a.Z2[(int64_t)l * NP + k + c] = vr;
+        Vsr[rr * s + c] = vr;
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < k * s; e += DS_THREADS) {
+      const int x = e % k, c = e / k;
+      T v = T(0);
+      for (int rr = 0; rr < nr; ++rr) v = fma(Cs[rr * k + x], Vsr[rr * s + c], v);
+      CVp[e] = v;
+    }
+  }
+  cluster.sync();
+  // C V_s over the workers' partials, spread over every CTA
+  for (int e = rank + nc * tid; e < k * s; e += nc * DS_THREADS) a.CV[e] = cluster_sum_w(cluster, CVp, e, nc);
   // every CTA keeps its shared memory until the others have read it
   cluster.sync();
 }

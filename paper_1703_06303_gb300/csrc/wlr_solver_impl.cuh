@@ -1147,17 +1147,18 @@ class Solver final : public SolverBase {
     const bool front = k <= 32;
     ds_ne_ = std::max(b * b, front ? k * k : 0) <= DS_THREADS ? 1 : 2;
     const void* fn = ds_ne_ == 1 ? (const void*)dstep_cluster<T, 1> : (const void*)dstep_cluster<T, 2>;
-    for (int nc : {16, 8}) {
-      if (n2 < nc) continue;
-      const size_t bytes = sizeof(T) * DsLayout::make<T>(n2, k, b, s, cdiv(n2, nc), front).total;
-      if (bytes > 225 * 1024) continue;
-      if (nc > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+    // the steady-state step with the front stage has a kernel of its own (dstep_front)
+    const void* fnf = ds_ne_ == 1 ? (const void*)dstep_front<T, 1> : (const void*)dstep_front<T, 2>;
+    // a cluster of nc CTAs of `bytes` shared memory each can run fn
+    auto fits = [&](const void* f, int nc, size_t bytes) {
+      if (bytes > 225 * 1024) return false;
+      if (nc > 8 && cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
         cudaGetLastError();
-        continue;
+        return false;
       }
-      if (raise_smem_limit(fn, bytes) != cudaSuccess) {
+      if (raise_smem_limit(f, bytes) != cudaSuccess) {
         cudaGetLastError();
-        continue;
+        return false;
       }
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = dim3(nc);
@@ -1171,13 +1172,20 @@ class Solver final : public SolverBase {
       cfg.attrs = attr;
       cfg.numAttrs = 1;
       int ncl = 0;
-      if (cudaOccupancyMaxActiveClusters(&ncl, fn, &cfg) != cudaSuccess) {
+      if (cudaOccupancyMaxActiveClusters(&ncl, f, &cfg) != cudaSuccess) {
         cudaGetLastError();
-        continue;
+        return false;
       }
-      if (ncl < 1) continue;
+      return ncl >= 1;
+    };
+    for (int nc : {16, 8}) {
+      if (n2 < nc) continue;
+      const size_t bytes = sizeof(T) * DsLayout::make<T>(n2, k, b, s, cdiv(n2, nc), front).total;
+      const size_t bytes_f = front ? sizeof(T) * DfLayout::make<T>(k, b, s, df_rows(n2, nc)).total : 0;
+      if (!fits(fn, nc, bytes) || (front && !fits(fnf, nc, bytes_f))) continue;
       ds_nc_ = nc;
       ds_smem_ = bytes;
+      ds_smem_f_ = bytes_f;
       use_dstep_ = true;
       break;
     }
@@ -1294,7 +1302,15 @@ class Solver final : public SolverBase {
         kv_launch(stream_);
       }
       a.front = front && t == 0 ? 1 : 0;
-      {
+      if (a.front) {
+        Prof pf(this, "dstep");
+        cfg.dynamicSmemBytes = ds_smem_f_;
+        if (ds_ne_ == 1)
+          WLR_CUDA(cudaLaunchKernelEx(&cfg, dstep_front<T, 1>, a));
+        else
+          WLR_CUDA(cudaLaunchKernelEx(&cfg, dstep_front<T, 2>, a));
+        cfg.dynamicSmemBytes = ds_smem_;
+      } else {
         Prof pf(this, "dstep");
         if (ds_ne_ == 1)
           WLR_CUDA(cudaLaunchKernelEx(&cfg, dstep_cluster<T, 1>, a));
@@ -1563,7 +1579,7 @@ class Solver final : public SolverBase {
   bool fuse_front_ = false;  // ... with the second factor and B, C in front (k <= 32)
   const T* front_rpre_ = nullptr;
   int ds_nc_ = 0, ds_ne_ = 1;
-  size_t ds_smem_ = 0;
+  size_t ds_smem_ = 0, ds_smem_f_ = 0;
   float *Kh_ = nullptr, *Kl_ = nullptr;   // K as a float pair (float path)
   T *ZKh_ = nullptr, *ZKl_ = nullptr;     // K V (high, low)
   T *C_ = nullptr, *Z2_ = nullptr, *Z2prev_ = nullptr;
