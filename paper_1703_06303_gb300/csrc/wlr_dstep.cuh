@@ -108,36 +108,35 @@ struct DstepArgs {
   int* err;
   int n2, k, b, s, NP;
   int sweeps;    // Jacobi sweeps of the Rayleigh-Ritz step
-  // Steps a1 (second CholeskyQR factor) and a2 first, when `front` is set (k <= 32): the
-  // cluster sums the chunk partials of Q1^T [Q1 A2] itself, CTA 0 factors
-  // Q1^T Q1 = (I + Lambda)(I + Lambda)^T, and every CTA forms B and C for its columns.
+  // Steps a1 (second CholeskyQR factor) and a2 first, when `front` is set (k <= 32, the
+  // kernel dstep_front): CTA 0 forms the second factor of Q1^T Q1 = I + F, and the other
+  // CTAs form B and C for their columns.
   int front;
   const double* S2T;   // Q1^T [Q1 A2] summed over the Gram chunks: k x (k + n2) column-major
   const T* F2;         // S2 - I (k x k, column-major) = leading block of S2T minus I
-  const T* R1inv;      // inverse of the first factor (upper k x k)
-  T* Nout;             // N = (I + Lambda)^{-1} - I (lower k x k)
-  T* Rinv;             // R^{-1} = R1inv (I + N)^T (upper k x k); may be R1inv itself
+  const T* R1inv;      // inverse of the first factor (k x k; upper triangular after a
+                       // Cholesky first factor, full after chol2_series)
+  T* Nout;             // N = R2^{-T} - I (lower triangular, or full after chol2_series)
+  T* Rinv;             // R^{-1} = R1inv (I + N)^T
   T* Cout;             // C = R^{-1} B (k x n2)
   double* B64;         // B (k x n2), FP64 path
   float* Bho;          // B = Bho + Blo, float path
   float* Blo;
   double* bpart;       // ||B||^2 over each CTA's columns (nc entries)
+  int series;          // float front stage: the second factor may be (I + F)^{1/2} (chol2_series)
 };
 
 // Element offsets of the dynamic shared memory (every CTA has the same layout; the b x b
 // work arrays are used by CTA 0 only).
 struct DsLayout {
-  size_t Tq, Vt, Bs, Cs, Zh, Zl, Zr, Vsr, BVp, BV, HPp, Gp, CVp, Ml, Tt, NR, Wk, total;
-  // front: room for the front stage (second factor, B, C); without it Tq, Tt and NR are empty
+  size_t Vt, Bs, Cs, Zh, Zl, Zr, Vsr, BVp, BV, HPp, Gp, CVp, Ml, Wk, total;
   template <typename T>
-  __host__ __device__ static DsLayout make(int n2, int k, int b, int s, int R, bool front) {
-    return DsLayout(n2, k, b, s, R, (int)(sizeof(double) / sizeof(T)), front);
+  __host__ __device__ static DsLayout make(int n2, int k, int b, int s, int R) {
+    return DsLayout(n2, k, b, s, R);
   }
-  __host__ __device__ DsLayout(int n2, int k, int b, int s, int R, int dw, bool front) {
+  __host__ __device__ DsLayout(int n2, int k, int b, int s, int R) {
     const size_t ss = s > 0 ? s : 1;
-    const size_t kf = front ? k : 0;
     size_t o = 0;
-    Tq = o;  o += (size_t)dw * kf * R;      // (Q1^T A2)(:, rows) in double (front stage)
     Vt = o;  o += (size_t)b * n2;           // basis, V(j, c) at Vt[c*n2 + j]
     Bs = o;  o += 2 * (size_t)k * R;        // B(:, rows): high, low
     Cs = o;  o += (size_t)R * k;            // C(:, rows), C(x, j) at Cs[(j - l0)*k + x]
@@ -151,9 +150,7 @@ struct DsLayout {
     Gp = o;  o += (size_t)k * k;            // partial C C^T
     CVp = o; o += (size_t)k * ss;           // partial C V_s
     Ml = o;  o += 3 * (size_t)b * b;        // local copies of Y, Mv, Mz
-    Tt = o;  o += kf * R;                   // (Q1^T A2)(:, rows) rounded to T
-    NR = o;  o += 2 * kf * k;               // local copies of N and R^{-1}
-    Wk = o;  o += 10 * (size_t)DS_BM * DS_P;    // Rayleigh-Ritz / second-factor work arrays
+    Wk = o;  o += 10 * (size_t)DS_BM * DS_P;    // Rayleigh-Ritz work arrays
     total = o;
   }
 };
@@ -274,10 +271,13 @@ __device__ void ritz_step(T* wk, int b, int max_sweeps, T* __restrict__ theta,
     return R.c * (C.c * Hc[r][c] + C.s * Hc[r][C.partner]) +
            R.s * (C.c * Hc[R.partner][c] + C.s * Hc[R.partner][C.partner]);
   };
-  // pair i's angle is taken by thread 32 i (one per warp, spreading the shared-memory
-  // traffic of the angle computations over the schedulers)
-  const bool angler = (tid & 31) == 0 && (tid >> 5) < half;
-  const int ai = tid >> 5;
+  // pair i's angle is taken by lane 0 of warp DS_THREADS / 32 - 1 - i (one per warp,
+  // spreading the shared-memory traffic of the angle computations over the schedulers;
+  // counted from the last warp, which holds no elements while b^2 <= DS_THREADS - 32 i, so
+  // that a round's angles for the next round are computed alongside its element updates,
+  // from the same inputs, instead of after them)
+  const int ai = DS_THREADS / 32 - 1 - (tid >> 5);
+  const bool angler = (tid & 31) == 0 && ai < half;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     T off = T(0), tot = T(0);
     each([&](int, int r, int c) {
@@ -503,17 +503,101 @@ __device__ void chol2_block(T* wk, int k, Get get, const T* __restrict__ R1inv,
     Nout[i + c * k] = v;
   });
   __syncthreads();
+  // full sums: R1inv is upper triangular after a Cholesky first factor but a full matrix
+  // after chol2_series (the terms outside the triangles are exact zeros otherwise)
   each([&](int a, int b) {
-    T v = T(0);
-    if (a <= b) {
-      v = Rm[a * k + b];
-      for (int l = a; l <= b; ++l) v = fma(Rm[a * k + l], Nm[b * k + l], v);
-    }
+    T v = Rm[a * k + b];
+    for (int l = 0; l < k; ++l) v = fma(Rm[a * k + l], Nm[b * k + l], v);
     Ri[a * k + b] = v;
     Rinv[a + b * k] = v;
   });
   __syncthreads();
   if (tid == 0 && flag_s) atomicOr(err, ERRBIT_RANK_DEFICIENT);
+}
+
+// Second factor as an inverse square root (float path, small F).  With Q1^T Q1 = I + F,
+// any R2 with R2^T R2 = I + F completes X1 = Q1 R1 to X1 = (Q1 R2^{-1}) (R2 R1) with an
+// orthonormal first factor; the symmetric R2 = (I + F)^{1/2} serves as well as the
+// triangular Cholesky factor, because what the step uses (C = (X1^T X1)^{-1} X1^T A2,
+// B^T B and ||B||^2) does not depend on which orthonormal basis of range(X1) is taken.
+// Its inverse is the binomial series (I + F)^{-1/2} = I + sum_{j>=1} c_j F^j,
+// c_j = c_{j-1} (1 - 2j) / (2j), summed by Horner's rule with the fewest terms whose
+// remainder (about 0.3 ||F||_F^{m+1}) is below float precision: m products of k x k
+// matrices instead of k serial elimination steps.  Writes N = (I + F)^{-1/2} - I (full,
+// symmetric up to rounding) and R^{-1} = R1inv (I + N)^T in the places chol2_block uses.
+// Returns false, having written nothing outside wk, when ||F||_F > 0.06 (or is not finite).
+template <typename Get>
+__device__ bool chol2_series(float* wk, int k, Get get, const float* __restrict__ R1inv,
+                             float* __restrict__ Nout, float* __restrict__ Rinv) {
+  float* F = wk;                          // row-major k x k
+  float* Rm = wk + DS_BM * DS_BM;         // R1inv, row-major
+  float* Nm = wk + 2 * DS_BM * DS_BM;     // N, row-major
+  float* Ri = wk + 3 * DS_BM * DS_BM;     // R^{-1}, row-major
+  float* P = wk + 4 * DS_BM * DS_BM;      // Horner partial sums (two buffers)
+  float* Pn = wk + 5 * DS_BM * DS_BM;
+  constexpr int MMAX = 8;
+  __shared__ float red_s[DS_THREADS / 32];
+  __shared__ float cj[MMAX + 1];
+  __shared__ int m_s;
+  const int tid = threadIdx.x, kk = k * k;
+  float f2 = 0.f;
+  for (int e = tid; e < kk; e += DS_THREADS) {
+    const int i = e / k, j = e % k;
+    const float v = i >= j ? get(i + j * k) : get(j + i * k);   // the lower triangle of F
+    F[e] = v;
+    Rm[e] = R1inv[i + j * k];
+    f2 = fmaf(v, v, f2);
+  }
+  f2 = warp_sum(f2);
+  if ((tid & 31) == 0) red_s[tid >> 5] = f2;
+  __syncthreads();
+  if (tid == 0) {
+    float t = 0.f;
+    for (int w = 0; w < DS_THREADS / 32; ++w) t += red_s[w];
+    const float nf = sqrtf(t);
+    int m = 0;
+    if (nf <= 0.06f) {
+      float pw = nf;   // nf^m
+      m = 1;
+      while (m < MMAX && 0.3f * pw * nf > 3e-8f) {
+        pw *= nf;
+        ++m;
+      }
+    }
+    m_s = m;
+    cj[0] = 1.f;
+    for (int j = 1; j <= MMAX; ++j) cj[j] = cj[j - 1] * (float)(1 - 2 * j) / (float)(2 * j);
+  }
+  __syncthreads();
+  const int m = m_s;
+  if (m == 0) return false;
+  // P = c_m I, then P <- c_j I + F P for j = m - 1 .. 1, and N = F P
+  for (int e = tid; e < kk; e += DS_THREADS) P[e] = (e / k == e % k) ? cj[m] : 0.f;
+  __syncthreads();
+  for (int j = m - 1; j >= 0; --j) {
+    float* out = j == 0 ? Nm : Pn;
+    for (int e = tid; e < kk; e += DS_THREADS) {
+      const int r = e / k, c = e % k;
+      float v = (j > 0 && r == c) ? cj[j] : 0.f;
+      for (int l = 0; l < k; ++l) v = fmaf(F[r * k + l], P[l * k + c], v);
+      out[e] = v;
+      if (j == 0) Nout[r + c * k] = v;
+    }
+    __syncthreads();
+    float* t = P;
+    P = Pn;
+    Pn = t;
+  }
+  // R^{-1} = R1inv (I + N)^T
+  for (int e = tid; e < kk; e += DS_THREADS) {
+    const int r = e / k, c = e % k;
+    float v = Rm[e];
+    for (int l = 0; l < k; ++l) v = fmaf(Rm[r * k + l], Nm[c * k + l], v);
+    Ri[e] = v;
+    Rinv[r + c * k] = v;
+  }
+  __syncthreads();
+  return true;
 }
 
 // Sum over the cluster's CTAs, in rank order, of element e of a shared array (the remote
@@ -602,7 +686,7 @@ dstep_cluster(DstepArgs<T> a) {
   const int n2 = a.n2, k = a.k, b = a.b, s = a.s, NP = a.NP;
   const int R = (n2 + nc - 1) / nc;
   const int l0 = min(n2, rank * R), l1 = min(n2, l0 + R), nr = l1 - l0;
-  const DsLayout L = DsLayout::make<T>(n2, k, b, s, R, a.front);
+  const DsLayout L = DsLayout::make<T>(n2, k, b, s, R);
   T* Vt = sm + L.Vt;
   T* Bs = sm + L.Bs;
   T* Cs = sm + L.Cs;
@@ -620,16 +704,13 @@ dstep_cluster(DstepArgs<T> a) {
   const int kb = k * b;
 
   // ---- inputs into shared memory (asynchronous copies, one group): the whole basis,
-  // and for the CTA's rows: K V, and (unless the front stage makes them) B's columns and
-  // C (from Z2)
+  // and for the CTA's rows: K V, B's columns and C (from Z2)
   for (int e = tid; e < b * n2; e += DS_THREADS) cp_async_elem(Vt + e, a.V + e, true);
-  if (!a.front) {
-    for (int e = tid; e < k * nr; e += DS_THREADS) {
-      cp_async_elem(Bs + e, a.Bh + (int64_t)l0 * k + e, true);
-      if (a.Bl) cp_async_elem(Bs + k * R + e, a.Bl + (int64_t)l0 * k + e, true);
-      const int rr = e / k, x = e % k;
-      cp_async_elem(Cs + e, a.Z2 + (int64_t)(l0 + rr) * NP + x, true);
-    }
+  for (int e = tid; e < k * nr; e += DS_THREADS) {
+    cp_async_elem(Bs + e, a.Bh + (int64_t)l0 * k + e, true);
+    if (a.Bl) cp_async_elem(Bs + k * R + e, a.Bl + (int64_t)l0 * k + e, true);
+    const int rr = e / k, x = e % k;
+    cp_async_elem(Cs + e, a.Z2 + (int64_t)(l0 + rr) * NP + x, true);
   }
   for (int e = tid; e < b * nr; e += DS_THREADS) {
     const int c = e / nr, rr = e % nr;
@@ -638,65 +719,6 @@ dstep_cluster(DstepArgs<T> a) {
   }
   cp_async_commit();
 
-  if (a.front) {
-    double* Tq = reinterpret_cast<double*>(sm + L.Tq);
-    T* Tt = sm + L.Tt;
-    T* Nl = sm + L.NR;
-    T* Rl = Nl + k * k;
-    // ---- a1/a2 (1): t = Q1^T A2 for this CTA's columns (column k + j of the sums)
-    for (int v = tid; v < k * nr; v += DS_THREADS) {
-      const double sum = __ldcg(&a.S2T[(int64_t)(k + l0) * k + v]);
-      Tq[v] = sum;
-      Tt[v] = (T)sum;
-    }
-    // ---- (2) the second factor on CTA 0 (from the reduced S2 - I in global memory)
-    if (rank == 0) chol2_block<T, NE>(Wk, k, [&](int e) { return a.F2[e]; }, a.R1inv, a.Nout, a.Rinv, a.err);
-    cluster.sync();
-    // ---- (3) B = (I + N) t and C = R^{-1} B for this CTA's columns
-    {
-      const T* w0 = cluster.map_shared_rank(Wk, 0);
-      for (int e = tid; e < k * k; e += DS_THREADS) {
-        Nl[e] = w0[2 * DS_BM * DS_BM + e];
-        Rl[e] = w0[3 * DS_BM * DS_BM + e];
-      }
-    }
-    __syncthreads();
-    double bn = 0.0;
-    for (int v = tid; v < k * nr; v += DS_THREADS) {
-      const int x = v % k, jj = v / k;
-      T corr = T(0);
-      for (int l = 0; l <= x; ++l) corr = fma(Nl[x * k + l], Tt[jj * k + l], corr);
-      const double bv = Tq[v] + (double)corr;
-      const int64_t o = (int64_t)(l0 + jj) * k + x;
-      if (a.B64) a.B64[o] = bv;
-      if constexpr (sizeof(T) == 4) {
-        const float hi = (float)bv, lo = (float)(bv - (double)hi);
-        a.Bho[o] = hi;
-        a.Blo[o] = lo;
-        Bs[v] = hi;
-        Bs[k * R + v] = lo;
-      } else {
-        Bs[v] = (T)bv;
-      }
-      bn += bv * bv;
-    }
-    __syncthreads();
-    for (int v = tid; v < k * nr; v += DS_THREADS) {
-      const int x = v % k, jj = v / k;
-      T cv = T(0);
-      for (int l = x; l < k; ++l) {
-        const T bl = sizeof(T) == 4 ? Bs[jj * k + l] + Bs[k * R + jj * k + l] : Bs[jj * k + l];
-        cv = fma(Rl[x * k + l], bl, cv);
-      }
-      Cs[v] = cv;
-      const int64_t o = (int64_t)(l0 + jj) * k + x;
-      a.Cout[o] = cv;
-      a.Z2[(int64_t)(l0 + jj) * NP + x] = cv;
-    }
-    __shared__ double bsh[32];
-    bn = block_sum_double(bn, bsh);
-    if (tid == 0) a.bpart[rank] = bn;
-  }
   cp_async_wait<0>();
   __syncthreads();
 
@@ -826,12 +848,13 @@ dstep_cluster(DstepArgs<T> a) {
 // CholeskyQR factor does not hold up the products over the basis rows.  With
 // t = Q1^T A2 (the Gram's sums), B = (I + N) t and C = R^{-1} B:
 //   B V = (I + N) (t V)   and   B^T (B V) = t^T X,  X = (I + N)^T (B V),
-// so the partials of t V need only t.  CTA 0 owns no basis rows: it factors
-// Q1^T Q1 = (I + Lambda)(I + Lambda)^T (chol2_block) while CTAs 1 .. nc-1 form t V over
-// their rows; after one cluster barrier they form (I + N) and X from the summed t V and
-// their rows of Z = K V - t^T X, H and P.  CTA 0 then runs the Rayleigh-Ritz step while
-// the others form their columns of B, C (and ||B||^2, C C^T) in its shadow.  Same
-// quantities as dstep_cluster's front stage; only the order of the float sums differs.
+// so the partials of t V need only t.  CTA 0 owns no basis rows: it forms the second
+// factor of Q1^T Q1 = I + F (chol2_series while ||F|| is small, else the elimination
+// chol2_block) while CTAs 1 .. nc-1 form t V over their rows; after one cluster barrier
+// they form (I + N) t V and X from the summed t V and their rows of Z = K V - t^T X, H
+// and P.  CTA 0 then runs the Rayleigh-Ritz step while the others form their columns of
+// B, C (and ||B||^2, C C^T) in its shadow.  N and R^{-1} are full matrices after the
+// series, triangular after the elimination; the loops below run over full rows.
 struct DfLayout {
   size_t Tq, Th, Tl, Vr, Zh, Zl, Zr, Bs, Cs, Vsr, TVp, TV, BVx, Xs, HPp, Gp, CVp, Ml, NR, Wk, total;
   template <typename T>
@@ -917,8 +940,12 @@ dstep_front(DstepArgs<T> a) {
   }
   cp_async_commit();
   if (rank == 0) {
-    // ---- (1) the second factor: N and R^{-1} into Wk (and global memory)
-    chol2_block<T, NE>(Wk, k, [&](int e) { return a.F2[e]; }, a.R1inv, a.Nout, a.Rinv, a.err);
+    // ---- (1) the second factor: N and R^{-1} into Wk (and global memory), by the
+    // inverse square root series when F is small enough, else by elimination
+    auto getF = [&](int e) { return a.F2[e]; };
+    bool done = false;
+    if constexpr (kF) done = a.series && chol2_series(Wk, k, getF, a.R1inv, a.Nout, a.Rinv);
+    if (!done) chol2_block<T, NE>(Wk, k, getF, a.R1inv, a.Nout, a.Rinv, a.err);
     if (tid == 0) a.bpart[0] = 0.0;
     cp_async_wait<0>();
   } else {
@@ -972,7 +999,7 @@ dstep_front(DstepArgs<T> a) {
     for (int e = tid; e < kb; e += DS_THREADS) {
       const int x = e % k, c = e / k;
       T corr = T(0);
-      for (int l = 0; l <= x; ++l) corr = fma(Nl[x * k + l], TV[l + c * k], corr);
+      for (int l = 0; l < k; ++l) corr = fma(Nl[x * k + l], TV[l + c * k], corr);
       DfAcc<T> acc;
       acc.hi = TV[e];
       acc.lo = TV[kb + e];
@@ -984,7 +1011,7 @@ dstep_front(DstepArgs<T> a) {
     for (int e = tid; e < kb; e += DS_THREADS) {
       const int x = e % k, c = e / k;
       T corr = T(0);
-      for (int l = x; l < k; ++l) corr = fma(Nl[l * k + x], BVx[l + c * k], corr);
+      for (int l = 0; l < k; ++l) corr = fma(Nl[l * k + x], BVx[l + c * k], corr);
       DfAcc<T> acc;
       acc.hi = BVx[e];
       acc.lo = BVx[kb + e];
@@ -1033,7 +1060,7 @@ dstep_front(DstepArgs<T> a) {
     for (int v = tid; v < k * nr; v += DS_THREADS) {
       const int x = v % k, jj = v / k;
       T corr = T(0);
-      for (int l = 0; l <= x; ++l) corr = fma(Nl[x * k + l], Th[jj * k + l], corr);
+      for (int l = 0; l < k; ++l) corr = fma(Nl[x * k + l], Th[jj * k + l], corr);
       const double bv = Tq[v] + (double)corr;
       const int64_t o = (int64_t)(l0 + jj) * k + x;
       if (a.B64) a.B64[o] = bv;
@@ -1052,7 +1079,7 @@ dstep_front(DstepArgs<T> a) {
     for (int v = tid; v < k * nr; v += DS_THREADS) {
       const int x = v % k, jj = v / k;
       T cv = T(0);
-      for (int l = x; l < k; ++l) {
+      for (int l = 0; l < k; ++l) {
         const T bl = kF ? Bs[jj * k + l] + Bs[k * RL + jj * k + l] : Bs[jj * k + l];
         cv = fma(Rl[x * k + l], bl, cv);
       }

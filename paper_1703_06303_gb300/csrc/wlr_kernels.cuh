@@ -1483,8 +1483,10 @@ __device__ __forceinline__ void rp_phase1(const T* __restrict__ A2, int64_t lda,
 }
 
 // Row i of Q1 = X1new R^{-1} (QSplitOut) from the row's solution, held by a group of LG
-// lanes (lane g: x[sl] = X1new(i, g + LG sl)): q_a = sum_{b <= a} x_b R^{-1}(b, a), summed
-// in the order b = 0, 1, ..., then split into TF32 h + l.
+// lanes (lane g: x[sl] = X1new(i, g + LG sl)): q_a = sum_b x_b R^{-1}(b, a), summed in the
+// order b = 0, 1, ..., then split into TF32 h + l.  R^{-1} may be a full matrix (after the
+// series form of the second factor); when it is upper triangular the terms below the
+// diagonal are exact zeros.
 template <typename T, int KP, int LG, int NS>
 __device__ __forceinline__ void q_split_row(const T (&x)[NS], const T* __restrict__ Rqs, int k, int g,
                                             bool active, int i, const QSplitOut& qo) {
@@ -1499,7 +1501,7 @@ __device__ __forceinline__ void q_split_row(const T (&x)[NS], const T* __restric
 #pragma unroll
       for (int sl = 0; sl < NS; ++sl) {
         const int a = g + LG * sl;
-        if (a < k && bq <= a) qa[sl] = fma(xb, Rqs[bq + a * k], qa[sl]);
+        if (a < k) qa[sl] = fma(xb, Rqs[bq + a * k], qa[sl]);
       }
     }
   }

@@ -884,7 +884,7 @@ class Solver final : public SolverBase {
       q_from_row_pass_ = false;
       Prof pf(this, "form_q_split");
       tc::form_q_split<<<grid1d((int64_t)m * k), 256, sizeof(float) * k * k, stream_>>>(
-          (const float*)X1, m, (const float*)Rpre, m, k, Q1h_, Q1l_, ld4_);
+          (const float*)X1, m, (const float*)Rpre, m, k, Q1h_, Q1l_, ld4_, fuse_front_ ? 1 : 0);
       count(1);
     }
     if (fork) fork_kv();
@@ -1180,7 +1180,7 @@ class Solver final : public SolverBase {
     };
     for (int nc : {16, 8}) {
       if (n2 < nc) continue;
-      const size_t bytes = sizeof(T) * DsLayout::make<T>(n2, k, b, s, cdiv(n2, nc), front).total;
+      const size_t bytes = sizeof(T) * DsLayout::make<T>(n2, k, b, s, cdiv(n2, nc)).total;
       const size_t bytes_f = front ? sizeof(T) * DfLayout::make<T>(k, b, s, df_rows(n2, nc)).total : 0;
       if (!fits(fn, nc, bytes) || (front && !fits(fnf, nc, bytes_f))) continue;
       ds_nc_ = nc;
@@ -1271,6 +1271,9 @@ class Solver final : public SolverBase {
     a.Rinv = Rinv_;
     a.Cout = C_;
     a.bpart = bpart_;
+    // the series form of the second factor leaves a full R^{-1}, which the tensor-core
+    // path's Q1 formation (form_q_split, the row pass) takes as such
+    a.series = use_tc_ ? 1 : 0;
     if constexpr (std::is_same<T, float>::value) {
       a.B64 = nullptr;
       a.Bho = Bh_;

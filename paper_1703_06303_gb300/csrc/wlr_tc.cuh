@@ -135,7 +135,8 @@ static __global__ void split_tf32(const float* __restrict__ src, int64_t lds, in
 
 // Q1 = X1 R^{-1} written as the TF32 split (hi, lo), leading dimension ldq.
 static __global__ void form_q_split(const float* __restrict__ X1, int64_t ldx, const float* __restrict__ Rinv,
-                             int m, int k, float* __restrict__ qh, float* __restrict__ ql, int64_t ldq) {
+                             int m, int k, float* __restrict__ qh, float* __restrict__ ql, int64_t ldq,
+                             int full) {
   extern __shared__ unsigned char smem_q[];
   float* Ri = reinterpret_cast<float*>(smem_q);
   for (int e = threadIdx.x; e < k * k; e += blockDim.x) Ri[e] = Rinv[e];
@@ -146,7 +147,8 @@ static __global__ void form_q_split(const float* __restrict__ X1, int64_t ldx, c
     const int a = (int)(e / m);
     const int64_t i = e - (int64_t)a * m;
     float v = 0.f;
-    for (int b = 0; b <= a; ++b) v = fmaf(X1[i + b * ldx], Ri[b + a * k], v);
+    const int bend = full ? k : a + 1;   // Rinv upper triangular unless full
+    for (int b = 0; b < bend; ++b) v = fmaf(X1[i + b * ldx], Ri[b + a * k], v);
     const float h = round_tf32(v);
     qh[i + (int64_t)a * ldq] = h;
     ql[i + (int64_t)a * ldq] = round_tf32(v - h);
