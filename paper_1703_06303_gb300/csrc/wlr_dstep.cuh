@@ -614,19 +614,6 @@ __device__ __forceinline__ T cluster_sum(cgrp::cluster_group& cl, T* base, int e
   return (T)acc.value();
 }
 
-// The same sum over ranks 1 .. nc - 1 only (the front-stage kernel, whose CTA 0 owns no rows).
-template <typename T>
-__device__ __forceinline__ T cluster_sum_w(cgrp::cluster_group& cl, T* base, int e, int nc) {
-  T v[15];
-#pragma unroll
-  for (int u = 0; u < 15; ++u) v[u] = u + 1 < nc ? cl.map_shared_rank(base, u + 1)[e] : T(0);
-  WideAcc<T> acc;
-#pragma unroll
-  for (int u = 0; u < 15; ++u)
-    if (u + 1 < nc) acc.add(v[u]);
-  return (T)acc.value();
-}
-
 // (K V)(l, c) for all rows in double-float: one warp per (row l, group of KV_CG columns),
 // the lanes splitting the sum over j (K is symmetric, so row l of K is the contiguous
 // column l).  Each lane loads the K and V entries of KV_JM values of j before using them
@@ -855,13 +842,25 @@ dstep_cluster(DstepArgs<T> a) {
 // and P.  CTA 0 then runs the Rayleigh-Ritz step while the others form their columns of
 // B, C (and ||B||^2, C C^T) in its shadow.  N and R^{-1} are full matrices after the
 // series, triangular after the elimination; the loops below run over full rows.
+// Partial sums travel by remote stores from their producers into slot rank - 1 of the
+// consumer's exchange region (PUSH, where one slot per worker fits), which the consumer
+// adds in rank order after the next cluster barrier: the stores are posted, and each
+// consumer then reads its own shared memory.  What CTA 0 hands to every worker (N,
+// R^{-1}, then Y, Mv, Mz) the workers load from it: fifteen SMs loading in parallel
+// beat one SM storing fifteen copies.  Without PUSH every partial is loaded remotely.
 struct DfLayout {
-  size_t Tq, Th, Tl, Vr, Zh, Zl, Zr, Bs, Cs, Vsr, TVp, TV, BVx, Xs, HPp, Gp, CVp, Ml, NR, Wk, total;
+  size_t Tq, Th, Tl, Vr, Zh, Zl, Zr, Bs, Cs, Vsr, TV, BVx, Xs, Ml, NR, Wk, Xch, total;
+  // Exchange region Xch.  push: on a worker, the t V partials of every worker (slot
+  // u = rank - 1, 2 k b values); on CTA 0, the workers' partials of H and P (2 b^2 each), of
+  // C C^T (k^2) and of C V_s (k s), all written by their owners with remote stores.
+  // Otherwise (pull, when those slots do not fit): each CTA's own partials at the same
+  // offsets with one slot, read by their consumers with remote loads.
+  size_t xtv, xhp, xg, xcv;   // offsets inside Xch
   template <typename T>
-  __host__ __device__ static DfLayout make(int k, int b, int s, int RL) {
-    return DfLayout(k, b, s, RL, (int)(sizeof(double) / sizeof(T)));
+  __host__ __device__ static DfLayout make(int k, int b, int s, int RL, int nw, bool push) {
+    return DfLayout(k, b, s, RL, nw, (int)(sizeof(double) / sizeof(T)), push);
   }
-  __host__ __device__ DfLayout(int k, int b, int s, int RL, int dw) {
+  __host__ __device__ DfLayout(int k, int b, int s, int RL, int nw, int dw, bool push) {
     const size_t ss = s > 0 ? s : 1;
     size_t o = 0;
     Tq = o;  o += (size_t)dw * k * RL;     // t(:, rows) in double, t(x, j) at Tq[(j - l0) k + x]
@@ -874,22 +873,41 @@ struct DfLayout {
     Bs = o;  o += 2 * (size_t)k * RL;      // B(:, rows): high, low
     Cs = o;  o += (size_t)RL * k;          // C(:, rows)
     Vsr = o; o += (size_t)RL * ss;         // V_s(rows)
-    TVp = o; o += 2 * (size_t)k * b;       // partial t V (high, low)
     TV = o;  o += 2 * (size_t)k * b;       // t V
     BVx = o; o += 2 * (size_t)k * b;       // B V = (I + N) t V
     Xs = o;  o += 2 * (size_t)k * b;       // X = (I + N)^T B V
-    HPp = o; o += 2 * (size_t)b * b;       // partial H, P
-    Gp = o;  o += (size_t)k * k;           // partial C C^T
-    CVp = o; o += (size_t)k * ss;          // partial C V_s
-    Ml = o;  o += 3 * (size_t)b * b;       // local copies of Y, Mv, Mz
-    NR = o;  o += 2 * (size_t)k * k;       // local copies of N and R^{-1}
+    Ml = o;  o += 3 * (size_t)b * b;       // local copies of Y, Mv, Mz (from CTA 0)
+    NR = o;  o += 2 * (size_t)k * k;       // local copies of N and R^{-1} (from CTA 0)
     Wk = o;  o += 10 * (size_t)DS_BM * DS_P;   // second factor, then Rayleigh-Ritz (CTA 0)
+    const size_t slots = push ? (size_t)nw : 1;
+    xhp = 0;
+    xg = xhp + slots * 2 * b * b;
+    xcv = xg + slots * k * k;
+    const size_t x0 = xcv + slots * k * ss;
+    xtv = push ? 0 : x0;                   // push: the t V slots share the space with the above
+    const size_t x1 = xtv + slots * 2 * k * b;
+    Xch = o; o += x0 > x1 ? x0 : x1;
     total = o;
   }
 };
 __host__ __device__ inline int df_rows(int n2, int nc) { return (n2 + nc - 2) / (nc - 1); }
 
-template <typename T, int NE>
+// Sum over ranks 1 .. nc - 1, in rank order, of element e of a shared array (the remote
+// loads issued together; float sums compensated): the exchange of dstep_front without
+// room for one slot per worker.
+template <typename T>
+__device__ __forceinline__ T pull_sum(cgrp::cluster_group& cl, T* base, int e, int nc) {
+  T v[15];
+#pragma unroll
+  for (int u = 0; u < 15; ++u) v[u] = u + 1 < nc ? cl.map_shared_rank(base, u + 1)[e] : T(0);
+  WideAcc<T> acc;
+#pragma unroll
+  for (int u = 0; u < 15; ++u)
+    if (u + 1 < nc) acc.add(v[u]);
+  return (T)acc.value();
+}
+
+template <typename T, int NE, bool PUSH>
 __global__ void __launch_bounds__(DS_THREADS, 1)
 dstep_front(DstepArgs<T> a) {
   extern __shared__ unsigned char smem_raw[];
@@ -897,13 +915,14 @@ dstep_front(DstepArgs<T> a) {
   cgrp::cluster_group cluster = cgrp::this_cluster();
   const int rank = (int)cluster.block_rank();
   const int nc = (int)cluster.num_blocks();
+  const int nw = nc - 1;
   const int tid = threadIdx.x;
   const int n2 = a.n2, k = a.k, b = a.b, s = a.s, NP = a.NP;
   const int RL = df_rows(n2, nc);
   const int l0 = rank == 0 ? 0 : min(n2, (rank - 1) * RL);
   const int l1 = rank == 0 ? 0 : min(n2, l0 + RL);
   const int nr = l1 - l0;
-  const DfLayout L = DfLayout::make<T>(k, b, s, RL);
+  const DfLayout L = DfLayout::make<T>(k, b, s, RL, nw, PUSH);
   double* Tq = reinterpret_cast<double*>(sm + L.Tq);
   T* Th = sm + L.Th;
   T* Tl = sm + L.Tl;
@@ -914,18 +933,15 @@ dstep_front(DstepArgs<T> a) {
   T* Bs = sm + L.Bs;
   T* Cs = sm + L.Cs;
   T* Vsr = sm + L.Vsr;
-  T* TVp = sm + L.TVp;
   T* TV = sm + L.TV;
   T* BVx = sm + L.BVx;
   T* Xs = sm + L.Xs;
-  T* HPp = sm + L.HPp;
-  T* Gp = sm + L.Gp;
-  T* CVp = sm + L.CVp;
   T* Ml = sm + L.Ml;
   T* Nl = sm + L.NR;
   T* Rl = Nl + k * k;
   T* Wk = sm + L.Wk;
-  const int kb = k * b;
+  T* Xch = sm + L.Xch;
+  const int kb = k * b, bb = b * b, ss = s > 0 ? s : 1;
   constexpr bool kF = sizeof(T) == 4;
   __shared__ double bsh[32];
 
@@ -940,8 +956,8 @@ dstep_front(DstepArgs<T> a) {
   }
   cp_async_commit();
   if (rank == 0) {
-    // ---- (1) the second factor: N and R^{-1} into Wk (and global memory), by the
-    // inverse square root series when F is small enough, else by elimination
+    // ---- (1) the second factor (into Wk and global memory) by the inverse square root
+    // series when F is small enough, else by elimination
     auto getF = [&](int e) { return a.F2[e]; };
     bool done = false;
     if constexpr (kF) done = a.series && chol2_series(Wk, k, getF, a.R1inv, a.Nout, a.Rinv);
@@ -958,13 +974,23 @@ dstep_front(DstepArgs<T> a) {
       Tl[v] = kF ? (T)(t - (double)h) : T(0);
     }
     __syncthreads();
-    // ---- (2) partial t V over the CTA's rows (double-float)
+    // ---- (2) partial t V over the CTA's rows (double-float): with PUSH into slot
+    // rank - 1 of every worker's exchange region, else into the CTA's own
     for (int e = tid; e < kb; e += DS_THREADS) {
       const int x = e % k, c = e / k;
       DfAcc<T> acc;
       for (int rr = 0; rr < nr; ++rr) acc.add(Th[rr * k + x], Tl[rr * k + x], Vr[c * RL + rr]);
-      TVp[e] = acc.hi;
-      TVp[kb + e] = acc.lo;
+      if constexpr (PUSH) {
+        const size_t o = L.xtv + (size_t)(rank - 1) * 2 * kb + e;
+        for (int w = 1; w < nc; ++w) {
+          T* dst = cluster.map_shared_rank(Xch, w);
+          dst[o] = acc.hi;
+          dst[o + kb] = acc.lo;
+        }
+      } else {
+        Xch[L.xtv + e] = acc.hi;
+        Xch[L.xtv + kb + e] = acc.lo;
+      }
     }
   }
   cluster.sync();
@@ -979,19 +1005,24 @@ dstep_front(DstepArgs<T> a) {
       }
     }
     for (int e = tid; e < kb; e += DS_THREADS) {
-      T ph[15], pl[15];
-#pragma unroll
-      for (int u = 0; u < 15; ++u) {
-        if (u + 1 < nc) {
-          const T* rp = cluster.map_shared_rank(TVp, u + 1);
-          ph[u] = rp[e];
-          pl[u] = rp[kb + e];
-        }
-      }
       DfAcc<T> acc;
+      if constexpr (PUSH) {
+        const T* tv = Xch + L.xtv;
+        for (int u = 0; u < nw; ++u) acc.add_pair(tv[(size_t)u * 2 * kb + e], tv[(size_t)u * 2 * kb + kb + e]);
+      } else {
+        T ph[15], pl[15];
 #pragma unroll
-      for (int u = 0; u < 15; ++u)
-        if (u + 1 < nc) acc.add_pair(ph[u], pl[u]);
+        for (int u = 0; u < 15; ++u) {
+          if (u + 1 < nc) {
+            const T* rp = cluster.map_shared_rank(Xch, u + 1) + L.xtv;
+            ph[u] = rp[e];
+            pl[u] = rp[kb + e];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 15; ++u)
+          if (u + 1 < nc) acc.add_pair(ph[u], pl[u]);
+      }
       TV[e] = acc.hi;
       TV[kb + e] = acc.lo;
     }
@@ -1031,25 +1062,38 @@ dstep_front(DstepArgs<T> a) {
     }
     __syncthreads();
     // ---- partial H = V^T Z and P = Z^T Z over the CTA's rows
-    for (int e = tid; e < b * b; e += DS_THREADS) {
-      const int c1 = e % b, c2 = e / b;
-      T h = T(0), p = T(0);
-      for (int rr = 0; rr < nr; ++rr) {
-        const T z2 = Zr[rr * b + c2];
-        h = fma(Vr[c1 * RL + rr], z2, h);
-        p = fma(Zr[rr * b + c1], z2, p);
+    {
+      T* dst = (PUSH ? cluster.map_shared_rank(Xch, 0) + (size_t)(rank - 1) * 2 * bb : Xch) + L.xhp;
+      for (int e = tid; e < bb; e += DS_THREADS) {
+        const int c1 = e % b, c2 = e / b;
+        T h = T(0), p = T(0);
+        for (int rr = 0; rr < nr; ++rr) {
+          const T z2 = Zr[rr * b + c2];
+          h = fma(Vr[c1 * RL + rr], z2, h);
+          p = fma(Zr[rr * b + c1], z2, p);
+        }
+        dst[e] = h;
+        dst[bb + e] = p;
       }
-      HPp[e] = h;
-      HPp[b * b + e] = p;
     }
   }
   cluster.sync();
   if (rank == 0) {
-    // ---- (4) Rayleigh-Ritz on CTA 0 (H into work array 0, P into work array 4)
-    for (int e = tid; e < 2 * b * b; e += DS_THREADS) {
-      const T v = cluster_sum_w(cluster, HPp, e, nc);
-      const int f = e % (b * b), r_ = f % b, c_ = f / b;
-      Wk[(e < b * b ? 0 : 4 * DS_BM * DS_P) + r_ * DS_P + c_] = v;
+    // ---- (4) Rayleigh-Ritz on CTA 0 (H into work array 0, P into work array 4, summed over
+    // the workers in rank order)
+    for (int e = tid; e < 2 * bb; e += DS_THREADS) {
+      const int part = e / bb, f = e % bb;
+      T v;
+      if constexpr (PUSH) {
+        const T* hp = Xch + L.xhp;
+        WideAcc<T> acc;
+        for (int u = 0; u < nw; ++u) acc.add(hp[(size_t)u * 2 * bb + e]);
+        v = (T)acc.value();
+      } else {
+        v = pull_sum(cluster, Xch + L.xhp, e, nc);
+      }
+      const int r_ = f % b, c_ = f / b;
+      Wk[(part == 0 ? 0 : 4 * DS_BM * DS_P) + r_ * DS_P + c_] = v;
     }
     __syncthreads();
     ritz_step<T, NE>(Wk, b, a.sweeps, a.theta, a.resid, a.err);
@@ -1091,29 +1135,39 @@ dstep_front(DstepArgs<T> a) {
     bn = block_sum_double(bn, bsh);
     if (tid == 0) a.bpart[rank] = bn;
     __syncthreads();
-    for (int e = tid; e < k * k; e += DS_THREADS) {
-      const int x = e % k, y = e / k;
-      T v = T(0);
-      for (int rr = 0; rr < nr; ++rr) v = fma(Cs[rr * k + x], Cs[rr * k + y], v);
-      Gp[e] = v;
+    {
+      T* dst = (PUSH ? cluster.map_shared_rank(Xch, 0) + (size_t)(rank - 1) * k * k : Xch) + L.xg;
+      for (int e = tid; e < k * k; e += DS_THREADS) {
+        const int x = e % k, y = e / k;
+        T v = T(0);
+        for (int rr = 0; rr < nr; ++rr) v = fma(Cs[rr * k + x], Cs[rr * k + y], v);
+        dst[e] = v;
+      }
     }
   }
   cluster.sync();
   if (rank == 0) {
     // ---- (5) G = C C^T over the workers' partials
-    for (int e = tid; e < k * k; e += DS_THREADS) a.G[e] = cluster_sum_w(cluster, Gp, e, nc);
-  } else {
-    // ---- next basis rows and Ritz vectors (Y, Mv, Mz from CTA 0), then partial C V_s
-    const T* w0 = cluster.map_shared_rank(Wk, 0);
-    T* Yl = Ml;
-    T* Mvl = Ml + b * b;
-    T* Mzl = Ml + 2 * b * b;
-    for (int e = tid; e < b * b; e += DS_THREADS) {
-      Yl[e] = w0[7 * DS_BM * DS_P + e];
-      Mvl[e] = w0[8 * DS_BM * DS_P + e];
-      Mzl[e] = w0[9 * DS_BM * DS_P + e];
+    for (int e = tid; e < k * k; e += DS_THREADS) {
+      if constexpr (PUSH) {
+        const T* gp = Xch + L.xg;
+        WideAcc<T> acc;
+        for (int u = 0; u < nw; ++u) acc.add(gp[(size_t)u * k * k + e]);
+        a.G[e] = (T)acc.value();
+      } else {
+        a.G[e] = pull_sum(cluster, Xch + L.xg, e, nc);
+      }
     }
-    __syncthreads();
+  } else {
+    // ---- next basis rows and Ritz vectors (Y, Mv, Mz from CTA 0), then the partial C V_s
+    {
+      const T* w0 = cluster.map_shared_rank(Wk, 0);
+      for (int e = tid; e < 3 * bb; e += DS_THREADS) Ml[e] = w0[(7 + e / bb) * DS_BM * DS_P + e % bb];
+      __syncthreads();
+    }
+    const T* Yl = Ml;
+    const T* Mvl = Ml + bb;
+    const T* Mzl = Ml + 2 * bb;
     for (int e = tid; e < nr * b; e += DS_THREADS) {
       const int rr = e % nr, c = e / nr;
       const int l = l0 + rr;
@@ -1132,18 +1186,31 @@ dstep_front(DstepArgs<T> a) {
       }
     }
     __syncthreads();
+    T* dst = (PUSH ? cluster.map_shared_rank(Xch, 0) + (size_t)(rank - 1) * k * ss : Xch) + L.xcv;
     for (int e = tid; e < k * s; e += DS_THREADS) {
       const int x = e % k, c = e / k;
       T v = T(0);
       for (int rr = 0; rr < nr; ++rr) v = fma(Cs[rr * k + x], Vsr[rr * s + c], v);
-      CVp[e] = v;
+      dst[e] = v;
     }
   }
   cluster.sync();
-  // C V_s over the workers' partials, spread over every CTA
-  for (int e = rank + nc * tid; e < k * s; e += nc * DS_THREADS) a.CV[e] = cluster_sum_w(cluster, CVp, e, nc);
-  // every CTA keeps its shared memory until the others have read it
-  cluster.sync();
+  if constexpr (PUSH) {
+    // after the last exchange no CTA reads another's shared memory
+    if (rank == 0) {
+      const T* cvp = Xch + L.xcv;
+      for (int e = tid; e < k * s; e += DS_THREADS) {
+        WideAcc<T> acc;
+        for (int u = 0; u < nw; ++u) acc.add(cvp[(size_t)u * k * ss + e]);
+        a.CV[e] = (T)acc.value();
+      }
+    }
+  } else {
+    // C V_s over the workers' partials, spread over every CTA; each CTA keeps its shared
+    // memory until the others have read it
+    for (int e = rank + nc * tid; e < k * s; e += nc * DS_THREADS) a.CV[e] = pull_sum(cluster, Xch + L.xcv, e, nc);
+    cluster.sync();
+  }
 }
 
 // K = Kh + Kl as a float pair (once per problem).

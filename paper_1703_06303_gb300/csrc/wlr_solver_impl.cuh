@@ -1147,8 +1147,13 @@ class Solver final : public SolverBase {
     const bool front = k <= 32;
     ds_ne_ = std::max(b * b, front ? k * k : 0) <= DS_THREADS ? 1 : 2;
     const void* fn = ds_ne_ == 1 ? (const void*)dstep_cluster<T, 1> : (const void*)dstep_cluster<T, 2>;
-    // the steady-state step with the front stage has a kernel of its own (dstep_front)
-    const void* fnf = ds_ne_ == 1 ? (const void*)dstep_front<T, 1> : (const void*)dstep_front<T, 2>;
+    // the steady-state step with the front stage has a kernel of its own (dstep_front),
+    // exchanging partial sums by remote stores where one slot per worker fits (push),
+    // else by remote loads
+    auto front_fn = [&](bool push) {
+      if (push) return ds_ne_ == 1 ? (const void*)dstep_front<T, 1, true> : (const void*)dstep_front<T, 2, true>;
+      return ds_ne_ == 1 ? (const void*)dstep_front<T, 1, false> : (const void*)dstep_front<T, 2, false>;
+    };
     // a cluster of nc CTAs of `bytes` shared memory each can run fn
     auto fits = [&](const void* f, int nc, size_t bytes) {
       if (bytes > 225 * 1024) return false;
@@ -1181,11 +1186,24 @@ class Solver final : public SolverBase {
     for (int nc : {16, 8}) {
       if (n2 < nc) continue;
       const size_t bytes = sizeof(T) * DsLayout::make<T>(n2, k, b, s, cdiv(n2, nc)).total;
-      const size_t bytes_f = front ? sizeof(T) * DfLayout::make<T>(k, b, s, df_rows(n2, nc)).total : 0;
-      if (!fits(fn, nc, bytes) || (front && !fits(fnf, nc, bytes_f))) continue;
+      if (!fits(fn, nc, bytes)) continue;
+      size_t bytes_f = 0;
+      bool push = false;
+      if (front) {
+        for (bool p : {true, false}) {
+          const size_t bf = sizeof(T) * DfLayout::make<T>(k, b, s, df_rows(n2, nc), nc - 1, p).total;
+          if (fits(front_fn(p), nc, bf)) {
+            bytes_f = bf;
+            push = p;
+            break;
+          }
+        }
+        if (bytes_f == 0) continue;
+      }
       ds_nc_ = nc;
       ds_smem_ = bytes;
       ds_smem_f_ = bytes_f;
+      ds_push_ = push;
       use_dstep_ = true;
       break;
     }
@@ -1308,10 +1326,17 @@ class Solver final : public SolverBase {
       if (a.front) {
         Prof pf(this, "dstep");
         cfg.dynamicSmemBytes = ds_smem_f_;
-        if (ds_ne_ == 1)
-          WLR_CUDA(cudaLaunchKernelEx(&cfg, dstep_front<T, 1>, a));
-        else
-          WLR_CUDA(cudaLaunchKernelEx(&cfg, dstep_front<T, 2>, a));
+        if (ds_push_) {
+          if (ds_ne_ == 1)
+            WLR_CUDA(cudaLaunchKernelEx(&cfg, dstep_front<T, 1, true>, a));
+          else
+            WLR_CUDA(cudaLaunchKernelEx(&cfg, dstep_front<T, 2, true>, a));
+        } else {
+          if (ds_ne_ == 1)
+            WLR_CUDA(cudaLaunchKernelEx(&cfg, dstep_front<T, 1, false>, a));
+          else
+            WLR_CUDA(cudaLaunchKernelEx(&cfg, dstep_front<T, 2, false>, a));
+        }
         cfg.dynamicSmemBytes = ds_smem_;
       } else {
         Prof pf(this, "dstep");
@@ -1583,6 +1608,7 @@ class Solver final : public SolverBase {
   const T* front_rpre_ = nullptr;
   int ds_nc_ = 0, ds_ne_ = 1;
   size_t ds_smem_ = 0, ds_smem_f_ = 0;
+  bool ds_push_ = false;     // dstep_front exchanges by remote stores
   float *Kh_ = nullptr, *Kl_ = nullptr;   // K as a float pair (float path)
   T *ZKh_ = nullptr, *ZKl_ = nullptr;     // K V (high, low)
   T *C_ = nullptr, *Z2_ = nullptr, *Z2prev_ = nullptr;
