@@ -1482,6 +1482,111 @@ __device__ __forceinline__ void rp_phase1(const T* __restrict__ A2, int64_t lda,
     for (int v = 0; v < NPU; ++v) Ys[(4 * rg + u) * (NP + 1) + cg * NPU + v] = acc[u][v];
 }
 
+// Phase 1 with each slab split over four groups of 64 threads (float, NP <= 64): group kg
+// takes the steps kk = 8 kg .. 8 kg + 7 of every slab, and its thread (rg, cg) =
+// (t / 8, t % 8) owns rows 8 rg .. 8 rg + 7 and columns cg CB .. cg CB + CB - 1 (CB = NP / 8):
+// two 4-row vectors of A2 and one CB-vector of Z2 per step for 8 CB products (four times
+// the products per shared-memory load of rp_phase1, and 8 CB independent sums per thread).
+// After the last slab the groups' sums go to the stage buffers and Ys takes them in group
+// order.
+template <int NPU>
+__device__ __forceinline__ void rp_phase1_ks(const float* __restrict__ A2, int64_t lda,
+                                             const float* __restrict__ Z2, int m, int n2, int i0,
+                                             bool vec, float* __restrict__ As, float* __restrict__ Ys) {
+  using T = float;
+  constexpr int NP = 16 * NPU, CB = NP / 8;
+  constexpr int S = RowPassSmem<T>::kStages;
+  constexpr int CH = 16 / sizeof(T);
+  constexpr int slab = RP_BK * RP_BM + RP_BK * NP;
+  static_assert(4 * RP_BM * NP <= S * slab, "the group sums fit in the stage buffers");
+  const int tid = threadIdx.x;
+  const int kg = tid >> 6, rg = (tid & 63) >> 3, cg = tid & 7;
+  T acc[8][CB];
+#pragma unroll
+  for (int u = 0; u < 8; ++u)
+#pragma unroll
+    for (int v = 0; v < CB; ++v) acc[u][v] = T(0);
+  const int nsl = (n2 + RP_BK - 1) / RP_BK;
+  auto issue = [&](int sl) {
+    if (sl < nsl) {
+      T* As_ = As + (size_t)(sl % S) * slab;
+      T* Zs_ = As_ + RP_BK * RP_BM;
+      const int j0 = sl * RP_BK;
+      if (vec) {
+        for (int e = tid; e < RP_BK * RP_BM / CH; e += 256) {
+          const int rc = e % (RP_BM / CH), kk = e / (RP_BM / CH);
+          const int i = i0 + CH * rc, j = j0 + kk;
+          T* dst = As_ + kk * RP_BM + CH * rc;
+          if (j >= n2 || i >= m) {
+            cp_async16(dst, A2, 0);
+          } else if (i + CH <= m) {
+            cp_async16(dst, A2 + i + (int64_t)j * lda, 16);
+          } else {
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+              const bool ok = i + c < m;
+              cp_async_elem(dst + c, ok ? A2 + i + c + (int64_t)j * lda : A2, ok);
+            }
+          }
+        }
+      } else {
+        for (int e = tid; e < RP_BK * RP_BM; e += 256) {
+          const int r = e % RP_BM, kk = e / RP_BM;
+          const int i = i0 + r, j = j0 + kk;
+          const bool ok = i < m && j < n2;
+          cp_async_elem(As_ + kk * RP_BM + r, ok ? A2 + i + (int64_t)j * lda : A2, ok);
+        }
+      }
+      for (int e = tid; e < RP_BK * NP / CH; e += 256) {
+        const bool ok = j0 + (CH * e) / NP < n2;
+        cp_async16(Zs_ + CH * e, ok ? Z2 + (int64_t)j0 * NP + CH * e : Z2, ok ? 16 : 0);
+      }
+    }
+    cp_async_commit();
+  };
+#pragma unroll 1
+  for (int sl = 0; sl < S - 1; ++sl) issue(sl);
+#pragma unroll 1
+  for (int sl = 0; sl < nsl; ++sl) {
+    cp_async_wait<S - 2>();
+    __syncthreads();
+    issue(sl + S - 1);
+    const T* As_ = As + (size_t)(sl % S) * slab + 8 * rg + (size_t)(8 * kg) * RP_BM;
+    const T* Zs_ = As + (size_t)(sl % S) * slab + RP_BK * RP_BM + cg * CB + (size_t)(8 * kg) * NP;
+#pragma unroll
+    for (int kk = 0; kk < 8; ++kk) {
+      T a[4], b4[4], z[CB];
+      load4(a, As_ + kk * RP_BM);
+      load4(b4, As_ + kk * RP_BM + 4);
+      load_n<CB>(z, Zs_ + kk * NP);
+#pragma unroll
+      for (int v = 0; v < CB; ++v) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          acc[u][v] = fma(a[u], z[v], acc[u][v]);
+          acc[4 + u][v] = fma(b4[u], z[v], acc[4 + u][v]);
+        }
+      }
+    }
+  }
+  cp_async_wait<0>();
+  __syncthreads();
+  T* Pk = As;   // group kg's sums: Pk[(kg RP_BM + r) NP + c]
+#pragma unroll
+  for (int u = 0; u < 8; ++u)
+#pragma unroll
+    for (int v = 0; v < CB; ++v) Pk[(size_t)(kg * RP_BM + 8 * rg + u) * NP + cg * CB + v] = acc[u][v];
+  __syncthreads();
+  for (int e = tid; e < RP_BM * NP; e += 256) {
+    const int r = e / NP, c = e % NP;
+    T v = Pk[e];
+    v += Pk[RP_BM * NP + e];
+    v += Pk[2 * RP_BM * NP + e];
+    v += Pk[3 * RP_BM * NP + e];
+    Ys[r * (NP + 1) + c] = v;
+  }
+}
+
 // Row i of Q1 = X1new R^{-1} (QSplitOut) from the row's solution, held by a group of LG
 // lanes (lane g: x[sl] = X1new(i, g + LG sl)): q_a = sum_b x_b R^{-1}(b, a), summed in the
 // order b = 0, 1, ..., then split into TF32 h + l.  R^{-1} may be a full matrix (after the
@@ -1644,13 +1749,24 @@ row_pass(const T* __restrict__ A, int64_t lda, const T* __restrict__ W1, int64_t
   {
     const bool vec = ((reinterpret_cast<uintptr_t>(A2) & 15) == 0) &&
                      (((uint64_t)lda * sizeof(T)) % 16 == 0);
-    switch (NP / 16) {
-      case 1: rp_phase1<T, 1>(A2, lda, Z2, m, n2, i0, vec, As, Ys); break;
-      case 2: rp_phase1<T, 2>(A2, lda, Z2, m, n2, i0, vec, As, Ys); break;
-      case 3: rp_phase1<T, 3>(A2, lda, Z2, m, n2, i0, vec, As, Ys); break;
-      case 4: rp_phase1<T, 4>(A2, lda, Z2, m, n2, i0, vec, As, Ys); break;
-      case 5: rp_phase1<T, 5>(A2, lda, Z2, m, n2, i0, vec, As, Ys); break;
-      default: rp_phase1<T, 6>(A2, lda, Z2, m, n2, i0, vec, As, Ys); break;
+    if constexpr (sizeof(T) == 4) {
+      switch (NP / 16) {
+        case 1: rp_phase1_ks<1>(A2, lda, Z2, m, n2, i0, vec, As, Ys); break;
+        case 2: rp_phase1_ks<2>(A2, lda, Z2, m, n2, i0, vec, As, Ys); break;
+        case 3: rp_phase1_ks<3>(A2, lda, Z2, m, n2, i0, vec, As, Ys); break;
+        case 4: rp_phase1_ks<4>(A2, lda, Z2, m, n2, i0, vec, As, Ys); break;
+        case 5: rp_phase1<T, 5>(A2, lda, Z2, m, n2, i0, vec, As, Ys); break;
+        default: rp_phase1<T, 6>(A2, lda, Z2, m, n2, i0, vec, As, Ys); break;
+      }
+    } else {
+      switch (NP / 16) {
+        case 1: rp_phase1<T, 1>(A2, lda, Z2, m, n2, i0, vec, As, Ys); break;
+        case 2: rp_phase1<T, 2>(A2, lda, Z2, m, n2, i0, vec, As, Ys); break;
+        case 3: rp_phase1<T, 3>(A2, lda, Z2, m, n2, i0, vec, As, Ys); break;
+        case 4: rp_phase1<T, 4>(A2, lda, Z2, m, n2, i0, vec, As, Ys); break;
+        case 5: rp_phase1<T, 5>(A2, lda, Z2, m, n2, i0, vec, As, Ys); break;
+        default: rp_phase1<T, 6>(A2, lda, Z2, m, n2, i0, vec, As, Ys); break;
+      }
     }
   }
   __syncthreads();
