@@ -5,17 +5,21 @@
 // (G = C C^T and C V_s).
 //
 // Z = G2 V is formed without G2: kv_pair takes K V in double-float on all SMs (K = Kh + Kl
-// is stored as a float pair), and the cluster kernel subtracts B^T (B V) before rounding
-// to T (K and B^T B nearly cancel on the subspace).  The cluster kernel (NC = 16 CTAs where
-// the device allows it, else 8) splits the n2 basis rows; CTA r owns rows
-// [r R, r R + R), R = ceil(n2 / NC):
-//   1. partial B V over the CTA's rows, summed by every CTA through distributed shared
-//      memory; Z(rows) = K V - B^T (B V);
-//   2. partial H = V^T Z and P = Z^T Z, summed by CTA 0, which runs the Rayleigh-Ritz
-//      step (ritz_step) on the b x b problem;
-//   3. every CTA reads Y, Mv, Mz from CTA 0 and forms its rows of the next basis
-//      V Mv + Z Mz and of V_s = (V Y)(:, :s); then the partials of C C^T and C V_s are
-//      summed by CTA 0.
+// is stored as a float pair), and the cluster kernels subtract B^T (B V) before rounding
+// to T (K and B^T B nearly cancel on the subspace).  Two cluster kernels (NC = 16 CTAs
+// where the device allows it, else 8):
+//   dstep_front, the steady-state step for k <= 32: also steps a1 (the second CholeskyQR
+//     factor, on CTA 0) and a2 (B, C), arranged so that the other CTAs work on their basis
+//     rows while CTA 0 factors (see the comment above the kernel);
+//   dstep_cluster, the further steps of a cold start and every step for k > 32 (B and C
+//     come from coef_kernel3): CTA r owns rows [r R, r R + R), R = ceil(n2 / NC):
+//     1. partial B V over the CTA's rows, summed by every CTA through distributed shared
+//        memory; Z(rows) = K V - B^T (B V);
+//     2. partial H = V^T Z and P = Z^T Z, summed by CTA 0, which runs the Rayleigh-Ritz
+//        step (ritz_step) on the b x b problem;
+//     3. every CTA reads Y, Mv, Mz from CTA 0 and forms its rows of the next basis
+//        V Mv + Z Mz and of V_s = (V Y)(:, :s); then the partials of C C^T and C V_s are
+//        summed by CTA 0.
 // All waits are cluster barriers reached unconditionally by every CTA.
 #pragma once
 
