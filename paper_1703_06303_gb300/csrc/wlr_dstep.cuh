@@ -249,15 +249,25 @@ __device__ void ritz_step(T* wk, int b, int max_sweeps, T* __restrict__ theta,
     if (p > q) { const int t = p; p = q; q = t; }
   };
 
+  // the partner of index x in round `round` (the inverse of pair_of: N - 1 meets `round`,
+  // the others meet when their sum is 2 round mod N - 1)
+  auto partner_of = [&](int round, int x) -> int {
+    if (x == N - 1) return round;
+    if (x == round) return N - 1;
+    int y = 2 * round - x;
+    if (y < 0) y += N - 1;
+    if (y >= N - 1) y -= N - 1;
+    return y;
+  };
   // rotation annihilating (p, q): t = sign(tau) / (|tau| + sqrt(1 + tau^2)),
   // c = 1 / sqrt(1 + t^2), s = t c (square roots as x rsqrt(x); t ~ 1/(2 tau) once tau^2
-  // would overflow, which also covers a 1 / (2 a_pq) that overflows)
+  // would overflow).  An off-diagonal entry below 1e-30 in magnitude counts as zero.
   auto set_rot = [&](int cb, int p, int q, T app, T aqq, T apq) {
     T c = T(1), sn = T(0);
-    if (q < b && apq != T(0)) {
+    if (q < b && fabs(apq) >= T(5e-31)) {
       const T dq = aqq - app;
       const T a2 = T(2) * apq;
-      const T tau = dq == T(0) ? T(0) : (fabs(a2) < T(1e-30) ? dq / a2 : dq * qrcp(a2));
+      const T tau = dq == T(0) ? T(0) : dq * qrcp(a2);
       const T at = fabs(tau), tt = T(1) + tau * tau;
       T ta;
       if (at > T(1e15)) ta = at < T(1e30) ? T(0.5) * qrcp(at) : T(0);
@@ -268,12 +278,6 @@ __device__ void ritz_step(T* wk, int b, int max_sweeps, T* __restrict__ theta,
     }
     rot[cb][p] = Rot{c, -sn, q, 0};
     rot[cb][q] = Rot{c, sn, p, 0};
-  };
-  // entry (r, c) of J^T H J for the rotation set cb
-  auto rotated = [&](int cb, int r, int c) -> T {
-    const Rot R = rot[cb][r], C = rot[cb][c];
-    return R.c * (C.c * Hc[r][c] + C.s * Hc[r][C.partner]) +
-           R.s * (C.c * Hc[R.partner][c] + C.s * Hc[R.partner][C.partner]);
   };
   // pair i's angle is taken by lane 0 of warp DS_THREADS / 32 - 1 - i (one per warp,
   // spreading the shared-memory traffic of the angle computations over the schedulers;
@@ -319,10 +323,24 @@ __device__ void ritz_step(T* wk, int b, int max_sweeps, T* __restrict__ theta,
         Yn[r][c] = C.c * Yc[r][c] + C.s * Yc[r][C.partner];
       });
       if (round + 1 < N - 1 && angler) {
+        // the next round's pair (p, q) from the entries (p,p), (q,q), (p,q) of this round's
+        // J^T H J; this round's partners P, Q of p, q follow from the order, so the loads
+        // of H do not wait for those of the rotations
         int p, q;
         pair_of(round + 1, ai, p, q);
-        if (q < b) set_rot(cb ^ 1, p, q, rotated(cb, p, p), rotated(cb, q, q), rotated(cb, p, q));
-        else set_rot(cb ^ 1, p, q, T(0), T(0), T(0));
+        if (q < b) {
+          const int P = partner_of(round, p), Q = partner_of(round, q);
+          const Rot Rp = rot[cb][p], Rq = rot[cb][q];
+          const T hpp = Hc[p][p], hpP = Hc[p][P], hPp = Hc[P][p], hPP = Hc[P][P];
+          const T hqq = Hc[q][q], hqQ = Hc[q][Q], hQq = Hc[Q][q], hQQ = Hc[Q][Q];
+          const T hpq = Hc[p][q], hpQ = Hc[p][Q], hPq = Hc[P][q], hPQ = Hc[P][Q];
+          const T app = Rp.c * (Rp.c * hpp + Rp.s * hpP) + Rp.s * (Rp.c * hPp + Rp.s * hPP);
+          const T aqq = Rq.c * (Rq.c * hqq + Rq.s * hqQ) + Rq.s * (Rq.c * hQq + Rq.s * hQQ);
+          const T apq = Rp.c * (Rq.c * hpq + Rq.s * hpQ) + Rp.s * (Rq.c * hPq + Rq.s * hPQ);
+          set_rot(cb ^ 1, p, q, app, aqq, apq);
+        } else {
+          set_rot(cb ^ 1, p, q, T(0), T(0), T(0));
+        }
       }
       __syncthreads();
       Row* t0 = Hc; Hc = Hn; Hn = t0;

@@ -282,6 +282,47 @@ reduce_partials_split(const T* __restrict__ part, int64_t stride, int nchunks, i
   }
 }
 
+// The same reduction for chunk partials stored as float pairs (hi, lo) in 8-byte slots
+// (tc::gram_tf32x3_t): each warp adds its chunks c = w, w + 8, ... in double-float
+// (TwoSum), warp 0 adds the eight pairs in warp order, and the sum is converted to double
+// once.
+template <typename TF>
+__global__ void __launch_bounds__(256)
+reduce_pairs_split(const double* __restrict__ part, int64_t stride, int nchunks, int64_t len,
+                   double* __restrict__ out64, int kf = 0, TF* __restrict__ Fout = nullptr) {
+  __shared__ float2 sh[8][33];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t e = (int64_t)blockIdx.x * 32 + lane;
+  float hs = 0.f, ls = 0.f;
+  if (e < len) {
+    const float2* p2 = reinterpret_cast<const float2*>(part);
+#pragma unroll 4
+    for (int c = w; c < nchunks; c += 8) {
+      const float2 v = p2[(int64_t)c * stride + e];
+      float s, er;
+      two_sum(hs, v.x, s, er);
+      hs = s;
+      ls = (ls + v.y) + er;
+    }
+  }
+  sh[w][lane] = make_float2(hs, ls);
+  __syncthreads();
+  if (w == 0 && e < len) {
+    float h = 0.f, l = 0.f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const float2 v = sh[q][lane];
+      float s, er;
+      two_sum(h, v.x, s, er);
+      h = s;
+      l = (l + v.y) + er;
+    }
+    const double t = (double)h + (double)l;
+    if (out64) out64[e] = t;
+    if (Fout && e < (int64_t)kf * kf) Fout[e] = (TF)(t - (e % (kf + 1) == 0 ? 1.0 : 0.0));
+  }
+}
+
 // Sum of squares of an m x ncols column-major block, partial per block (double).
 template <typename T>
 __global__ void sumsq_partial(const T* __restrict__ A, int64_t lda, int m, int ncols,

@@ -999,11 +999,16 @@ class Solver final : public SolverBase {
 #undef WLR_GRAM
     count(1);
   }
-  void reduce64(int64_t stride, int nch, int64_t len, double* out64, int kf = 0, T* Fout = nullptr) {
+  // pairs: the partials are float pairs (the tensor-core Gram), else doubles
+  void reduce64(int64_t stride, int nch, int64_t len, double* out64, int kf = 0, T* Fout = nullptr,
+                bool pairs = false) {
     if (len <= 0) return;
     Prof pf(this, "reduce_partials");
-    reduce_partials_split<double, T><<<(unsigned)cdiv(len, 32), 256, 0, stream_>>>(part64_, stride, nch, len, out64,
-                                                                                    nullptr, kf, Fout);
+    if (pairs)
+      reduce_pairs_split<T><<<(unsigned)cdiv(len, 32), 256, 0, stream_>>>(part64_, stride, nch, len, out64, kf, Fout);
+    else
+      reduce_partials_split<double, T><<<(unsigned)cdiv(len, 32), 256, 0, stream_>>>(part64_, stride, nch, len, out64,
+                                                                                      nullptr, kf, Fout);
     count(1);
   }
 
@@ -1091,7 +1096,7 @@ class Solver final : public SolverBase {
       gram(Q1_, m, Q1_, m, k, A2, lda_, k, k + n2, L, ch_T_);
     }
     // Q1^T [Q1 A2] summed over the chunks by all SMs; chol2 and coef read the sum
-    reduce64(L, nchT, L, S2T_, k, k <= 32 ? F2_ : nullptr);
+    reduce64(L, nchT, L, S2T_, k, k <= 32 ? F2_ : nullptr, use_tc_);
     if (fused) {
       front_rpre_ = Rpre;
       return;

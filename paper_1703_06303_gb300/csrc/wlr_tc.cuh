@@ -157,7 +157,8 @@ static __global__ void form_q_split(const float* __restrict__ X1, int64_t ldx, c
 
 // ------------------------------------------------------------------------------------
 // Transposed form with per-slab read-back (the one the solver uses):
-//   part[c*pstride + a + col*P] = sum over the rows of chunk c of Y(i, col) X(i, a)
+//   part[c*pstride + a + col*P] = sum over the rows of chunk c of Y(i, col) X(i, a), stored
+//   as the float pair hi + lo in the 8 bytes of the slot (reduce_pairs_split adds them)
 // computed as D = Y^T X with the columns of Y on the 128 MMA rows (all TMEM lanes carry
 // data) and the P <= TNV columns of X as N = TNV (32 or 64).  Each 32-row slab is
 // accumulated by the tensor cores in FP32 into one of two TMEM buffers; while the MMA
@@ -394,12 +395,15 @@ gram_tf32x3_t(const __grid_constant__ CUtensorMap mY1h, const __grid_constant__ 
     if (!ok || *(volatile int*)&fail) {
       if (lane == 0) atomicOr(err, ERRBIT_TIMEOUT);
     } else {
+      // each chunk partial leaves as its float pair (hi, lo) in the 8 bytes of its slot;
+      // the reduction over the chunks adds the pairs and converts once (FP64 arithmetic,
+      // slow on this GPU, stays out of this kernel's tail)
       const int j = 32 * qd + lane;
       if (j < ncols) {
-        double* out = part + (int64_t)c * pstride + (int64_t)(gcol0 + j) * P + 32 * hf;
+        float2* out = reinterpret_cast<float2*>(part + (int64_t)c * pstride + (int64_t)(gcol0 + j) * P + 32 * hf);
 #pragma unroll
         for (int a = 0; a < 32; ++a)
-          if (32 * hf + a < P) out[a] = (double)hi[a] + (double)lo[a];
+          if (32 * hf + a < P) out[a] = make_float2(hi[a], lo[a]);
       }
     }
   }
