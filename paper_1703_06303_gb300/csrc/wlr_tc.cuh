@@ -47,18 +47,24 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
                : "memory");
 }
 // Wait for the phase with the given parity to complete; false after limit_ns.
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// The clock is read only once a first try has failed (most waits of a running pipeline
+// find the phase complete), then the wait gives up after limit_ns.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity,
                                           unsigned long long limit_ns = kWaitNs) {
+  if (mbar_try(bar, parity)) return true;
   const unsigned long long t0 = now_ns();
   while (true) {
-    unsigned done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    if (done) return true;
+    if (mbar_try(bar, parity)) return true;
     if (now_ns() - t0 > limit_ns) return false;
   }
 }
